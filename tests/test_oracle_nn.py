@@ -1,0 +1,144 @@
+"""Pins of the oracle's networks (Secs. 3.1, 4.2): feature layout, Eq. 15,
+the hand-written backward pass, Adam and the data-set normalisation.  No GPU."""
+import numpy as np
+import pytest
+
+from oracle import lbm, mlp
+from synth import glorot_mlp
+
+rng = np.random.default_rng(7)
+
+
+def _net(sizes, act, seed=3):
+    net = mlp.MLP(glorot_mlp(sizes, seed), act)
+    # non-zero biases so that their gradients are exercised
+    net.layers = [(Wl, rng.uniform(-0.2, 0.2, bl.shape)) for Wl, bl in net.layers]
+    return net
+
+
+def test_feature_layout():
+    ny, nx = 6, 8
+    g = np.zeros((9, ny, nx))
+    for i in range(9):
+        for y in range(ny):
+            for x in range(nx):
+                g[i, y, x] = 1000 * i + 10 * y + x
+    feats = lbm.nn_features(g, nx - 1)
+    for y in range(ny):
+        for k in range(3):
+            for j in range(3):
+                for i in range(9):
+                    v = feats[y, k * 27 + j * 9 + i]
+                    assert v == 1000 * i + 10 * ((y + j - 1) % ny) + (nx - 2 - k)
+    assert lbm.nn_base_index(3) == 12  # f_3 at (L-1, y)
+
+
+def test_zero_network_extrapolates_with_zero_gradient():
+    ny, nx = 10, 12
+    rho = 1 + 0.01 * rng.uniform(-1, 1, (ny, nx))
+    g = lbm.equilibrium(rho, 0.04 + 0.01 * rng.uniform(-1, 1, (ny, nx)), 0.0)
+    net = mlp.MLP([(np.zeros((64, 81)), np.zeros(64)), (np.zeros((64, 64)), np.zeros(64)),
+                   (np.zeros((3, 64)), np.zeros(3))], "tanh")
+    feats = lbm.nn_features(g, nx - 1)
+    out, bad = lbm.nn_reconstruct_east(g[:, :, nx - 1], feats, net, 1.0, 0.05)
+    assert not bad.any()
+    for i in (3, 6, 7):
+        assert np.array_equal(out[i], g[i, :, nx - 2])
+    for i in (0, 1, 2, 4, 5, 8):
+        assert np.array_equal(out[i], g[i, :, nx - 1])
+
+
+def test_fallback_to_zouhe():
+    ny, nx = 5, 6
+    g = lbm.equilibrium(np.ones((ny, nx)), 0.05, 0.0)
+    net = mlp.MLP([(np.zeros((3, 81)), np.array([10.0, 0.0, 0.0]))], "tanh")   # g3 += 10
+    feats = lbm.nn_features(g, nx - 1)
+    out, bad = lbm.nn_reconstruct_east(g[:, :, nx - 1], feats, net, 1.0, 0.05)
+    assert bad.all()
+    zh, _ = lbm.zouhe_pressure_east(g[:, :, nx - 1], 1.0)
+    assert np.array_equal(out, zh)
+    net2 = mlp.MLP([(np.zeros((3, 81)), np.array([np.nan, 0.0, 0.0]))], "tanh")
+    _, bad2 = lbm.nn_reconstruct_east(g[:, :, nx - 1], feats, net2, 1.0, 0.05)
+    assert bad2.all()
+
+
+def _fd_check(net, loss_fn, eps=1e-6):
+    p0 = net.flat()
+    loss, grads = loss_fn(net)
+    g = mlp.flatten_grads(grads)
+    num = np.empty_like(p0)
+    for k in range(p0.size):
+        p = p0.copy()
+        p[k] += eps
+        net.set_flat(p)
+        lp, _ = loss_fn(net)
+        p[k] -= 2 * eps
+        net.set_flat(p)
+        lm, _ = loss_fn(net)
+        num[k] = (lp - lm) / (2 * eps)
+    net.set_flat(p0)
+    return g, num
+
+
+@pytest.mark.parametrize("act", ["tanh", "leaky"])
+def test_backward_matches_central_differences(act):
+    net = _net([81, 12, 10, 3], act)
+    net.in_mean = rng.uniform(0, 0.3, 81)
+    net.in_std = rng.uniform(0.05, 0.2, 81)
+    net.out_scale = 0.01
+    batch = np.hstack([rng.uniform(0, 0.5, (16, 81)), rng.uniform(0, 0.5, (16, 3))])
+    g, num = _fd_check(net, lambda n: mlp.direct_loss_and_grad(n, batch))
+    assert np.allclose(g, num, rtol=1e-6, atol=5e-11)
+    assert np.abs(g).max() > 1e-5
+
+
+def test_adam_first_step_closed_form():
+    """After one step, m_hat = g and v_hat = g^2, so every parameter moves by
+    exactly lr * g / (|g| + eps)  (Kingma & Ba 2015, Algorithm 1)."""
+    p = rng.normal(size=50)
+    g = rng.normal(size=50)
+    opt = mlp.Adam(lr=1e-3)
+    p1 = opt.step(p, g)
+    assert np.allclose(p1, p - 1e-3 * g / (np.abs(g) + 1e-8), atol=1e-16)
+
+
+def test_linear_network_converges_to_least_squares():
+    """A network without hidden layers is linear; training Eq. 16 to
+    convergence must reach the normal-equations solution."""
+    n = 400
+    x = rng.uniform(-1, 1, (n, 81))
+    true_w = rng.normal(size=(3, 81)) * 0.1
+    base = x[:, [12, 15, 16]]
+    ref = base + x @ true_w.T + 0.3 + 0.01 * rng.normal(size=(n, 3))
+    data = np.hstack([x, ref])
+    net = mlp.MLP([(np.zeros((3, 81)), np.zeros(3))], "tanh")
+    opt = mlp.Adam(lr=0.02)
+    order = np.tile(np.arange(4), 1500)
+    mlp.train_direct(net, data, 100, order, opt)
+    opt2 = mlp.Adam(lr=0.002)
+    opt2.t = 0
+    mlp.train_direct(net, data, 100, np.tile(np.arange(4), 1500), opt2)
+    # least squares with intercept on the residual target
+    A = np.hstack([x, np.ones((n, 1))])
+    sol, *_ = np.linalg.lstsq(A, ref - base, rcond=None)
+    Wl, bl = net.layers[0]
+    assert np.allclose(Wl, sol[:81].T, atol=2e-3)
+    assert np.allclose(bl, sol[81], atol=2e-3)
+
+
+def test_dataset_stats_on_constructed_data():
+    n = 64
+    z = np.where(np.arange(n) % 2 == 0, -1.0, 1.0)      # mean 0, population std 1
+    a = rng.uniform(-1, 1, 81)
+    b = rng.uniform(0.1, 2, 81)
+    x = a + b * z[:, None]
+    x[:, 40] = 0.25                                      # a constant feature
+    b[40] = 0.0
+    a[40] = 0.25
+    resid = 0.003 * z[:, None] * np.ones((1, 3)) + 0.5
+    ref = x[:, [12, 15, 16]] + resid
+    mean, std, out_scale = mlp.dataset_stats(np.hstack([x, ref]))
+    assert np.allclose(mean, a, atol=1e-15)
+    expect_std = np.where(b == 0, 1.0, b)
+    assert np.allclose(std, expect_std, atol=1e-14)
+    assert abs(out_scale - 0.003) < 1e-15
