@@ -1,0 +1,213 @@
+/*
+ * lbm.h -- C ABI of the GB300 lattice Boltzmann outflow library.
+ *
+ * The library advances a 2D D2Q9 lattice Boltzmann simulation on one GPU:
+ * a fused pull-stream-and-collide step (BGK or MRT) with full-way bounce-back
+ * walls and momentum-exchange forces, a Zou & He velocity inlet on the west
+ * edge, and an east outflow that rebuilds the unknown incoming populations
+ * f3, f6, f7 by Zou & He, by a small neural network, or by a characteristic
+ * boundary condition.  This follows "Reduction of Outflow Boundary Influence
+ * on Aerodynamic Performance using Neural Networks" (arXiv 2506.05293),
+ * cited below by section and equation.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an lbm_status; nothing throws across the ABI.  On an
+ *    error lbm_last_error() gives a message (thread-local, valid until the
+ *    next call on that thread).
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership.  Host arrays passed out are written in full.
+ *  - 2D host arrays are row-major (ny rows of nx values, x fastest);
+ *    population arrays are (9, ny, nx) with the direction slowest.
+ *  - Velocities: c0=(0,0) c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1) c5=(1,1)
+ *    c6=(-1,1) c7=(-1,-1) c8=(1,-1); weights 4/9, 1/9 (1-4), 1/36 (5-8).
+ *  - Work is enqueued on the simulation's CUDA stream.  lbm_step never
+ *    blocks; calls that return data to the host synchronise that stream.
+ *    Device-side faults (non-finite density) are latched in a status word
+ *    that lbm_sync and the data-returning calls report.
+ *  - Calls on one lbm_sim are not thread-safe; different sims are.
+ */
+#ifndef GB300_LBM_H
+#define GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_sim lbm_sim; /* opaque, owned by the library */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,         /* invalid argument (null pointer, bad size, bad enum)   */
+  LBM_ERR_STATE = 2,       /* call not valid in the simulation's current state       */
+  LBM_ERR_OOM = 3,         /* device allocation failed                               */
+  LBM_ERR_CUDA = 4,        /* a CUDA runtime call failed (no device, launch error)   */
+  LBM_ERR_NONFINITE = 5,   /* the device saw a non-finite density (run diverged)     */
+  LBM_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                          */
+  LBM_ERR_UNSUPPORTED = 7  /* valid request this build does not implement            */
+} lbm_status;
+
+typedef enum { LBM_BGK = 0, LBM_MRT = 1 } lbm_collision;
+
+/* Storage precision of the populations.  All store the deviation from the rest
+ * state, h_i = f_i - w_i.  FP64 collides in FP64; FP32 and FP16DEV collide in
+ * FP32 (FP16DEV rounds to nearest-even on store). */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2 } lbm_precision;
+
+typedef enum { LBM_OUTFLOW_ZOUHE = 0, LBM_OUTFLOW_NN = 1, LBM_OUTFLOW_CBC = 2 } lbm_outflow_kind;
+
+/* Cell kinds used by lbm_set_geometry. */
+enum { LBM_CELL_FLUID = 0, LBM_CELL_SOLID = 1, LBM_CELL_WALL = 2 };
+
+/* Optional device allocator (for instance backed by a framework's caching
+ * allocator).  alloc returns NULL on failure; free accepts what alloc gave. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* ctx;
+} lbm_allocator;
+
+typedef struct {
+  int32_t nx, ny;           /* lattice size; nx >= 3 (>= 5 for NN/CBC outflow) unless x_periodic;
+                               ny <= 65535, 9 * ny * pitch < 2^31 (pitch = nx rounded up to 64) */
+  double tau;               /* BGK relaxation time (Eq. 2), tau > 1/2; nu = (tau - 1/2) / 3 */
+  int32_t collision;        /* lbm_collision */
+  double mrt_rates[9];      /* MRT rates in moment order (rho, e, eps, jx, qx, jy, qy, pxx, pxy);
+                               the conserved ones (0, 3, 5) are ignored; the stress rates 7, 8
+                               default to 1/tau.  All zero: e, eps, q rates 1, stress 1/tau. */
+  int32_t precision;        /* lbm_precision */
+  int32_t x_periodic;       /* 1: x wraps too (no inlet, no outflow); 0: open in x */
+  double u_in;              /* west inlet velocity (Zou & He, Sec. 2.2 "by symmetry") */
+  double v_pert_amp;        /* amplitude of the seeded inlet v perturbation */
+  uint64_t seed;            /* v(y,t) = amp (2 xi - 1), xi from SplitMix64(seed ^ (t 2^20 + y)) */
+  double rho_out;           /* outflow density for Zou & He (Eq. 7) */
+  void* stream;             /* cudaStream_t to run on; NULL: the library creates one */
+  const lbm_allocator* alloc; /* NULL: cudaMalloc / cudaFree */
+  int64_t force_capacity;   /* device ring of per-step forces; 0: 1 << 20 steps */
+} lbm_config;
+
+/* Fill *cfg with defaults (tau 0.6, BGK, FP32, open x, rho_out 1). */
+lbm_status lbm_config_default(lbm_config* cfg);
+
+/* Create a simulation: allocates two population buffers of
+ * 9 * ny * pitch elements (pitch = nx rounded up to 64), initialised to the
+ * rest state (rho = 1, u = 0), all cells fluid, Zou & He outflow. */
+lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out);
+lbm_status lbm_destroy(lbm_sim* sim);
+
+/* Cell kinds, host uint8[ny][nx]: 0 fluid, 1 solid counted in the force,
+ * 2 solid not counted (channel walls).  Solid nodes use full-way bounce-back
+ * (Eq. 11).  A counted link joins a kind-1 node s and a fluid node s - c_i
+ * (x wraps only if x_periodic; y always wraps). */
+lbm_status lbm_set_geometry(lbm_sim* sim, const uint8_t* kind);
+
+/* Set every node to f^eq(rho, ux, uy) (Eq. 3), host double[ny][nx] each;
+ * NULL means rho = 1 or u = 0.  Resets the step counter, the force series and
+ * the boundary state. */
+lbm_status lbm_init_equilibrium(lbm_sim* sim, const double* rho, const double* ux,
+                                const double* uy);
+
+/* Outflow by Zou & He with prescribed density (Sec. 2.2, Eqs. 5-10): rho_out,
+ * u from Eq. 7, zero tangential velocity. */
+lbm_status lbm_set_outflow_zouhe(lbm_sim* sim, double rho_out);
+
+/* A small fully connected network: n_layers layers, layer l maps sizes[l] ->
+ * sizes[l+1]; hidden layers apply act (0 tanh, 1 LeakyReLU slope 0.01), the
+ * last is linear.  params holds, per layer, W (row-major, sizes[l+1] x
+ * sizes[l]) then b.  Inputs are z-scored with in_mean / in_std (NULL: 0 / 1)
+ * before the first layer and the output is multiplied by out_scale.
+ * All pointers are host memory and are copied. */
+#define LBM_MLP_MAX_LAYERS 4
+typedef struct {
+  int32_t n_layers;
+  int32_t sizes[LBM_MLP_MAX_LAYERS + 1];
+  int32_t act;
+  const float* params;
+  int64_t n_params;
+  const float* in_mean;
+  const float* in_std;
+  float out_scale;
+} lbm_mlp;
+
+/* Outflow by direct reconstruction (Sec. 3.1, Eq. 15): for every east node,
+ * s = net(81 inputs), g_i(L) = f_i(L-1) + s_i for i = 3, 6, 7.  The inputs
+ * are the nine post-stream populations of columns L-1, L-2, L-3 at rows
+ * y-1, y, y+1 (index k*27 + j*9 + i for column L-1-k, row y-1+j).  The net
+ * must map 81 -> ... -> 3 with at most 64 units per hidden layer.  A node
+ * falls back to Zou & He (rho_out of the config) when an output is not finite,
+ * a rebuilt population is negative, or |rho - rho_out| > fallback_drho; the
+ * count is reported by lbm_nn_fallbacks.  Needs nx >= 5. */
+lbm_status lbm_set_outflow_nn(lbm_sim* sim, const lbm_mlp* net, double fallback_drho);
+lbm_status lbm_nn_fallbacks(lbm_sim* sim, int64_t* count);
+
+/* Enqueue n time steps (n >= 0).  Each step: pull streaming (Eq. 1), momentum
+ * exchange (Eqs. 13-14) and bounce-back (Eq. 11) at solid nodes, the west
+ * inlet, the east outflow, and collision of all fluid nodes; the force on
+ * kind-1 nodes is appended to the device force ring. */
+lbm_status lbm_step(lbm_sim* sim, int64_t n);
+
+/* Wait for the stream; report a latched device fault. */
+lbm_status lbm_sync(lbm_sim* sim);
+
+/* Number of completed steps. */
+lbm_status lbm_time(lbm_sim* sim, int64_t* t);
+
+/* Drain the force series: writes up to cap per-step forces (F_x, F_y, lattice
+ * units, F = Delta P / Delta t of Eqs. 13-14) recorded since the previous
+ * drain, oldest first, and sets *n_out.  If more steps than the ring holds ran
+ * since the previous drain, only the newest ring-capacity entries remain. */
+lbm_status lbm_forces(lbm_sim* sim, double* fx, double* fy, int64_t cap, int64_t* n_out);
+
+/* Macroscopic fields rho, ux, uy (Eq. 4), host double[ny][nx] each (any may
+ * be NULL).  At solid nodes these are moments of what bounce-back stored. */
+lbm_status lbm_fields(lbm_sim* sim, double* rho, double* ux, double* uy);
+
+/* Read / write the populations f_i (not shifted), host double[9][ny][nx].
+ * lbm_get_populations returns the post-collision state of the last step. */
+lbm_status lbm_get_populations(lbm_sim* sim, double* f);
+lbm_status lbm_set_populations(lbm_sim* sim, const double* f);
+
+/* Total mass: sum of every population on every node, accumulated in FP64. */
+lbm_status lbm_mass(lbm_sim* sim, double* mass);
+
+/* Device pointer of the current population buffer and its geometry, for
+ * zero-copy access: element (i, y, x) is at base[i * plane + y * pitch + x],
+ * storing f_i - w_i in the configured precision.  Valid until the next call
+ * that steps or destroys the sim. */
+lbm_status lbm_device_state(lbm_sim* sim, void** base, int64_t* pitch, int64_t* plane);
+
+/* Tiling of the step kernel: rows per strip (1..64; a strip is 128 columns)
+ * and register-budget variant (0..2: at least 6, 8 or 10 resident blocks of
+ * 128 threads per SM).  Populations do not depend on the tiling; the FP64
+ * force sum may differ in its last bits (partial sums change order). */
+lbm_status lbm_set_tiling(lbm_sim* sim, int32_t rows, int32_t variant);
+lbm_status lbm_get_tiling(lbm_sim* sim, int32_t* rows, int32_t* variant);
+
+/* Autotuner: time `steps` (1..10000) single steps of every candidate tiling
+ * (rows 2, 4, 8, 16, 32 x the three variants) with CUDA events on the sim's
+ * stream and keep the fastest; *best_ms (nullable) gets its mean step time.
+ * With flush_bytes > 0 a scratch buffer of that size is written before each
+ * timed step so the step starts from a cold L2.  The populations, step
+ * counter, force series and fallback count are restored afterwards.  Uses
+ * temporary device memory (one population buffer + flush_bytes). */
+lbm_status lbm_autotune(lbm_sim* sim, int32_t steps, int64_t flush_bytes, float* best_ms);
+
+/* Strouhal number of a lift series (Sec. 2.3): St = f D / U with f the peak of
+ * |DFT| of the last 2^m samples (largest power of two <= n, n >= 8), mean
+ * removed, Hann window, refined by a parabola through the peak bin and its
+ * neighbours.  Host-only; needs no device. */
+lbm_status lbm_strouhal(const double* cl, int64_t n, double length, double u, double* st);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+/* Library version string. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_LBM_H */

