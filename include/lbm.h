@@ -194,6 +194,34 @@ lbm_status lbm_get_tiling(lbm_sim* sim, int32_t* rows, int32_t* variant);
  * temporary device memory (one population buffer + flush_bytes). */
 lbm_status lbm_autotune(lbm_sim* sim, int32_t steps, int64_t flush_bytes, float* best_ms);
 
+/* One FP32 time step of a lattice whose buffers the caller owns, without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory themselves or let a library
+ * do it -- code recording a CUDA stream capture that must not contain
+ * allocations, frameworks whose pool owns all device memory, real-time loops
+ * that forbid allocator calls after start-up.
+ *
+ * It applies the same step as lbm_step with the Zou & He outflow (or periodic
+ * x): src -> dst, both device float[9][ny][pitch] holding h_i = f_i - w_i;
+ * kind is a device uint8[ny][nx] of cell kinds as for lbm_set_geometry; t is
+ * the step index (it keys the seeded inlet perturbation); force is a device
+ * double[2] that receives (F_x, F_y) of the step.  From cfg it uses nx, ny,
+ * tau, collision, mrt_rates, x_periodic, u_in, v_pert_amp, seed, rho_out and
+ * stream (NULL: the legacy default stream); precision must be LBM_FP32 and
+ * alloc and force_capacity are ignored.  The call only enqueues work and
+ * reports launch errors; it does not synchronise.
+ *
+ * Scratch: the per-block force partials live in a 128 KiB static device
+ * array that every GPU loading the library holds until exit, so the lattice
+ * may have at most 8192 strips of 128 x 8 nodes (8,388,608 nodes); larger
+ * lattices are rejected with LBM_ERR_ARG.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (for instance on two streams) race on it and
+ * must be ordered by the caller. */
+lbm_status lbm_step_noalloc(const lbm_config* cfg, const float* src, float* dst,
+                            const uint8_t* kind, int64_t pitch, int64_t t, double* force);
+
 /* Strouhal number of a lift series (Sec. 2.3): St = f D / U with f the peak of
  * |DFT| of the last 2^m samples (largest power of two <= n, n >= 8), mean
  * removed, Hann window, refined by a parabola through the peak bin and its

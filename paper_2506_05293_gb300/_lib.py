@@ -64,6 +64,8 @@ SIGNATURES = {
     "lbm_set_tiling": (c_int, [c_void_p, c_int32, c_int32]),
     "lbm_get_tiling": (c_int, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     "lbm_autotune": (c_int, [c_void_p, c_int32, c_int64, POINTER(c_float)]),
+    "lbm_step_noalloc": (c_int, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_int64,
+                                 c_int64, c_void_p]),
     "lbm_strouhal": (c_int, [POINTER(c_double), c_int64, c_double, c_double, POINTER(c_double)]),
     "lbm_last_error": (c_char_p, []),
     "lbm_version": (c_char_p, []),

@@ -224,6 +224,14 @@ def lbm_autotune(sim, steps=20, flush_bytes=0):
     return r, v, ms.value
 
 
+def lbm_step_noalloc(cfg, src_ptr, dst_ptr, kind_ptr, pitch, t, force_ptr):
+    """One step on caller-owned device buffers (raw device pointers as ints);
+    the library allocates nothing.  See include/lbm.h."""
+    _check(_lib.load().lbm_step_noalloc(byref(cfg), c_void_p(src_ptr), c_void_p(dst_ptr),
+                                        c_void_p(kind_ptr), int(pitch), int(t),
+                                        c_void_p(force_ptr)))
+
+
 def lbm_strouhal(cl, length, u):
     cl = np.ascontiguousarray(cl, dtype=np.float64)
     st = c_double()

@@ -259,6 +259,10 @@ void fft_inplace(std::vector<std::complex<double>>& a) {
 
 }  // namespace
 
+namespace lbm {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace lbm
+
 extern "C" {
 
 const char* lbm_last_error(void) { return g_err.c_str(); }

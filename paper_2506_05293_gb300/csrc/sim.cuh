@@ -102,6 +102,9 @@ void launch_mass(int prec, const void* src, int nx, int ny, int64_t pitch, int64
                  double* partials, int n_partials, double* out, cudaStream_t s);
 void launch_nn_outflow(int prec, const NnParams& p, cudaStream_t s);
 
+// message returned by lbm_last_error() on this thread
+void set_last_error(const std::string& msg);
+
 }  // namespace lbm
 
 // The opaque simulation object behind the C ABI.
