@@ -1,22 +1,26 @@
-"""Benchmark of the hot path: D2Q9 stream-and-collide with the cylinder
-geometry of the paper's truncation study, through the C ABI.
+"""Benchmark of the hot path through the C ABI: D2Q9 stream-and-collide with
+the cylinder geometry of the paper's truncation study (Sec. 3.1, Fig. 6).
 
-Workload (default): cylinder D = 40 centred at x = 8D, mid-height; height
-16D = 640, wake L = 32D behind the centre, nx = 8D + L = 1600, so
-1600 x 640 = 1,024,000 nodes; BGK, Re = 100 (U = 0.05), FP32 storage, Zou & He inlet and outflow,
-periodic sides, started from f^eq(1, (U, 0)).  One bench step = one time step
-of the whole lattice (one fused kernel launch).  The 74 MB working set fits
-in the 129 MB L2, so L2 is flushed (a 256 MB device write) between timed steps
-and each step is timed alone with CUDA events on the simulation's stream.
+Default workload ``cylinder_sweep_D40``: the truncation-study sweep as one
+batch of 12 lattices advanced together -- cylinder D = 40 centred at x = 8D,
+mid-height, height 16D = 640, wake L in {4D, 8D, 32D} behind the centre
+(nx = 8D + L = 480, 640, 1600), Re in {100, 200} (U = 0.05), BGK and MRT,
+FP32 storage, Zou & He inlet and outflow, periodic sides, started from
+f^eq(1, (U, 0)): 6,963,200 nodes, 501 MB of populations, larger than the
+129 MB L2, so steps run back to back (no flush).  One bench step = one time
+step of every lattice (one kernel launch).
 
-Prints one JSON line (see the repository's benchmark contract).
+Other workloads: ``cylinder_D40_L32D_Re100`` (the 1600 x 640 lattice alone;
+its 74 MB fit in L2, so a 256 MB write flushes L2 before each timed step and
+steps are timed one by one) and ``cylinder_D160_8192x4096``.
+
+Prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import re
 import statistics
@@ -29,23 +33,32 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 BYTES_PER_NODE = {"fp32": 72, "fp16dev": 36, "fp64": 144}
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _cyl(D, height_D, wake_D, re_, coll, U=0.05):
+    return dict(D=D, ny=int(round(height_D * D)), nx=int(round(8 * D + wake_D * D)), Re=re_,
+                U=U, collision=coll)
+
+
 WORKLOADS = {
-    # name: (D, height in D, wake length L in D, Re, U, collision)
-    "cylinder_D40_L32D_Re100": (40, 16, 32, 100.0, 0.05, "bgk"),
-    "cylinder_D40_L32D_Re100_mrt": (40, 16, 32, 100.0, 0.05, "mrt"),
-    "cylinder_D160_8192x4096": (160, 25.6, 43.2, 100.0, 0.05, "bgk"),
+    "cylinder_sweep_D40": [_cyl(40, 16, L, re_, c) for c in ("bgk", "mrt") for re_ in (100, 200)
+                           for L in (4, 8, 32)],
+    "cylinder_D40_L32D_Re100": [_cyl(40, 16, 32, 100, "bgk")],
+    "cylinder_D160_8192x4096": [_cyl(160, 25.6, 43.2, 100, "bgk")],
 }
 
 
-def workload_geometry(name):
+def member_geometry(m):
+    """Cell kinds and tau of one workload member (cylinder at (8D, ny/2))."""
     from synth import cylinder_mask
-    D, hD, LD, re_, U, coll = WORKLOADS[name]
-    ny = int(round(hD * D))
-    nx = int(round(8 * D + LD * D))
-    kind = cylinder_mask(nx, ny, 8 * D, ny / 2, D)
-    nu = U * D / re_
-    tau = 3 * nu + 0.5
-    return dict(nx=nx, ny=ny, kind=kind, tau=tau, U=U, D=D, collision=coll)
+    kind = cylinder_mask(m["nx"], m["ny"], 8 * m["D"], m["ny"] / 2, m["D"])
+    tau = 3 * m["U"] * m["D"] / m["Re"] + 0.5
+    return kind, tau
+
+
+def workload_nodes(wl):
+    return sum(m["nx"] * m["ny"] for m in WORKLOADS[wl])
 
 
 def measured_peaks():
@@ -55,6 +68,14 @@ def measured_peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("step.cu", "lattice.cuh", "sim.cuh"):
+        with open(os.path.join(ROOT, "paper_2506_05293_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def step_kernel_traffic(prec, wl):
@@ -71,14 +92,6 @@ def step_kernel_traffic(prec, wl):
     return float(t.group(1))
 
 
-def kernel_source_hash():
-    h = hashlib.sha256()
-    for f in ("step.cu", "lattice.cuh", "sim.cuh"):
-        with open(os.path.join(ROOT, "paper_2506_05293_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
 class ClockSampler:
     """SM clock and clock-event (throttle) reasons sampled every 10 ms during
     the timed region, read through NVML (libnvidia-ml) with ctypes; read-only."""
@@ -91,6 +104,7 @@ class ClockSampler:
         self.samples = []
         self.max_mhz = None
         self.error = None
+        self.thread = None
 
     def _nvml(self):
         import ctypes
@@ -98,7 +112,6 @@ class ClockSampler:
         if lib.nvmlInit_v2() != 0:
             raise RuntimeError("nvmlInit failed")
         h = ctypes.c_void_p()
-        # NVML enumerates by PCI order; honour CUDA_VISIBLE_DEVICES if it is numeric
         idx = self.index
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         if vis and all(v.strip().isdigit() for v in vis.split(",")):
@@ -131,7 +144,6 @@ class ClockSampler:
             self.thread.start()
         except Exception as ex:   # no NVML: report the clocks as unsampled
             self.error = str(ex)
-            self.thread = None
         return self
 
     def __exit__(self, *a):
@@ -161,24 +173,29 @@ def dist_env():
 
 
 def cpu_oracle_sample(wl, steps, warmup=1):
-    """Time the FP64 oracle on the same workload in a single-threaded child
-    process: ``warmup`` untimed steps, then ``steps`` steps timed one by one.
-    Returns (GLUPS, total seconds, per-step seconds)."""
+    """Time the FP64 oracle on the workload in a single-threaded child process:
+    bench step k advances member k mod n by one time step (a bounded sample of
+    the batch step).  Returns (GLUPS, total seconds, per-step seconds, nodes)."""
     code = (
         "import sys, time, json; sys.path.insert(0, %r)\n"
-        "from bench import workload_geometry\n"
+        "from bench import WORKLOADS, member_geometry\n"
         "from oracle import lbm\n"
         "import numpy as np\n"
-        "g = workload_geometry(%r)\n"
-        "cfg = lbm.Config(nx=g['nx'], ny=g['ny'], tau=g['tau'], collision=g['collision'], u_in=g['U'])\n"
-        "s = lbm.Solver(cfg, g['kind'])\n"
-        "fl = g['kind'] == 0\n"
-        "s.init_equilibrium(None, np.where(fl, g['U'], 0.0), None)\n"
-        "s.step(%d)\n"
-        "dts = []\n"
-        "for _ in range(%d):\n"
-        "    t0 = time.perf_counter(); s.step(1); dts.append(time.perf_counter() - t0)\n"
-        "print(json.dumps({'dts': dts, 'cells': g['nx'] * g['ny']}))\n" % (ROOT, wl, warmup, steps))
+        "ms = WORKLOADS[%r]\n"
+        "sims = []\n"
+        "for m in ms:\n"
+        "    kind, tau = member_geometry(m)\n"
+        "    s = lbm.Solver(lbm.Config(nx=m['nx'], ny=m['ny'], tau=tau, collision=m['collision'],"
+        " u_in=m['U']), kind)\n"
+        "    s.init_equilibrium(None, np.where(kind == 0, m['U'], 0.0), None)\n"
+        "    sims.append((s, m['nx'] * m['ny']))\n"
+        "for k in range(%d):\n"
+        "    sims[k %% len(sims)][0].step(1)\n"
+        "dts, nodes = [], 0\n"
+        "for k in range(%d):\n"
+        "    s, n = sims[k %% len(sims)]\n"
+        "    t0 = time.perf_counter(); s.step(1); dts.append(time.perf_counter() - t0); nodes += n\n"
+        "print(json.dumps({'dts': dts, 'nodes': nodes}))\n" % (ROOT, wl, warmup, steps))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
@@ -187,7 +204,7 @@ def cpu_oracle_sample(wl, steps, warmup=1):
         raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
     dt = sum(d["dts"])
-    return d["cells"] * steps / dt / 1e9, dt, d["dts"]
+    return d["nodes"] / dt / 1e9, dt, d["dts"], d["nodes"]
 
 
 def run_reference(args):
@@ -195,24 +212,46 @@ def run_reference(args):
     if rank != 0:
         return 0
     wl = args.workload
-    _, _, per_step = cpu_oracle_sample(wl, args.steps, args.warmup)
-    g = workload_geometry(wl)
-    cells = g["nx"] * g["ny"]
-    total = sum(per_step)
-    value = cells * args.steps / total / 1e9
+    value, total, per_step, nodes = cpu_oracle_sample(wl, args.steps, args.warmup)
+    sample = (f"{args.steps} oracle time steps, one member lattice of {wl} per bench step "
+              f"(round robin over its {len(WORKLOADS[wl])} lattices), numpy FP64, 1 thread")
     line = {
-        "impl": "reference", "metric": "GLUPS", "value": value, "unit": "GLUPS", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": wl, "nx": g["nx"], "ny": g["ny"], "collision": g["collision"],
-                   "outflow": "zouhe", "sample": "one oracle time step per bench step"},
+        "impl": "reference", "metric": "GLUPS", "value": value, "unit": "GLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl, "lattices": len(WORKLOADS[wl]), "nodes": workload_nodes(wl),
+                   "outflow": "zouhe", "sample": sample},
         "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full time steps of {wl}, numpy FP64, 1 thread"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _make_members(L, wl, prec, stream):
+    import numpy as np
+    sims, kinds, ux0s = [], [], []
+    for m in WORKLOADS[wl]:
+        kind, tau = member_geometry(m)
+        cfg = L.lbm_config_default(nx=m["nx"], ny=m["ny"], tau=tau, precision=prec,
+                                   collision=m["collision"], u_in=m["U"], stream=stream)
+        sims.append(L.lbm_create(cfg))
+        kinds.append(kind)
+        ux0s.append(np.where(kind == 0, m["U"], 0.0))
+    return sims, kinds, ux0s
+
+
+def _drain(L, sim, call):
+    """Run a data-returning call; a lattice that went non-finite still returns
+    its data (the status is reported separately)."""
+    try:
+        return call()
+    except L.LbmError as ex:
+        if ex.status != 5:
+            raise
+        return call()
 
 
 def run_ours(args):
@@ -228,101 +267,114 @@ def run_ours(args):
     ge.build()
     import paper_2506_05293_gb300 as L
 
-    prec = args.precision
-    wl = args.workload
-    g = workload_geometry(wl)
-    nx, ny = g["nx"], g["ny"]
-    cells = nx * ny
+    prec, wl = args.precision, args.workload
+    nodes = workload_nodes(wl)
+    bpn = BYTES_PER_NODE[prec]
+    working_set = bpn * nodes          # two population buffers of bpn / 2 bytes per node
+    flush_mode = working_set < L2_BYTES
     stream = torch.cuda.Stream()
-    fl = g["kind"] == 0
-    ux0 = np.where(fl, g["U"], 0.0)
-    cfg = L.lbm_config_default(nx=nx, ny=ny, tau=g["tau"], precision=prec,
-                               collision=g["collision"], u_in=g["U"], stream=stream.cuda_stream)
-    sim = L.lbm_create(cfg)
-    L.lbm_set_geometry(sim, g["kind"])
-    L.lbm_init_equilibrium(sim, None, ux0, None)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sims, kinds, ux0s = _make_members(L, wl, prec, stream.cuda_stream)
+    for s, kind, ux0 in zip(sims, kinds, ux0s):
+        L.lbm_set_geometry(s, kind)
+        L.lbm_init_equilibrium(s, None, ux0, None)
+    batch = L.lbm_batch_create(sims)
+    flush_bytes = 256 * 1024 * 1024 if flush_mode else 0
     if args.rows:
-        # fixed tiling (reproducible launch sequence for profiling)
-        rows, variant = args.rows, args.variant
-        L.lbm_set_tiling(sim, rows, variant)
+        rows, variant = args.rows, args.variant          # fixed tiling (profiling)
+        L.lbm_batch_set_tiling(batch, rows, variant)
     else:
-        # project autotuner: fastest tiling for this lattice with a cold L2 per step
-        rows, variant, _ = L.lbm_autotune(sim, steps=20, flush_bytes=256 * 1024 * 1024)
+        rows, variant, _ = L.lbm_batch_autotune(batch, steps=10, flush_bytes=flush_bytes)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda") if flush_mode else None
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            L.lbm_step(sim, 1)
-            flush.fill_(1.0)
-        L.lbm_sync(sim)
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            L.lbm_batch_step(batch, 1)
+            if flush is not None:
+                flush.fill_(1.0)
+        torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
             wall0 = time.perf_counter()
-            for k in range(args.steps):
-                starts[k].record(stream)
-                L.lbm_step(sim, 1)
-                ends[k].record(stream)
-                flush.fill_(float(k))
-            torch.cuda.synchronize()
+            if flush_mode:
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
+                for k in range(args.steps):
+                    ev[k][0].record(stream)
+                    L.lbm_batch_step(batch, 1)
+                    ev[k][1].record(stream)
+                    flush.fill_(float(k))
+                torch.cuda.synchronize()
+                total_ms = sum(a.elapsed_time(b) for a, b in ev)
+            else:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                L.lbm_batch_step(batch, args.steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                total_ms = e0.elapsed_time(e1)
             wall = time.perf_counter() - wall0
         if world > 1:
             torch.distributed.barrier()
-        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        L.lbm_sync(sim)
-        # steady stepping without flushes (CUDA-graph chunks), for context
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        n_hot = 640
-        t0.record(stream)
-        L.lbm_step(sim, n_hot)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        hot_glups = cells * n_hot / (t0.elapsed_time(t1) * 1e-3) / 1e9
-        L.lbm_sync(sim)
+    # lattices that went non-finite (the work per node is the same either way)
+    diverged = []
+    for m, s in zip(WORKLOADS[wl], sims):
+        try:
+            L.lbm_sync(s)
+        except L.LbmError as ex:
+            if ex.status != 5:
+                raise
+            diverged.append(f"{m['nx']}x{m['ny']} Re{m['Re']} {m['collision']}")
 
-    total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * cells * args.steps / (total_ms * 1e-3) / 1e9
+    value = world * nodes * args.steps / (total_ms * 1e-3) / 1e9
     ms_per_step = total_ms / args.steps
+    L.lbm_batch_destroy(batch)
+    for s in sims:
+        L.lbm_destroy(s)
 
-    # end to end through the C ABI with host buffers: geometry + initial
-    # fields in, 1000 steps, force series and fields out
+    # end to end through the C ABI with host buffers: per lattice, geometry and
+    # initial fields in from pinned host memory; 1000 steps of the batch; force
+    # series and fields out
     e2e_steps = 1000
-    pinned = {k: torch.empty((ny, nx), dtype=torch.float64, pin_memory=True).numpy()
-              for k in ("rho", "ux", "uy", "orho", "oux", "ouy")}
-    kind_p = torch.empty((ny, nx), dtype=torch.uint8, pin_memory=True).numpy()
-    kind_p[:] = g["kind"]
-    pinned["rho"][:] = 1.0
-    pinned["ux"][:] = ux0
-    pinned["uy"][:] = 0.0
-    sim2 = L.lbm_create(cfg)
-    L.lbm_set_tiling(sim2, rows, variant)
+    sims2, kinds2, ux02 = _make_members(L, wl, prec, stream.cuda_stream)
+    pinned_in = []
+    for kind, ux0 in zip(kinds2, ux02):
+        k_p = torch.empty(kind.shape, dtype=torch.uint8, pin_memory=True).numpy()
+        k_p[:] = kind
+        r_p = torch.ones(kind.shape, dtype=torch.float64, pin_memory=True).numpy()
+        u_p = torch.empty(kind.shape, dtype=torch.float64, pin_memory=True).numpy()
+        u_p[:] = ux0
+        v_p = torch.zeros(kind.shape, dtype=torch.float64, pin_memory=True).numpy()
+        pinned_in.append((k_p, r_p, u_p, v_p))
     torch.cuda.synchronize()
+    h2d = d2h = 0
     w0 = time.perf_counter()
-    L.lbm_set_geometry(sim2, kind_p)
-    L.lbm_init_equilibrium(sim2, pinned["rho"], pinned["ux"], pinned["uy"])
-    L.lbm_step(sim2, e2e_steps)
-    fx, fy = L.lbm_forces(sim2)
-    r_, u_, v_ = L.lbm_fields(sim2)
+    for s, (k_p, r_p, u_p, v_p) in zip(sims2, pinned_in):
+        L.lbm_set_geometry(s, k_p)
+        L.lbm_init_equilibrium(s, r_p, u_p, v_p)
+        h2d += k_p.nbytes + r_p.nbytes + u_p.nbytes + v_p.nbytes
+    batch2 = L.lbm_batch_create(sims2)
+    L.lbm_batch_set_tiling(batch2, rows, variant)
+    L.lbm_batch_step(batch2, e2e_steps)
+    for s in sims2:
+        fx, fy = _drain(L, s, lambda: L.lbm_forces(s))
+        r_, u_, v_ = _drain(L, s, lambda: L.lbm_fields(s))
+        d2h += fx.nbytes + fy.nbytes + r_.nbytes + u_.nbytes + v_.nbytes
     e2e_s = time.perf_counter() - w0
-    L.lbm_destroy(sim2)
-    e2e_value = world * cells * e2e_steps / e2e_s / 1e9
-    h2d = (kind_p.nbytes + 3 * pinned["rho"].nbytes) / e2e_steps
-    d2h = (fx.nbytes + fy.nbytes + r_.nbytes + u_.nbytes + v_.nbytes) / e2e_steps
+    L.lbm_batch_destroy(batch2)
+    for s in sims2:
+        L.lbm_destroy(s)
+    e2e_value = world * nodes * e2e_steps / e2e_s / 1e9
 
     peak, peak_kind = measured_peaks()
-    bpn = BYTES_PER_NODE[prec]
-    kernel_ms = statistics.mean(step_ms)
-    achieved = bpn * cells / (kernel_ms * 1e-3) / 1e9
+    achieved = bpn * nodes / (ms_per_step * 1e-3) / 1e9
     traffic = step_kernel_traffic(prec, wl)
-    L.lbm_destroy(sim)
 
     if rank != 0:
         if world > 1:
@@ -330,34 +382,36 @@ def run_ours(args):
         return 0
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        n_cpu = args.cpu_steps
-        glups_cpu, dt_cpu, _ = cpu_oracle_sample(wl, n_cpu)
+        glups_cpu, dt_cpu, _, _ = cpu_oracle_sample(wl, args.cpu_steps)
         cpu = {"value": glups_cpu, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{n_cpu} time steps of {wl} ({dt_cpu:.1f} s), numpy FP64, 1 thread"}
-    clocks = clk.summary()
+               "sample": f"{args.cpu_steps} oracle time steps, one member lattice of {wl} per "
+                         f"step, round robin ({dt_cpu:.1f} s), numpy FP64, 1 thread"}
     line = {
         "metric": "GLUPS", "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64",
-                                                          "fp16dev": "f16"}[prec],
-        "data": "synthetic",
-        "config": {"workload": wl, "nx": nx, "ny": ny, "nodes": cells, "collision": g["collision"],
-                   "Re": WORKLOADS[wl][3], "outflow": "zouhe", "storage": prec,
-                   "l2": "flushed between timed steps (256 MB device write); each step timed "
-                         "alone with CUDA events",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16"}[prec], "data": "synthetic",
+        "config": {"workload": wl, "lattices": len(WORKLOADS[wl]), "nodes": nodes,
+                   "members": [f"{m['nx']}x{m['ny']} Re{m['Re']} {m['collision']}"
+                               for m in WORKLOADS[wl]],
+                   "outflow": "zouhe", "storage": prec, "working_set_bytes": working_set,
+                   "l2": ("flushed before each timed step (256 MB device write), steps timed one "
+                          "by one") if flush_mode else
+                         "working set larger than L2: no flush, steps back to back",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "tiling": {"rows": rows, "variant": variant},
-                   "hot_l2_resident_glups": hot_glups, "wall_s": wall},
+                   "tiling": {"rows": rows, "variant": variant}, "wall_s": wall,
+                   "diverged_during_run": diverged},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "note": f"{bpn} B/node/step algorithmic; peak {peak_kind} hbm_gbs"},
+                     "note": f"{bpn} B/node/step algorithmic x {nodes} nodes per launch; peak "
+                             f"{peak_kind} hbm_gbs"},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h,
-                "note": f"lbm_set_geometry + lbm_init_equilibrium from pinned host, "
-                        f"{e2e_steps} steps, lbm_forces + lbm_fields to host"},
+        "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": h2d / e2e_steps,
+                "d2h_bytes_per_step": d2h / e2e_steps,
+                "note": f"per lattice lbm_set_geometry + lbm_init_equilibrium from pinned host; "
+                        f"{e2e_steps} batch steps; lbm_forces + lbm_fields to host"},
         "gpu_launches": args.steps,
-        "clocks": clocks,
+        "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -368,15 +422,15 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cylinder_D40_L32D_Re100", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cylinder_sweep_D40", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=sorted(BYTES_PER_NODE))
-    ap.add_argument("--cpu-steps", type=int, default=12)
+    ap.add_argument("--cpu-steps", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=0, help="fixed tiling instead of the autotuner")
-    ap.add_argument("--variant", type=int, default=2)
+    ap.add_argument("--variant", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

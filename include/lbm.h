@@ -36,7 +36,8 @@
 extern "C" {
 #endif
 
-typedef struct lbm_sim lbm_sim; /* opaque, owned by the library */
+typedef struct lbm_sim lbm_sim;     /* opaque, owned by the library */
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
 
 typedef enum {
   LBM_OK = 0,
@@ -86,6 +87,8 @@ typedef struct {
   void* stream;             /* cudaStream_t to run on; NULL: the library creates one */
   const lbm_allocator* alloc; /* NULL: cudaMalloc / cudaFree */
   int64_t force_capacity;   /* device ring of per-step forces; 0: 1 << 20 steps */
+  int64_t ramp_steps;       /* > 0: the inlet velocity of step t is u_in min(1, (t+1)/ramp_steps)
+                               (a smooth start; the paper does not state how its runs start) */
 } lbm_config;
 
 /* Fill *cfg with defaults (tau 0.6, BGK, FP32, open x, rho_out 1). */
@@ -179,14 +182,17 @@ lbm_status lbm_mass(lbm_sim* sim, double* mass);
 lbm_status lbm_device_state(lbm_sim* sim, void** base, int64_t* pitch, int64_t* plane);
 
 /* Tiling of the step kernel: rows per strip (1..64; a strip is 128 columns)
- * and register-budget variant (0..2: at least 6, 8 or 10 resident blocks of
- * 128 threads per SM).  Populations do not depend on the tiling; the FP64
- * force sum may differ in its last bits (partial sums change order). */
+ * and variant: 0..2 = the register-pipelined kernel on a persistent grid with
+ * at least 6, 8 or 10 resident blocks of 128 threads per SM; 3..4 = the
+ * staged kernel (one block per strip; its rows are copied into a 4- or 6-slot
+ * shared-memory ring by cp.async.bulk and collided from there; rows >= 2).
+ * Populations do not depend on the tiling; the FP64 force sum may differ in
+ * its last bits (partial sums change order). */
 lbm_status lbm_set_tiling(lbm_sim* sim, int32_t rows, int32_t variant);
 lbm_status lbm_get_tiling(lbm_sim* sim, int32_t* rows, int32_t* variant);
 
 /* Autotuner: time `steps` (1..10000) single steps of every candidate tiling
- * (rows 2, 4, 8, 16, 32 x the three variants) with CUDA events on the sim's
+ * (rows 2, 4, 8, 16, 32 x the five variants) with CUDA events on the sim's
  * stream and keep the fastest; *best_ms (nullable) gets its mean step time.
  * With flush_bytes > 0 a scratch buffer of that size is written before each
  * timed step so the step starts from a cold L2.  The populations, step
@@ -221,6 +227,30 @@ lbm_status lbm_autotune(lbm_sim* sim, int32_t steps, int64_t flush_bytes, float*
  * must be ordered by the caller. */
 lbm_status lbm_step_noalloc(const lbm_config* cfg, const float* src, float* dst,
                             const uint8_t* kind, int64_t pitch, int64_t t, double* force);
+
+/* Batches.  A batch advances several sims -- of any sizes, relaxation times,
+ * collision operators, inlet velocities and outflows -- by one kernel launch
+ * per time step (plus one east-column launch per NN-outflow member), the
+ * launch table listing every member's strips; chunks of 32 steps replay from
+ * CUDA graphs.  Members must share one precision and one stream
+ * (lbm_config.stream) and be at the same step (for instance all freshly
+ * initialised); the batch keeps them in lockstep.  Members remain ordinary
+ * sims for every other call (lbm_forces, lbm_fields, ...); stepping a member
+ * alone breaks the lockstep, after which lbm_batch_step reports
+ * LBM_ERR_STATE.  Destroy batches before their members.  The batch allocates
+ * its own launch table and force partials.  sims is a host array of n >= 1
+ * distinct sims (copied). */
+lbm_status lbm_batch_create(lbm_sim* const* sims, int32_t n, lbm_batch** out);
+lbm_status lbm_batch_destroy(lbm_batch* batch);
+lbm_status lbm_batch_step(lbm_batch* batch, int64_t n);
+/* Wait for the stream; report the first latched device fault of any member. */
+lbm_status lbm_batch_sync(lbm_batch* batch);
+/* Tiling and autotuner of the batch launch, as lbm_set_tiling / lbm_autotune
+ * (in a batch every variant launches one block per strip). */
+lbm_status lbm_batch_set_tiling(lbm_batch* batch, int32_t rows, int32_t variant);
+lbm_status lbm_batch_get_tiling(lbm_batch* batch, int32_t* rows, int32_t* variant);
+lbm_status lbm_batch_autotune(lbm_batch* batch, int32_t steps, int64_t flush_bytes,
+                              float* best_ms);
 
 /* Strouhal number of a lift series (Sec. 2.3): St = f D / U with f the peak of
  * |DFT| of the last 2^m samples (largest power of two <= n, n >= 8), mean

@@ -272,6 +272,7 @@ class Config:
     mrt_rates: Optional[np.ndarray] = None  # None -> mrt_default_rates(tau)
     x_periodic: bool = False               # True: no open boundaries at all
     u_in: float = 0.0                      # inlet velocity (Zou & He, west)
+    u_ramp_steps: int = 0                  # > 0: inlet velocity u_in min(1, (t+1)/ramp)
     v_pert_amp: float = 0.0                # amplitude of the seeded inlet v
     seed: int = 0
     rho_out: float = 1.0
@@ -329,7 +330,10 @@ class Solver:
             # inlet (column 0): Zou & He velocity with the seeded perturbation
             v = np.asarray(_rng.inlet_perturbation(cfg.seed, self.t, cfg.ny,
                                                    cfg.v_pert_amp))
-            col = zouhe_velocity_west(g[:, :, 0], cfg.u_in, v)
+            u = cfg.u_in
+            if cfg.u_ramp_steps > 0:
+                u = cfg.u_in * min(1.0, (self.t + 1) / cfg.u_ramp_steps)
+            col = zouhe_velocity_west(g[:, :, 0], u, v)
             m = fluid[:, 0]
             g[:, m, 0] = col[:, m]
             # outflow (column nx-1)

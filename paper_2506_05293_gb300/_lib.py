@@ -31,7 +31,7 @@ class LbmConfig(Structure):
                 ("mrt_rates", c_double * 9), ("precision", c_int32), ("x_periodic", c_int32),
                 ("u_in", c_double), ("v_pert_amp", c_double), ("seed", c_uint64),
                 ("rho_out", c_double), ("stream", c_void_p), ("alloc", POINTER(LbmAllocator)),
-                ("force_capacity", c_int64)]
+                ("force_capacity", c_int64), ("ramp_steps", c_int64)]
 
 
 class LbmMlp(Structure):
@@ -66,6 +66,13 @@ SIGNATURES = {
     "lbm_autotune": (c_int, [c_void_p, c_int32, c_int64, POINTER(c_float)]),
     "lbm_step_noalloc": (c_int, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_int64,
                                  c_int64, c_void_p]),
+    "lbm_batch_create": (c_int, [POINTER(c_void_p), c_int32, POINTER(c_void_p)]),
+    "lbm_batch_destroy": (c_int, [c_void_p]),
+    "lbm_batch_step": (c_int, [c_void_p, c_int64]),
+    "lbm_batch_sync": (c_int, [c_void_p]),
+    "lbm_batch_set_tiling": (c_int, [c_void_p, c_int32, c_int32]),
+    "lbm_batch_get_tiling": (c_int, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
+    "lbm_batch_autotune": (c_int, [c_void_p, c_int32, c_int64, POINTER(c_float)]),
     "lbm_strouhal": (c_int, [POINTER(c_double), c_int64, c_double, c_double, POINTER(c_double)]),
     "lbm_last_error": (c_char_p, []),
     "lbm_version": (c_char_p, []),

@@ -232,6 +232,62 @@ def lbm_step_noalloc(cfg, src_ptr, dst_ptr, kind_ptr, pitch, t, force_ptr):
                                         c_void_p(force_ptr)))
 
 
+class Batch:
+    """Handle of a batch created by lbm_batch_create (keeps its members alive)."""
+
+    def __init__(self, handle, sims):
+        self.handle = handle
+        self.sims = list(sims)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _lib.load().lbm_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def lbm_batch_create(sims):
+    arr = (c_void_p * len(sims))(*[s.handle.value if isinstance(s.handle, c_void_p) else s.handle
+                                   for s in sims])
+    h = c_void_p()
+    _check(_lib.load().lbm_batch_create(arr, len(sims), byref(h)))
+    return Batch(h, sims)
+
+
+def lbm_batch_destroy(batch):
+    if batch.handle:
+        _check(_lib.load().lbm_batch_destroy(batch.handle))
+        batch.handle = None
+
+
+def lbm_batch_step(batch, n=1):
+    _check(_lib.load().lbm_batch_step(batch.handle, int(n)))
+
+
+def lbm_batch_sync(batch):
+    _check(_lib.load().lbm_batch_sync(batch.handle))
+
+
+def lbm_batch_set_tiling(batch, rows, variant):
+    _check(_lib.load().lbm_batch_set_tiling(batch.handle, int(rows), int(variant)))
+
+
+def lbm_batch_get_tiling(batch):
+    r = ctypes.c_int32()
+    v = ctypes.c_int32()
+    _check(_lib.load().lbm_batch_get_tiling(batch.handle, byref(r), byref(v)))
+    return r.value, v.value
+
+
+def lbm_batch_autotune(batch, steps=20, flush_bytes=0):
+    ms = c_float()
+    _check(_lib.load().lbm_batch_autotune(batch.handle, int(steps), int(flush_bytes), byref(ms)))
+    r, v = lbm_batch_get_tiling(batch)
+    return r, v, ms.value
+
+
 def lbm_strouhal(cl, length, u):
     cl = np.ascontiguousarray(cl, dtype=np.float64)
     st = c_double()

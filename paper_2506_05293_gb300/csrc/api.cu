@@ -16,20 +16,14 @@
 
 namespace {
 
+using lbm::CudaError;
+using lbm::ck;
+
 thread_local std::string g_err;
 
 lbm_status fail(lbm_status s, const std::string& msg) {
   g_err = msg;
   return s;
-}
-
-struct CudaError {
-  cudaError_t e;
-  const char* what;
-};
-
-inline void ck(cudaError_t e, const char* what) {
-  if (e != cudaSuccess) throw CudaError{e, what};
 }
 
 lbm_status from_cuda(const CudaError& ce) {
@@ -45,177 +39,21 @@ lbm_status from_cuda(const CudaError& ce) {
   catch (const std::bad_alloc&) { return fail(LBM_ERR_OOM, "host allocation failed"); } \
   catch (const std::exception& ex) { return fail(LBM_ERR_CUDA, ex.what()); }
 
-constexpr int64_t kGraphChunk = 32;   // steps per captured graph (even)
 constexpr int64_t kDefaultRing = int64_t(1) << 20;
 
 void* dev_alloc(lbm_sim* s, size_t bytes) {
-  void* p = nullptr;
-  if (bytes == 0) bytes = 16;
-  if (s->have_alloc) {
-    p = s->alloc.alloc(bytes, s->alloc.ctx);
-    if (!p) throw CudaError{cudaErrorMemoryAllocation, "injected allocator"};
-  } else {
-    ck(cudaMalloc(&p, bytes), "cudaMalloc");
-  }
+  void* p = lbm::dev_alloc_raw(s->have_alloc ? &s->alloc : nullptr, bytes);
   s->owned.push_back(p);
   return p;
 }
 
 void release_all(lbm_sim* s) {
-  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
-  s->graphs.clear();
+  lbm::group_release(s->own);
   if (s->stream) cudaStreamSynchronize(s->stream);
-  for (void* p : s->owned) {
-    if (s->have_alloc) s->alloc.free(p, s->alloc.ctx);
-    else cudaFree(p);
-  }
+  for (void* p : s->owned) lbm::dev_free_raw(s->have_alloc ? &s->alloc : nullptr, p);
   s->owned.clear();
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   s->stream = nullptr;
-}
-
-void clear_graphs(lbm_sim* s) {
-  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
-  s->graphs.clear();
-}
-
-void mrt_rates(const lbm_sim* s, double& se, double& seps, double& sq, double& snu) {
-  const double* r = s->cfg.mrt_rates;
-  bool any = false;
-  for (int k = 0; k < 9; ++k) any |= r[k] != 0.0;
-  if (!any) {
-    se = seps = sq = 1.0;
-    snu = 1.0 / s->cfg.tau;
-    return;
-  }
-  se = r[1];
-  seps = r[2];
-  sq = r[4];
-  snu = r[7] != 0.0 ? r[7] : 1.0 / s->cfg.tau;
-}
-
-lbm::StepParams step_params(lbm_sim* s, int src_idx) {
-  lbm::StepParams p{};
-  p.src = s->buf[src_idx];
-  p.dst = s->buf[1 - src_idx];
-  p.nx = s->nx;
-  p.ny = s->ny;
-  p.pitch = s->pitch;
-  p.plane = s->plane;
-  p.solid_bits = s->solid_bits;
-  p.words_per_row = s->words_per_row;
-  p.links = s->links;
-  p.omega = 1.0 / s->cfg.tau;
-  mrt_rates(s, p.mrt_se, p.mrt_seps, p.mrt_sq, p.mrt_snu);
-  p.u_in = s->cfg.u_in;
-  p.v_amp = s->cfg.v_pert_amp;
-  p.rho_out = s->rho_out;
-  p.omega_f = (float)p.omega;
-  p.mrt_f[0] = (float)p.mrt_se;
-  p.mrt_f[1] = (float)p.mrt_seps;
-  p.mrt_f[2] = (float)p.mrt_sq;
-  p.mrt_f[3] = (float)p.mrt_snu;
-  p.u_in_f = (float)p.u_in;
-  p.rho_out_f = (float)p.rho_out;
-  p.seed = s->cfg.seed;
-  p.east_mode = s->east;
-  p.x_periodic = s->cfg.x_periodic;
-  p.rows = s->rows;
-  p.partials = s->partials;
-  p.partial_stride = s->partial_stride;
-  p.ring = s->ring;
-  p.ring_cap = s->ring_cap;
-  p.status = s->status;
-  return p;
-}
-
-int step_block_count(const lbm_sim* s) {
-  return lbm::step_blocks(s->nx, s->ny, s->rows, s->max_blocks_v[s->variant]);
-}
-
-// Sum the force partials of the last executed step into the ring, if that
-// has not happened yet (the next step's reducer block normally does it).
-void finalize_force(lbm_sim* s) {
-  if (!s->pending) return;
-  lbm::StepParams p = step_params(s, s->cur);
-  lbm::launch_finalize_force(p, s->t_host - 1, s->last_blocks, s->stream);
-  ck(cudaGetLastError(), "finalize launch");
-  s->pending = false;
-}
-
-// Enqueue one time step from buf[src_idx] to buf[1 - src_idx].  graph_k < 0:
-// a direct launch for step t_host; graph_k >= 0: step k of a captured chunk,
-// whose step index is read from t_base on the device.
-void enqueue_step(lbm_sim* s, int src_idx, int graph_k = -1) {
-  lbm::StepParams p = step_params(s, src_idx);
-  const int blocks = step_block_count(s);
-  if (graph_k < 0) {
-    p.t = s->t_host;
-    p.t_base = nullptr;
-    p.reduce_prev = s->pending ? 1 : 0;
-    p.prev_blocks = s->last_blocks;
-  } else {
-    p.t = 0;
-    p.t_base = s->t_base;
-    p.t_offset = graph_k;
-    p.reduce_prev = graph_k > 0 ? 1 : 0;
-    p.prev_blocks = blocks;
-  }
-  lbm::launch_step(s->prec, s->cfg.collision, p, s->variant, blocks, s->stream);
-  if (s->east == lbm::EAST_EXTERNAL && s->outflow == LBM_OUTFLOW_NN) {
-    lbm::NnParams q{};
-    q.src = p.src;
-    q.dst = p.dst;
-    q.nx = s->nx;
-    q.ny = s->ny;
-    q.pitch = s->pitch;
-    q.plane = s->plane;
-    q.solid_bits = s->solid_bits;
-    q.words_per_row = s->words_per_row;
-    q.net = s->prec == LBM_FP64 ? (const void*)s->nn.params_d : (const void*)s->nn.params_f;
-    q.n_layers = s->nn.n_layers;
-    for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) q.sizes[l] = s->nn.sizes[l];
-    q.act = s->nn.act;
-    q.out_scale = s->nn.out_scale;
-    q.rho_out = s->rho_out;
-    q.fallback_drho = s->nn_drho;
-    q.omega = p.omega;
-    q.mrt_se = p.mrt_se;
-    q.mrt_seps = p.mrt_seps;
-    q.mrt_sq = p.mrt_sq;
-    q.mrt_snu = p.mrt_snu;
-    q.collision = s->cfg.collision;
-    q.fallbacks = s->nn_fallbacks;
-    q.status = s->status;
-    lbm::launch_nn_outflow(s->prec, q, s->stream);
-  }
-  ck(cudaGetLastError(), "step launch");
-}
-
-cudaGraphExec_t chunk_graph(lbm_sim* s, int64_t len) {
-  const int64_t key = len * 2 + s->cur;
-  auto it = s->graphs.find(key);
-  if (it != s->graphs.end()) return it->second;
-  cudaGraph_t g = nullptr;
-  ck(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-  int idx = s->cur;
-  try {
-    for (int64_t k = 0; k < len; ++k) {
-      enqueue_step(s, idx, (int)k);
-      idx = 1 - idx;
-    }
-  } catch (...) {
-    cudaStreamEndCapture(s->stream, &g);
-    if (g) cudaGraphDestroy(g);
-    throw;
-  }
-  ck(cudaStreamEndCapture(s->stream, &g), "end capture");
-  cudaGraphExec_t ex = nullptr;
-  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
-  cudaGraphDestroy(g);
-  ck(e, "graph instantiate");
-  s->graphs[key] = ex;
-  return ex;
 }
 
 lbm_status check_sim(lbm_sim* s) {
@@ -229,6 +67,8 @@ lbm_status read_status(lbm_sim* s) {
   ck(cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream),
      "status copy");
   ck(cudaStreamSynchronize(s->stream), "stream sync");
+  if (st & lbm::DEV_TIMEOUT)
+    return fail(LBM_ERR_TIMEOUT, "a bounded device wait gave up (bulk-copy pipeline)");
   if (st & lbm::DEV_NONFINITE)
     return fail(LBM_ERR_NONFINITE, "non-finite density on the device (the run diverged)");
   return LBM_OK;
@@ -299,6 +139,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   if (!(std::fabs(cfg->u_in) < 1.0)) return fail(LBM_ERR_ARG, "|u_in| must be < 1");
   if (!(cfg->rho_out > 0.0)) return fail(LBM_ERR_ARG, "rho_out must be > 0");
   if (cfg->force_capacity < 0) return fail(LBM_ERR_ARG, "force_capacity must be >= 0");
+  if (cfg->ramp_steps < 0) return fail(LBM_ERR_ARG, "ramp_steps must be >= 0");
   if (cfg->alloc && (!cfg->alloc->alloc || !cfg->alloc->free))
     return fail(LBM_ERR_ARG, "allocator needs both alloc and free");
   for (int k = 0; k < 9; ++k)
@@ -327,35 +168,23 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
     ck(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking), "cudaStreamCreate");
     s->own_stream = true;
   }
-  const size_t bytes = (size_t)9 * s->plane * s->elem;
+  // + slack: the staged kernel copies whole 16-byte aligned row segments that
+  // may run up to 128 + 8 elements past the last row of the last population
+  const size_t bytes = ((size_t)9 * s->plane + 256) * s->elem;
   s->buf[0] = dev_alloc(s, bytes);
   s->buf[1] = dev_alloc(s, bytes);
   const int64_t cells = (int64_t)s->nx * s->ny;
   s->kind = (uint8_t*)dev_alloc(s, cells);
-  s->words_per_row = (s->nx + 31) / 32;
+  s->words_per_row = (s->nx + 127) / 128 * 4;   // whole 16-byte groups per row
   s->solid_bits = (uint32_t*)dev_alloc(s, (size_t)s->words_per_row * s->ny * 4);
   s->links = (uint8_t*)dev_alloc(s, cells);
-  int most = 0;
-  for (int v = 0; v < lbm::step_variants(); ++v) {
-    s->max_blocks_v[v] = lbm::step_max_blocks(s->prec, s->cfg.collision, v);
-    if (s->max_blocks_v[v] <= 0) throw CudaError{cudaGetLastError(), "occupancy query"};
-    most = std::max(most, s->max_blocks_v[v]);
-  }
-  // force partials: two parities x one per resident block x (Fx, Fy); the
-  // mass reduction reuses them and needs ny
-  s->partial_stride = most;
-  s->n_partials = std::max<int64_t>((int64_t)4 * most, s->ny);
-  s->partials = (double*)dev_alloc(s, (size_t)s->n_partials * sizeof(double));
-  s->t_base = (int64_t*)dev_alloc(s, sizeof(int64_t));
   s->ring_cap = cfg->force_capacity > 0 ? cfg->force_capacity : kDefaultRing;
   s->ring = (double*)dev_alloc(s, (size_t)2 * s->ring_cap * sizeof(double));
   s->status = (int*)dev_alloc(s, sizeof(int));
   s->scratch_fields = (double*)dev_alloc(s, (size_t)9 * cells * sizeof(double));
-  s->mass_out = (double*)dev_alloc(s, sizeof(double));
+  s->scratch_sums = (double*)dev_alloc(s, ((size_t)s->ny + 1) * sizeof(double));
   s->nn_fallbacks = (unsigned long long*)dev_alloc(s, sizeof(unsigned long long));
   ck(cudaMemsetAsync(s->kind, 0, cells, s->stream), "memset");
-  ck(cudaMemsetAsync(s->t_base, 0, sizeof(int64_t), s->stream), "memset");
-  ck(cudaMemsetAsync(s->partials, 0, (size_t)s->n_partials * sizeof(double), s->stream), "memset");
   ck(cudaMemsetAsync(s->status, 0, sizeof(int), s->stream), "memset");
   ck(cudaMemsetAsync(s->nn_fallbacks, 0, sizeof(unsigned long long), s->stream), "memset");
   ck(cudaMemsetAsync(s->ring, 0, (size_t)2 * s->ring_cap * sizeof(double), s->stream), "memset");
@@ -367,6 +196,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   lbm::launch_init_equilibrium(s->prec, s->buf[0], s->nx, s->ny, s->pitch, s->plane, nullptr,
                                nullptr, nullptr, s->stream);
   ck(cudaGetLastError(), "init launch");
+  lbm::group_init(s->own, std::vector<lbm_sim*>{s}, true);
   ck(cudaStreamSynchronize(s->stream), "create sync");
   *out = s;
   return LBM_OK;
@@ -386,6 +216,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
 
 lbm_status lbm_destroy(lbm_sim* s) {
   if (!s) return LBM_OK;
+  if (s->batch_refs > 0) return fail(LBM_ERR_STATE, "destroy the batches holding this sim first");
   release_all(s);
   delete s;
   return LBM_OK;
@@ -403,13 +234,14 @@ lbm_status lbm_set_geometry(lbm_sim* s, const uint8_t* kind) {
                             s->words_per_row, s->links, s->stream);
   ck(cudaGetLastError(), "geometry launch");
   ck(cudaStreamSynchronize(s->stream), "geometry sync");
-  clear_graphs(s);
+  s->version++;
   return LBM_OK;
   LBM_GUARD_END
 }
 
 static void reset_counters(lbm_sim* s) {
-  s->pending = false;
+  lbm::sim_settle(s);
+  s->last_group = nullptr;
   ck(cudaMemsetAsync(s->status, 0, sizeof(int), s->stream), "memset");
   ck(cudaMemsetAsync(s->nn_fallbacks, 0, sizeof(unsigned long long), s->stream), "memset");
   s->t_host = 0;
@@ -453,7 +285,7 @@ lbm_status lbm_set_outflow_zouhe(lbm_sim* s, double rho_out) {
   s->rho_out = rho_out;
   s->east = lbm::EAST_ZOUHE;
   s->outflow = LBM_OUTFLOW_ZOUHE;
-  clear_graphs(s);
+  s->version++;
   return LBM_OK;
 }
 
@@ -505,7 +337,7 @@ lbm_status lbm_set_outflow_nn(lbm_sim* s, const lbm_mlp* net, double fallback_dr
   s->nn_drho = fallback_drho;
   s->east = lbm::EAST_EXTERNAL;
   s->outflow = LBM_OUTFLOW_NN;
-  clear_graphs(s);
+  s->version++;
   return LBM_OK;
   LBM_GUARD_END
 }
@@ -526,27 +358,7 @@ lbm_status lbm_step(lbm_sim* s, int64_t n) {
   if (lbm_status st = check_sim(s)) return st;
   if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
   LBM_GUARD_BEGIN
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  ck(cudaStreamIsCapturing(s->stream, &cap), "capture query");
-  const bool use_graphs = cap == cudaStreamCaptureStatusNone;
-  while (n > 0) {
-    if (use_graphs && n >= kGraphChunk) {
-      cudaGraphExec_t ex = chunk_graph(s, kGraphChunk);
-      finalize_force(s);
-      lbm::launch_set_t(s->t_base, s->t_host, s->stream);
-      ck(cudaGetLastError(), "set_t launch");
-      ck(cudaGraphLaunch(ex, s->stream), "graph launch");
-      n -= kGraphChunk;
-      s->t_host += kGraphChunk;
-    } else {
-      enqueue_step(s, s->cur);
-      s->cur = 1 - s->cur;
-      n -= 1;
-      s->t_host += 1;
-    }
-    s->pending = true;
-    s->last_blocks = step_block_count(s);
-  }
+  lbm::group_step(s->own, n);
   return LBM_OK;
   LBM_GUARD_END
 }
@@ -554,7 +366,7 @@ lbm_status lbm_step(lbm_sim* s, int64_t n) {
 lbm_status lbm_sync(lbm_sim* s) {
   if (lbm_status st = check_sim(s)) return st;
   LBM_GUARD_BEGIN
-  finalize_force(s);
+  lbm::sim_settle(s);
   return read_status(s);
   LBM_GUARD_END
 }
@@ -572,7 +384,7 @@ lbm_status lbm_forces(lbm_sim* s, double* fx, double* fy, int64_t cap, int64_t* 
     return fail(LBM_ERR_ARG, "fx, fy and n_out must be non-NULL and cap >= 0");
   LBM_GUARD_BEGIN
   *n_out = 0;
-  finalize_force(s);
+  lbm::sim_settle(s);
   lbm_status st = read_status(s);
   int64_t avail = s->t_host - s->drained;
   int64_t start = s->drained;
@@ -649,10 +461,10 @@ lbm_status lbm_mass(lbm_sim* s, double* mass) {
   if (lbm_status st = check_sim(s)) return st;
   if (!mass) return fail(LBM_ERR_ARG, "mass is NULL");
   LBM_GUARD_BEGIN
-  lbm::launch_mass(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane, s->partials,
-                   (int)s->n_partials, s->mass_out, s->stream);
+  lbm::launch_mass(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane, s->scratch_sums,
+                   s->ny, s->scratch_sums + s->ny, s->stream);
   ck(cudaGetLastError(), "mass launch");
-  ck(cudaMemcpyAsync(mass, s->mass_out, 8, cudaMemcpyDeviceToHost, s->stream), "copy");
+  ck(cudaMemcpyAsync(mass, s->scratch_sums + s->ny, 8, cudaMemcpyDeviceToHost, s->stream), "copy");
   return read_status(s);
   LBM_GUARD_END
 }
@@ -666,24 +478,28 @@ lbm_status lbm_device_state(lbm_sim* s, void** base, int64_t* pitch, int64_t* pl
   return LBM_OK;
 }
 
-lbm_status lbm_set_tiling(lbm_sim* s, int32_t rows, int32_t variant) {
-  if (lbm_status st = check_sim(s)) return st;
+static lbm_status check_tiling(int32_t rows, int32_t variant) {
   if (rows < 1 || rows > 64) return fail(LBM_ERR_ARG, "rows must be in 1..64");
   if (variant < 0 || variant >= lbm::step_variants()) return fail(LBM_ERR_ARG, "bad variant");
-  LBM_GUARD_BEGIN
-  finalize_force(s);
-  LBM_GUARD_END
-  s->rows = rows;
-  s->variant = variant;
-  clear_graphs(s);
+  if (lbm::step_variant_is_bulk(variant) && rows < 2)
+    return fail(LBM_ERR_ARG, "the staged variants need rows >= 2");
   return LBM_OK;
+}
+
+lbm_status lbm_set_tiling(lbm_sim* s, int32_t rows, int32_t variant) {
+  if (lbm_status st = check_sim(s)) return st;
+  if (lbm_status st = check_tiling(rows, variant)) return st;
+  LBM_GUARD_BEGIN
+  lbm::group_set_tiling(s->own, rows, variant);
+  return LBM_OK;
+  LBM_GUARD_END
 }
 
 lbm_status lbm_get_tiling(lbm_sim* s, int32_t* rows, int32_t* variant) {
   if (lbm_status st = check_sim(s)) return st;
   if (!rows || !variant) return fail(LBM_ERR_ARG, "outputs must be non-NULL");
-  *rows = s->rows;
-  *variant = s->variant;
+  *rows = s->own.rows;
+  *variant = s->own.variant;
   return LBM_OK;
 }
 
@@ -691,89 +507,111 @@ lbm_status lbm_autotune(lbm_sim* s, int32_t steps, int64_t flush_bytes, float* b
   if (lbm_status st = check_sim(s)) return st;
   if (steps < 1 || steps > 10000) return fail(LBM_ERR_ARG, "steps must be in 1..10000");
   if (flush_bytes < 0) return fail(LBM_ERR_ARG, "flush_bytes must be >= 0");
-  void* snap = nullptr;
-  void* flush = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  auto cleanup = [&]() {
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (snap) cudaFree(snap);
-    if (flush) cudaFree(flush);
-  };
+  LBM_GUARD_BEGIN
+  const float ms = lbm::group_autotune(s->own, steps, flush_bytes);
+  if (best_ms) *best_ms = ms;
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+// ---- batches -------------------------------------------------------------------
+lbm_status lbm_batch_create(lbm_sim* const* sims, int32_t n, lbm_batch** out) {
+  if (!sims || !out || n < 1) return fail(LBM_ERR_ARG, "sims and out must be non-NULL, n >= 1");
+  *out = nullptr;
+  for (int32_t k = 0; k < n; ++k) {
+    if (lbm_status st = check_sim(sims[k])) return st;
+    if (sims[k]->prec != sims[0]->prec)
+      return fail(LBM_ERR_ARG, "batch members must share one precision");
+    if (sims[k]->stream != sims[0]->stream)
+      return fail(LBM_ERR_ARG, "batch members must share one stream (lbm_config.stream)");
+    if (sims[k]->t_host != sims[0]->t_host || sims[k]->cur != sims[0]->cur)
+      return fail(LBM_ERR_STATE, "batch members must be at the same step");
+    for (int32_t j = 0; j < k; ++j)
+      if (sims[j] == sims[k]) return fail(LBM_ERR_ARG, "a sim appears twice in the batch");
+  }
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return fail(LBM_ERR_OOM, "host allocation failed");
   try {
-    const size_t bytes = (size_t)9 * s->plane * s->elem;
-    ck(cudaStreamSynchronize(s->stream), "sync");
-    ck(cudaMalloc(&snap, bytes), "autotune snapshot");
-    if (flush_bytes > 0) ck(cudaMalloc(&flush, (size_t)flush_bytes), "autotune flush buffer");
-    ck(cudaEventCreate(&e0), "event");
-    ck(cudaEventCreate(&e1), "event");
-    finalize_force(s);
-    const int cur0 = s->cur;
-    unsigned long long fb0 = 0;
-    int st0 = 0;
-    ck(cudaMemcpyAsync(snap, s->buf[cur0], bytes, cudaMemcpyDeviceToDevice, s->stream), "snapshot");
-    ck(cudaMemcpyAsync(&fb0, s->nn_fallbacks, 8, cudaMemcpyDeviceToHost, s->stream), "snapshot");
-    ck(cudaMemcpyAsync(&st0, s->status, 4, cudaMemcpyDeviceToHost, s->stream), "snapshot");
-    ck(cudaStreamSynchronize(s->stream), "sync");
-    const int64_t t_host0 = s->t_host, drained0 = s->drained;
-    auto restore = [&]() {
-      s->cur = cur0;
-      ck(cudaMemcpyAsync(s->buf[cur0], snap, bytes, cudaMemcpyDeviceToDevice, s->stream), "restore");
-      ck(cudaMemcpyAsync(s->nn_fallbacks, &fb0, 8, cudaMemcpyHostToDevice, s->stream), "restore");
-      ck(cudaMemcpyAsync(s->status, &st0, 4, cudaMemcpyHostToDevice, s->stream), "restore");
-      ck(cudaStreamSynchronize(s->stream), "sync");
-      s->t_host = t_host0;
-      s->drained = drained0;
-      s->pending = false;
-    };
-    const int rows_c[] = {2, 4, 8, 16, 32};
-    float best = 1e30f;
-    int best_rows = s->rows, best_var = s->variant;
-    for (int v = 0; v < lbm::step_variants(); ++v) {
-      for (int r : rows_c) {
-        s->rows = r;
-        s->variant = v;
-        for (int w = 0; w < 2; ++w) {
-          enqueue_step(s, s->cur);
-          s->cur = 1 - s->cur;
-          s->t_host += 1;
-          s->pending = true;
-          s->last_blocks = step_block_count(s);
-        }
-        float total = 0.f;
-        for (int k = 0; k < steps; ++k) {
-          if (flush) ck(cudaMemsetAsync(flush, k & 0xff, (size_t)flush_bytes, s->stream), "flush");
-          ck(cudaEventRecord(e0, s->stream), "event");
-          enqueue_step(s, s->cur);
-          s->cur = 1 - s->cur;
-          s->t_host += 1;
-          s->pending = true;
-          s->last_blocks = step_block_count(s);
-          ck(cudaEventRecord(e1, s->stream), "event");
-          ck(cudaEventSynchronize(e1), "event sync");
-          float ms = 0.f;
-          ck(cudaEventElapsedTime(&ms, e0, e1), "event time");
-          total += ms;
-        }
-        const float mean = total / (float)steps;
-        if (mean < best) {
-          best = mean;
-          best_rows = r;
-          best_var = v;
-        }
-        restore();
-      }
-    }
-    s->rows = best_rows;
-    s->variant = best_var;
-    clear_graphs(s);
-    if (best_ms) *best_ms = best;
-    cleanup();
+    for (int32_t k = 0; k < n; ++k) lbm::sim_settle(sims[k]);
+    lbm::group_init(b->g, std::vector<lbm_sim*>(sims, sims + n), false);
+    b->g.rows = 8;
+    b->g.variant = 1;
+    ck(cudaStreamSynchronize(b->g.stream), "batch sync");
+    for (int32_t k = 0; k < n; ++k) sims[k]->batch_refs++;
+    *out = b;
     return LBM_OK;
   } catch (const CudaError& ce) {
-    cleanup();
+    lbm::group_release(b->g);
+    delete b;
     return from_cuda(ce);
+  } catch (...) {
+    lbm::group_release(b->g);
+    delete b;
+    return fail(LBM_ERR_OOM, "allocation failed");
   }
+}
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return LBM_OK;
+  LBM_GUARD_BEGIN
+  lbm::group_finalize(b->g);
+  for (lbm_sim* s : b->g.sims) s->batch_refs--;
+  lbm::group_release(b->g);
+  delete b;
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
+  if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+  if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
+  for (const lbm_sim* s : b->g.sims)
+    if (s->t_host != b->g.sims[0]->t_host || s->cur != b->g.sims[0]->cur)
+      return fail(LBM_ERR_STATE, "batch members were stepped apart: not in lockstep");
+  LBM_GUARD_BEGIN
+  lbm::group_step(b->g, n);
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b) {
+  if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+  LBM_GUARD_BEGIN
+  lbm::group_finalize(b->g);
+  lbm_status worst = LBM_OK;
+  for (lbm_sim* s : b->g.sims) {
+    const lbm_status st = read_status(s);
+    if (st != LBM_OK && worst == LBM_OK) worst = st;
+  }
+  return worst;
+  LBM_GUARD_END
+}
+
+lbm_status lbm_batch_set_tiling(lbm_batch* b, int32_t rows, int32_t variant) {
+  if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+  if (lbm_status st = check_tiling(rows, variant)) return st;
+  LBM_GUARD_BEGIN
+  lbm::group_set_tiling(b->g, rows, variant);
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+lbm_status lbm_batch_get_tiling(lbm_batch* b, int32_t* rows, int32_t* variant) {
+  if (!b || !rows || !variant) return fail(LBM_ERR_ARG, "arguments must be non-NULL");
+  *rows = b->g.rows;
+  *variant = b->g.variant;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t steps, int64_t flush_bytes, float* best_ms) {
+  if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+  if (steps < 1 || steps > 10000) return fail(LBM_ERR_ARG, "steps must be in 1..10000");
+  if (flush_bytes < 0) return fail(LBM_ERR_ARG, "flush_bytes must be >= 0");
+  LBM_GUARD_BEGIN
+  const float ms = lbm::group_autotune(b->g, steps, flush_bytes);
+  if (best_ms) *best_ms = ms;
+  return LBM_OK;
+  LBM_GUARD_END
 }
 
 lbm_status lbm_strouhal(const double* cl, int64_t n, double length, double u, double* st) {

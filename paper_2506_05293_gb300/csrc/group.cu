@@ -1,0 +1,444 @@
+// Launch groups: the sims that one step launch per time step advances.
+//
+// A group owns the device launch table (one Member per sim, strip layout for
+// the current tiling), the force partials, the step index used by captured
+// graphs, and the CUDA graphs of chunks of steps.  A single lbm_sim is a group
+// of one; lbm_batch is a group of many sims of different sizes and parameters
+// in lockstep.  Every numerical step runs in step.cu / nn.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sim.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr int64_t kGraphChunk = 32;   // steps per captured graph (even)
+
+void fill_member(const lbm_sim* s, Member& m) {
+  memset(&m, 0, sizeof(m));
+  m.buf[0] = s->buf[0];
+  m.buf[1] = s->buf[1];
+  m.nx = s->nx;
+  m.ny = s->ny;
+  m.pitch = (int32_t)s->pitch;
+  m.plane = (int32_t)s->plane;
+  m.solid_bits = s->solid_bits;
+  m.words_per_row = s->words_per_row;
+  m.links = s->links;
+  m.omega = 1.0 / s->cfg.tau;
+  const double* r = s->cfg.mrt_rates;
+  bool any = false;
+  for (int k = 0; k < 9; ++k) any |= r[k] != 0.0;
+  if (any) {
+    m.mrt_se = r[1];
+    m.mrt_seps = r[2];
+    m.mrt_sq = r[4];
+    m.mrt_snu = r[7] != 0.0 ? r[7] : 1.0 / s->cfg.tau;
+  } else {
+    m.mrt_se = m.mrt_seps = m.mrt_sq = 1.0;
+    m.mrt_snu = 1.0 / s->cfg.tau;
+  }
+  m.u_in = s->cfg.u_in;
+  m.v_amp = s->cfg.v_pert_amp;
+  m.rho_out = s->rho_out;
+  m.omega_f = (float)m.omega;
+  m.mrt_f[0] = (float)m.mrt_se;
+  m.mrt_f[1] = (float)m.mrt_seps;
+  m.mrt_f[2] = (float)m.mrt_sq;
+  m.mrt_f[3] = (float)m.mrt_snu;
+  m.u_in_f = (float)m.u_in;
+  m.rho_out_f = (float)m.rho_out;
+  m.seed = s->cfg.seed;
+  m.ramp_steps = s->cfg.ramp_steps;
+  m.east_mode = s->east;
+  m.x_periodic = s->cfg.x_periodic;
+  m.coll = s->cfg.collision;
+  m.tiles_x = (s->nx + 127) / 128;
+  m.ring = s->ring;
+  m.ring_cap = s->ring_cap;
+  m.status = s->status;
+}
+
+bool table_stale(const Group& g) {
+  if (g.built_versions.size() != g.sims.size()) return true;
+  for (size_t k = 0; k < g.sims.size(); ++k)
+    if (g.sims[k]->version != g.built_versions[k]) return true;
+  return false;
+}
+
+// (Re)build the launch table for the current tiling and member state.
+void build_table(Group& g) {
+  const int n = (int)g.sims.size();
+  std::vector<Member> ms((size_t)n);
+  g.persistent = g.single && !step_variant_is_bulk(g.variant);
+  int strip_total = 0;
+  for (int k = 0; k < n; ++k) {
+    fill_member(g.sims[k], ms[(size_t)k]);
+    const int strips = step_strips(g.sims[k]->nx, g.sims[k]->ny, g.rows);
+    ms[(size_t)k].strip_first = strip_total;
+    ms[(size_t)k].strip_count = strips;
+    strip_total += strips;
+  }
+  if (g.persistent) {
+    const int cap = g.max_blocks_v[g.variant];
+    g.blocks = std::min(strip_total, cap);
+    ms[0].part_first = 0;
+    ms[0].part_count = g.blocks;
+  } else {
+    g.blocks = strip_total;
+    for (int k = 0; k < n; ++k) {
+      ms[(size_t)k].part_first = ms[(size_t)k].strip_first;
+      ms[(size_t)k].part_count = ms[(size_t)k].strip_count;
+    }
+    if (n > 1) {
+      std::vector<int32_t> sm((size_t)strip_total);
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < ms[(size_t)k].strip_count; ++j)
+          sm[(size_t)(ms[(size_t)k].strip_first + j)] = k;
+      ck(cudaMemcpyAsync(g.d_strip_member, sm.data(), sm.size() * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, g.stream), "strip table copy");
+    }
+  }
+  if (g.blocks > g.partial_stride) throw CudaError{cudaErrorInvalidValue, "partial table too small"};
+  ck(cudaMemcpyAsync(g.d_members, ms.data(), ms.size() * sizeof(Member), cudaMemcpyHostToDevice,
+                     g.stream), "member table copy");
+  g.h_member0 = ms[0];
+  ck(cudaStreamSynchronize(g.stream), "table sync");
+  g.built_versions.assign((size_t)n, 0);
+  for (int k = 0; k < n; ++k) g.built_versions[(size_t)k] = g.sims[k]->version;
+  group_clear_graphs(g);
+}
+
+StepParams params(const Group& g, int q) {
+  StepParams p{};
+  if (g.sims.size() == 1) p.m0 = g.h_member0;
+  p.members = g.d_members;
+  p.n_members = (int32_t)g.sims.size();
+  p.strip_member = g.d_strip_member;
+  p.rows = g.rows;
+  p.q = q;
+  p.persistent = g.persistent ? 1 : 0;
+  p.partials = g.partials;
+  p.partial_stride = g.partial_stride;
+  return p;
+}
+
+// One step launch with source buffer index q.  graph_k < 0: a direct launch
+// for step index t; graph_k >= 0: step k of a captured chunk (index from
+// t_base on the device).
+void enqueue(Group& g, int q, int64_t t, int graph_k, bool reduce_prev) {
+  StepParams p = params(g, q);
+  if (graph_k < 0) {
+    p.t = t;
+    p.t_base = nullptr;
+  } else {
+    p.t_base = g.t_base;
+    p.t_offset = graph_k;
+  }
+  p.reduce_prev = reduce_prev ? 1 : 0;
+  launch_step(g.prec, g.coll_mode, p, g.variant, g.blocks, g.stream);
+  for (lbm_sim* s : g.sims) {
+    if (s->east == EAST_EXTERNAL && s->outflow == LBM_OUTFLOW_NN) {
+      NnParams n{};
+      n.src = s->buf[q];
+      n.dst = s->buf[1 - q];
+      n.nx = s->nx;
+      n.ny = s->ny;
+      n.pitch = s->pitch;
+      n.plane = s->plane;
+      n.solid_bits = s->solid_bits;
+      n.words_per_row = s->words_per_row;
+      n.net = s->prec == LBM_FP64 ? (const void*)s->nn.params_d : (const void*)s->nn.params_f;
+      n.n_layers = s->nn.n_layers;
+      for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) n.sizes[l] = s->nn.sizes[l];
+      n.act = s->nn.act;
+      n.out_scale = s->nn.out_scale;
+      n.rho_out = s->rho_out;
+      n.fallback_drho = s->nn_drho;
+      Member m;
+      fill_member(s, m);
+      n.omega = m.omega;
+      n.mrt_se = m.mrt_se;
+      n.mrt_seps = m.mrt_seps;
+      n.mrt_sq = m.mrt_sq;
+      n.mrt_snu = m.mrt_snu;
+      n.collision = s->cfg.collision;
+      n.fallbacks = s->nn_fallbacks;
+      n.status = s->status;
+      launch_nn_outflow(s->prec, n, g.stream);
+    }
+  }
+  ck(cudaGetLastError(), "step launch");
+}
+
+cudaGraphExec_t chunk_graph(Group& g, int64_t len, int q0) {
+  const int64_t key = len * 2 + q0;
+  auto it = g.graphs.find(key);
+  if (it != g.graphs.end()) return it->second;
+  cudaGraph_t graph = nullptr;
+  ck(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    for (int64_t k = 0; k < len; ++k) enqueue(g, (int)((q0 + k) & 1), 0, (int)k, k > 0);
+  } catch (...) {
+    cudaStreamEndCapture(g.stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  ck(cudaStreamEndCapture(g.stream, &graph), "end capture");
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+  cudaGraphDestroy(graph);
+  ck(e, "graph instantiate");
+  g.graphs[key] = ex;
+  return ex;
+}
+
+// Members must be in lockstep: same step index and same source buffer.
+void check_lockstep(const Group& g) {
+  for (const lbm_sim* s : g.sims)
+    if (s->t_host != g.sims[0]->t_host || s->cur != g.sims[0]->cur)
+      throw CudaError{cudaErrorInvalidValue, "batch members are not in lockstep"};
+}
+
+void advance_members(Group& g, int64_t n) {
+  for (lbm_sim* s : g.sims) {
+    s->t_host += n;
+    if (n & 1) s->cur = 1 - s->cur;
+    s->last_group = &g;
+  }
+}
+
+}  // namespace
+
+void* dev_alloc_raw(const lbm_allocator* a, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (a) {
+    p = a->alloc(bytes, a->ctx);
+    if (!p) throw CudaError{cudaErrorMemoryAllocation, "injected allocator"};
+  } else {
+    ck(cudaMalloc(&p, bytes), "cudaMalloc");
+  }
+  return p;
+}
+
+void dev_free_raw(const lbm_allocator* a, void* p) {
+  if (!p) return;
+  if (a) a->free(p, a->ctx);
+  else cudaFree(p);
+}
+
+void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single) {
+  g.sims = sims;
+  g.single = single;
+  lbm_sim* s0 = sims[0];
+  g.prec = s0->prec;
+  g.stream = s0->stream;
+  int mode = s0->cfg.collision;
+  for (const lbm_sim* s : sims)
+    if (s->cfg.collision != s0->cfg.collision) mode = 2;
+  g.coll_mode = mode;
+  const lbm_allocator* a = s0->have_alloc ? &s0->alloc : nullptr;
+  int most = 0;
+  for (int v = 0; v < step_variants(); ++v) {
+    g.max_blocks_v[v] = step_max_blocks(g.prec, mode == 2 ? 1 : mode, v);
+    if (g.max_blocks_v[v] <= 0) throw CudaError{cudaGetLastError(), "occupancy query"};
+    most = std::max(most, g.max_blocks_v[v]);
+  }
+  int strips1 = 0;   // strips at one row per strip: the most any tiling launches
+  for (const lbm_sim* s : sims) strips1 += step_strips(s->nx, s->ny, 1);
+  g.partial_stride = std::max(most, strips1);
+  auto alloc = [&](size_t bytes) {
+    void* p = dev_alloc_raw(a, bytes);
+    g.owned.push_back(p);
+    return p;
+  };
+  g.d_members = (Member*)alloc(sizeof(Member) * sims.size());
+  g.d_strip_member = sims.size() > 1 ? (int32_t*)alloc(sizeof(int32_t) * (size_t)strips1) : nullptr;
+  g.partials = (double*)alloc(sizeof(double) * 4 * (size_t)g.partial_stride);
+  g.t_base = (int64_t*)alloc(sizeof(int64_t));
+  ck(cudaMemsetAsync(g.partials, 0, sizeof(double) * 4 * (size_t)g.partial_stride, g.stream),
+     "memset");
+  ck(cudaMemsetAsync(g.t_base, 0, sizeof(int64_t), g.stream), "memset");
+  g.built_versions.clear();
+  g.pending = false;
+}
+
+void group_clear_graphs(Group& g) {
+  for (auto& kv : g.graphs) cudaGraphExecDestroy(kv.second);
+  g.graphs.clear();
+}
+
+void group_release(Group& g) {
+  group_clear_graphs(g);
+  if (g.stream) cudaStreamSynchronize(g.stream);
+  const lbm_allocator* a = (!g.sims.empty() && g.sims[0]->have_alloc) ? &g.sims[0]->alloc : nullptr;
+  for (void* p : g.owned) dev_free_raw(a, p);
+  g.owned.clear();
+  for (lbm_sim* s : g.sims)
+    if (s->last_group == &g) s->last_group = nullptr;
+}
+
+void group_finalize(Group& g) {
+  if (!g.pending) return;
+  StepParams p = params(g, 0);
+  launch_finalize_force(p, g.sims[0]->t_host - 1, g.stream);
+  ck(cudaGetLastError(), "finalize launch");
+  g.pending = false;
+}
+
+void sim_settle(lbm_sim* s) {
+  if (s->last_group) group_finalize(*s->last_group);
+}
+
+void group_step(Group& g, int64_t n) {
+  if (n <= 0) return;
+  check_lockstep(g);
+  // a member last stepped by another group: settle that group's forces first
+  for (lbm_sim* s : g.sims)
+    if (s->last_group && s->last_group != &g) {
+      group_finalize(*s->last_group);
+      g.pending = false;
+    }
+  for (lbm_sim* s : g.sims)
+    if (s->last_group != &g) g.pending = false;
+  if (table_stale(g)) {
+    group_finalize(g);
+    build_table(g);
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  ck(cudaStreamIsCapturing(g.stream, &cap), "capture query");
+  const bool use_graphs = cap == cudaStreamCaptureStatusNone;
+  while (n > 0) {
+    const int q = g.sims[0]->cur;
+    const int64_t t = g.sims[0]->t_host;
+    if (use_graphs && n >= kGraphChunk) {
+      cudaGraphExec_t ex = chunk_graph(g, kGraphChunk, q);
+      group_finalize(g);
+      launch_set_t(g.t_base, t, g.stream);
+      ck(cudaGetLastError(), "set_t launch");
+      ck(cudaGraphLaunch(ex, g.stream), "graph launch");
+      advance_members(g, kGraphChunk);
+      n -= kGraphChunk;
+    } else {
+      enqueue(g, q, t, -1, g.pending);
+      advance_members(g, 1);
+      n -= 1;
+    }
+    g.pending = true;
+  }
+}
+
+void group_set_tiling(Group& g, int rows, int variant) {
+  group_finalize(g);
+  g.rows = rows;
+  g.variant = variant;
+  g.built_versions.clear();   // forces a rebuild at the next step
+  group_clear_graphs(g);
+}
+
+// Time every candidate tiling on the group's own data and keep the fastest;
+// the members' populations, step counters, force series and fallback counts
+// are restored afterwards.
+float group_autotune(Group& g, int steps, int64_t flush_bytes) {
+  for (lbm_sim* s : g.sims) sim_settle(s);
+  check_lockstep(g);
+  ck(cudaStreamSynchronize(g.stream), "sync");
+  const size_t nsims = g.sims.size();
+  std::vector<void*> snaps(nsims, nullptr);
+  void* flush = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (void* p : snaps)
+      if (p) cudaFree(p);
+    if (flush) cudaFree(flush);
+  };
+  try {
+    struct Saved { int cur; int64_t t, drained; unsigned long long fb; int st; lbm::Group* lg; };
+    std::vector<Saved> saved(nsims);
+    for (size_t k = 0; k < nsims; ++k) {
+      lbm_sim* s = g.sims[k];
+      const size_t bytes = ((size_t)9 * s->plane + 256) * s->elem;
+      ck(cudaMalloc(&snaps[k], bytes), "autotune snapshot");
+      ck(cudaMemcpyAsync(snaps[k], s->buf[s->cur], bytes, cudaMemcpyDeviceToDevice, g.stream),
+         "snapshot");
+      saved[k].cur = s->cur;
+      saved[k].t = s->t_host;
+      saved[k].drained = s->drained;
+      saved[k].lg = s->last_group;
+      ck(cudaMemcpyAsync(&saved[k].fb, s->nn_fallbacks, 8, cudaMemcpyDeviceToHost, g.stream), "snap");
+      ck(cudaMemcpyAsync(&saved[k].st, s->status, 4, cudaMemcpyDeviceToHost, g.stream), "snap");
+    }
+    if (flush_bytes > 0) ck(cudaMalloc(&flush, (size_t)flush_bytes), "autotune flush buffer");
+    ck(cudaEventCreate(&e0), "event");
+    ck(cudaEventCreate(&e1), "event");
+    ck(cudaStreamSynchronize(g.stream), "sync");
+    auto restore = [&]() {
+      ck(cudaStreamSynchronize(g.stream), "sync");
+      for (size_t k = 0; k < nsims; ++k) {
+        lbm_sim* s = g.sims[k];
+        const size_t bytes = ((size_t)9 * s->plane + 256) * s->elem;
+        s->cur = saved[k].cur;
+        ck(cudaMemcpyAsync(s->buf[s->cur], snaps[k], bytes, cudaMemcpyDeviceToDevice, g.stream),
+           "restore");
+        ck(cudaMemcpyAsync(s->nn_fallbacks, &saved[k].fb, 8, cudaMemcpyHostToDevice, g.stream),
+           "restore");
+        ck(cudaMemcpyAsync(s->status, &saved[k].st, 4, cudaMemcpyHostToDevice, g.stream), "restore");
+        s->t_host = saved[k].t;
+        s->drained = saved[k].drained;
+        s->last_group = saved[k].lg;
+      }
+      ck(cudaStreamSynchronize(g.stream), "sync");
+      g.pending = false;
+    };
+    const int rows_c[] = {2, 4, 8, 16, 32};
+    float best = 1e30f;
+    int best_rows = g.rows, best_var = g.variant;
+    for (int v = 0; v < step_variants(); ++v) {
+      for (int r : rows_c) {
+        group_set_tiling(g, r, v);
+        build_table(g);
+        for (lbm_sim* s : g.sims) s->last_group = &g;
+        g.pending = false;
+        float total = 0.f;
+        for (int k = 0; k < steps + 2; ++k) {
+          const int q = g.sims[0]->cur;
+          if (flush && k >= 2)
+            ck(cudaMemsetAsync(flush, k & 0xff, (size_t)flush_bytes, g.stream), "flush");
+          ck(cudaEventRecord(e0, g.stream), "event");
+          enqueue(g, q, g.sims[0]->t_host, -1, g.pending);
+          ck(cudaEventRecord(e1, g.stream), "event");
+          advance_members(g, 1);
+          g.pending = true;
+          ck(cudaEventSynchronize(e1), "event sync");
+          float ms = 0.f;
+          ck(cudaEventElapsedTime(&ms, e0, e1), "event time");
+          if (k >= 2) total += ms;   // two untimed warm-up steps
+        }
+        const float mean = total / (float)steps;
+        if (mean < best) {
+          best = mean;
+          best_rows = r;
+          best_var = v;
+        }
+        restore();
+      }
+    }
+    group_set_tiling(g, best_rows, best_var);
+    cleanup();
+    return best;
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+}
+
+}  // namespace lbm

@@ -198,6 +198,12 @@ __device__ __forceinline__ void zouhe_west(R h[9], R u, R v) {
   h[8] = heq[8] + (h[6] - heq[6]) - half_t;
 }
 
+// inlet velocity of step t: u_in, ramped linearly over the first ramp_steps
+__device__ __forceinline__ double inlet_velocity(double u_in, int64_t ramp_steps, int64_t t) {
+  if (ramp_steps <= 0 || t + 1 >= ramp_steps) return u_in;
+  return u_in * ((double)(t + 1) / (double)ramp_steps);
+}
+
 // ---- SplitMix64 (Steele, Lea, Flood 2014), device copy --------------------
 __device__ __forceinline__ uint64_t splitmix64(uint64_t key) {
   uint64_t z = key + 0x9E3779B97F4A7C15ull;

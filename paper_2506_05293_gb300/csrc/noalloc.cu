@@ -44,7 +44,8 @@ struct NoAllocParams {
   int nx, ny, pitch, plane;
   float omega, u_in, rho_out;
   MrtRates<float> mrt;
-  double v_amp;
+  double v_amp, u_in_d;
+  int64_t ramp_steps;
   uint64_t seed;
   int x_periodic, coll;
   int64_t t;
@@ -105,7 +106,9 @@ __global__ void __launch_bounds__(128) noalloc_step_kernel(const NoAllocParams p
       }
       if (west) {
         const float v = (float)inlet_perturbation(p.seed, p.t, y, p.v_amp);
-        zouhe_west<float>(h, p.u_in, v);
+        const float u =
+            p.ramp_steps > 0 ? (float)inlet_velocity(p.u_in_d, p.ramp_steps, p.t) : p.u_in;
+        zouhe_west<float>(h, u, v);
       } else if (east) {
         zouhe_east<float>(h, p.rho_out);
       }
@@ -233,6 +236,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const float* src, 
     p.mrt = {1.f, 1.f, 1.f, (float)(1.0 / cfg->tau)};
   }
   p.v_amp = cfg->v_pert_amp;
+  p.u_in_d = cfg->u_in;
+  p.ramp_steps = cfg->ramp_steps;
   p.seed = cfg->seed;
   p.x_periodic = cfg->x_periodic;
   p.coll = cfg->collision;

@@ -17,35 +17,49 @@ namespace lbm {
 enum EastMode : int { EAST_ZOUHE = 0, EAST_EXTERNAL = 1 };
 
 // Status bits latched on the device.
-enum : int { DEV_NONFINITE = 1 };
+enum : int { DEV_NONFINITE = 1, DEV_TIMEOUT = 2 };
 
-// Parameters of one launch of the fused step kernel.
-struct StepParams {
-  const void* src;        // populations at t (post-collision), storage type S
-  void* dst;              // populations at t+1
-  int32_t nx, ny;
-  int64_t pitch, plane;   // elements
+// One member lattice of a step launch (a simulation, alone or in a batch).
+// Built on the host and kept in device memory; the kernels read it per block.
+struct Member {
+  void* buf[2];           // population buffers (storage type S); source = buf[q]
+  int32_t nx, ny, pitch, plane;   // elements; 9 * plane < 2^31
   const uint32_t* solid_bits;
   int32_t words_per_row;
-  const uint8_t* links;   // per cell: bit i-1 set for a counted link in direction i
-  double omega;
-  double mrt_se, mrt_seps, mrt_sq, mrt_snu;
-  double u_in, v_amp, rho_out;
+  const uint8_t* links;   // per node: bit i-1 set for a counted link in direction i
+  double omega, mrt_se, mrt_seps, mrt_sq, mrt_snu, u_in, v_amp, rho_out;
   float omega_f, mrt_f[4], u_in_f, rho_out_f;   // FP32 copies for the FP32/FP16 kernels
   uint64_t seed;
+  int64_t ramp_steps;     // > 0: inlet velocity u_in min(1, (t+1)/ramp_steps)
   int32_t east_mode;      // EastMode
   int32_t x_periodic;
-  int32_t rows;           // rows per strip (one strip = 128 columns x rows)
-  int64_t t;              // absolute step index of a direct launch
-  const int64_t* t_base;  // graph launches: t = *t_base + t_offset (t_base != NULL)
-  int32_t t_offset;
-  int32_t reduce_prev;    // the reducer block finalises the previous step's force
-  int32_t prev_blocks;    // lattice blocks of the previous launch
-  double* partials;       // [2 parities][partial_stride blocks][2]
-  int32_t partial_stride;
+  int32_t coll;           // lbm_collision
+  int32_t tiles_x;        // 128-column tiles
+  int32_t strip_first;    // first block (strip) of this member in the launch
+  int32_t strip_count;    // strips of this member
+  int32_t part_first;     // force partials of this member: [part_first, +part_count)
+  int32_t part_count;
   double* ring;           // 2 doubles per step
   int64_t ring_cap;
   int* status;
+};
+
+// Parameters of one launch of a step kernel.
+struct StepParams {
+  const Member* members;
+  int32_t n_members;
+  const int32_t* strip_member;   // member of each block (multi-member launches)
+  int32_t rows;                  // rows per strip (one strip = 128 columns x rows)
+  int32_t q;                     // index of the source buffer (members in lockstep)
+  int32_t persistent;            // one member whose strips the blocks stride over
+  int64_t t;                     // step index of a direct launch
+  const int64_t* t_base;         // graph launches: t = *t_base + t_offset
+  int32_t t_offset;
+  int32_t reduce_prev;           // extra blocks finalise the previous step's forces
+  double* partials;              // [2 parities][partial_stride][2]
+  int32_t partial_stride;
+  Member m0;                     // copy of the only member when n_members == 1: the
+                                 // kernels then read it from the parameter bank
 };
 
 // Direct-reconstruction network on the device (FP32 and FP64 copies).
@@ -79,13 +93,15 @@ struct NnParams {
   int* status;
 };
 
-// launches blocks + 1 blocks: the last one finalises the previous step's force
+// launches blocks + n_members blocks: the extra ones finalise the previous
+// step's forces; coll 0 BGK, 1 MRT, 2 per member
 void launch_step(int prec, int coll, const StepParams& p, int variant, int blocks,
                  cudaStream_t s);
-// force of step tt from its block partials (prev_blocks of them) into the ring
-void launch_finalize_force(const StepParams& p, int64_t tt, int blocks, cudaStream_t s);
+// forces of step tt from the block partials into each member's ring
+void launch_finalize_force(const StepParams& p, int64_t tt, cudaStream_t s);
 void launch_set_t(int64_t* t_base, int64_t value, cudaStream_t s);
-int step_blocks(int nx, int ny, int rows, int max_blocks);
+int step_strips(int nx, int ny, int rows);
+bool step_variant_is_bulk(int variant);
 int step_variants();
 // resident blocks per GPU (occupancy x SMs) of a register-budget variant
 int step_max_blocks(int prec, int coll, int variant);
@@ -107,6 +123,37 @@ void set_last_error(const std::string& msg);
 
 }  // namespace lbm
 
+struct lbm_sim;
+
+namespace lbm {
+
+// Sims advanced together by one step launch per time step: a single sim, or
+// a batch of sims of any sizes and parameters (same precision, same stream,
+// in lockstep).
+struct Group {
+  std::vector<lbm_sim*> sims;
+  bool single = true;            // the group of one lbm_sim (persistent variants allowed)
+  int prec = LBM_FP32;
+  int coll_mode = 0;             // 0 BGK, 1 MRT, 2 per member
+  int rows = 8, variant = 1;
+  cudaStream_t stream = nullptr;
+  Member* d_members = nullptr;   // device launch table
+  Member h_member0{};            // host copy of member 0 (single-member launches)
+  int32_t* d_strip_member = nullptr;
+  double* partials = nullptr;    // [2][partial_stride][2]
+  int partial_stride = 0;
+  int64_t* t_base = nullptr;
+  int blocks = 0;                // lattice blocks of the current table
+  bool persistent = false;
+  std::vector<uint64_t> built_versions;   // member versions the table was built from
+  bool pending = false;          // forces of the last launched step not yet in the rings
+  int max_blocks_v[8] = {0};
+  std::map<int64_t, cudaGraphExec_t> graphs;   // chunk graphs keyed by length and parity
+  std::vector<void*> owned;      // allocations owned by a batch group
+};
+
+}  // namespace lbm
+
 // The opaque simulation object behind the C ABI.
 struct lbm_sim {
   lbm_config cfg{};
@@ -120,20 +167,15 @@ struct lbm_sim {
   uint32_t* solid_bits = nullptr;
   int words_per_row = 0;
   uint8_t* links = nullptr;
-  double* partials = nullptr;
-  int64_t n_partials = 0;
-  int partial_stride = 0;
-  int64_t* t_base = nullptr;   // step index at the start of a graph chunk
   double* ring = nullptr;
   int64_t ring_cap = 0;
   int* status = nullptr;
   double* scratch_fields = nullptr;  // 9 * ny * nx doubles (import/export)
-  double* mass_out = nullptr;
+  double* scratch_sums = nullptr;    // ny doubles (mass rows) + 1 (total)
   unsigned long long* nn_fallbacks = nullptr;
   int64_t t_host = 0;
   int64_t drained = 0;
-  bool pending = false;        // forces of step t_host - 1 not yet in the ring
-  int last_blocks = 0;
+  uint64_t version = 1;              // bumped by every change that the launch table holds
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   lbm_allocator alloc{};
@@ -143,10 +185,34 @@ struct lbm_sim {
   double rho_out = 1.0;
   lbm::DevMlp nn;
   double nn_drho = 0.05;
-  int rows = 8;
-  int variant = 1;
-  int max_blocks_v[8] = {0};
-  // CUDA graphs of chunks of steps, keyed by chunk length and parity
-  std::map<int64_t, cudaGraphExec_t> graphs;
-  std::vector<void*> owned;   // every device allocation, freed by lbm_destroy
+  lbm::Group own;                    // this sim alone
+  lbm::Group* last_group = nullptr;  // the group that launched its last step
+  int batch_refs = 0;                // batches holding this sim
+  std::vector<void*> owned;          // every device allocation, freed by lbm_destroy
 };
+
+// The opaque batch object behind the C ABI.
+struct lbm_batch {
+  lbm::Group g;
+};
+
+namespace lbm {
+// group.cu
+void* dev_alloc_raw(const lbm_allocator* a, size_t bytes);
+void dev_free_raw(const lbm_allocator* a, void* p);
+void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single);
+void group_release(Group& g);
+void group_clear_graphs(Group& g);
+void group_finalize(Group& g);        // enqueue the pending force reduction
+void group_step(Group& g, int64_t n); // enqueue n time steps of every member
+void group_set_tiling(Group& g, int rows, int variant);
+float group_autotune(Group& g, int steps, int64_t flush_bytes);
+void sim_settle(lbm_sim* s);          // finalise the forces of the sim's last group
+struct CudaError {
+  cudaError_t e;
+  const char* what;
+};
+inline void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw CudaError{e, what};
+}
+}  // namespace lbm

@@ -1,9 +1,9 @@
 // Fused stream-and-collide step of the D2Q9 lattice Boltzmann method and its
 // helper kernels (geometry preparation, initialisation, export, mass).
 //
-// One launch advances the whole lattice by one time step (Sec. 2.1, Eq. 1,
-// order of Fig. 1) in pull form: every node reads its nine incoming
-// populations h_i(x - c_i) from the source buffer and writes its nine
+// One launch advances every member lattice of a launch table by one time step
+// (Sec. 2.1, Eq. 1, order of Fig. 1) in pull form: every node reads its nine
+// incoming populations h_i(x - c_i) from its source buffer and writes its nine
 // post-collision populations to the destination buffer, so each population is
 // read once and written once per step (72 B per node in FP32).
 //   - solid nodes (bit set in the solid mask): full-way bounce-back (Eq. 11)
@@ -11,11 +11,15 @@
 //     momentum exchange (Eqs. 13-14) to an FP64 force accumulator;
 //   - west column (open x): Zou & He velocity inlet, then collision;
 //   - east column (open x): Zou & He pressure outflow (Eqs. 5-10) then
-//     collision, or left to the outflow kernel (NN, CBC);
+//     collision, or left to the outflow kernel (NN);
 //   - all other fluid nodes: BGK (Eq. 2) or MRT collision.
-// Each block writes an FP64 partial of the force; an extra block of the next
-// launch (or a one-block finalise kernel) sums the partials in a fixed order
-// into the force ring, so results are bitwise reproducible run to run.
+// The lattice is cut into strips of 128 columns x `rows` rows.  A launch table
+// lists the member lattices (one simulation, or a batch of simulations of
+// different sizes and parameters advanced together); each block handles one
+// strip (or, for a single member, strides over its strips).  Each block writes
+// an FP64 partial of its member's force; one extra block per member in the
+// next launch (or a finalise launch) sums them in a fixed order into the
+// member's force ring, so results are bitwise reproducible run to run.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -56,29 +60,36 @@ __device__ __forceinline__ void pull_row(const S* __restrict__ A, int plane, int
 template <typename R>
 __device__ __forceinline__ bool nonfinite(R v) { return !(fabs(v) < R(1e30)); }
 
+// A member's scalars in the compute precision (FP32 copies are made on the
+// host: GB300's FP64 pipe is narrow).
 template <typename R> struct Scalars;
 template <> struct Scalars<float> {
   float omega, u_in, rho_out;
   MrtRates<float> mrt;
-  __device__ explicit Scalars(const StepParams& p)
-      : omega(p.omega_f), u_in(p.u_in_f), rho_out(p.rho_out_f),
-        mrt{p.mrt_f[0], p.mrt_f[1], p.mrt_f[2], p.mrt_f[3]} {}
+  __device__ explicit Scalars(const Member& m)
+      : omega(m.omega_f), u_in(m.u_in_f), rho_out(m.rho_out_f),
+        mrt{m.mrt_f[0], m.mrt_f[1], m.mrt_f[2], m.mrt_f[3]} {}
 };
 template <> struct Scalars<double> {
   double omega, u_in, rho_out;
   MrtRates<double> mrt;
-  __device__ explicit Scalars(const StepParams& p)
-      : omega(p.omega), u_in(p.u_in), rho_out(p.rho_out),
-        mrt{p.mrt_se, p.mrt_seps, p.mrt_sq, p.mrt_snu} {}
+  __device__ explicit Scalars(const Member& m)
+      : omega(m.omega), u_in(m.u_in), rho_out(m.rho_out),
+        mrt{m.mrt_se, m.mrt_seps, m.mrt_sq, m.mrt_snu} {}
 };
 
-// Fixed-order sum of the block partials of step tt into the force ring
-// (executed by one block of 128 threads).
-__device__ void reduce_force(const StepParams& p, int64_t tt, int nb) {
+__device__ __forceinline__ int64_t step_index(const StepParams& p) {
+  return p.t_base ? *p.t_base + p.t_offset : p.t;
+}
+
+// Fixed-order sum of member k's block partials of step tt into its force ring
+// (one block of 128 threads).
+__device__ void reduce_force(const StepParams& p, int k, int64_t tt) {
   __shared__ double s_x[4], s_y[4];
+  const Member& m = p.members[k];
   const double* part = p.partials + (size_t)(tt & 1) * 2 * p.partial_stride;
   double ax = 0.0, ay = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+  for (int b = m.part_first + threadIdx.x; b < m.part_first + m.part_count; b += blockDim.x) {
     ax += part[2 * b];
     ay += part[2 * b + 1];
   }
@@ -87,116 +98,64 @@ __device__ void reduce_force(const StepParams& p, int64_t tt, int nb) {
   if (lane == 0) { s_x[warp] = ax; s_y[warp] = ay; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int64_t k = tt % p.ring_cap;
-    p.ring[2 * k] = (s_x[0] + s_x[1]) + (s_x[2] + s_x[3]);
-    p.ring[2 * k + 1] = (s_y[0] + s_y[1]) + (s_y[2] + s_y[3]);
+    const int64_t slot = tt % m.ring_cap;
+    m.ring[2 * slot] = (s_x[0] + s_x[1]) + (s_x[2] + s_x[3]);
+    m.ring[2 * slot + 1] = (s_y[0] + s_y[1]) + (s_y[2] + s_y[3]);
   }
 }
 
-// One block = 128 consecutive x of a strip of `rows` rows; blocks stride over
-// the strips (grid sized to the resident capacity by the host).  Each thread
-// walks its column down the strip and prefetches the next row's populations
-// and solid-mask word while the current row collides.  The extra last block
-// does no lattice work: it sums the previous step's force partials, so no
-// block waits at the end of a step.
-template <typename S, int COLL, int MINB>
-__global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
-  using R = typename Compute<S>::R;
-  const int nblocks = gridDim.x - 1;
-  const int64_t t = p.t_base ? *p.t_base + p.t_offset : p.t;
-  if ((int)blockIdx.x == nblocks) {
-    if (p.reduce_prev && t >= 1) reduce_force(p, t - 1, p.prev_blocks);
-    return;
-  }
-  const S* __restrict__ A = static_cast<const S*>(p.src);
-  S* __restrict__ B = static_cast<S*>(p.dst);
-  const int plane = (int)p.plane, pitch = (int)p.pitch;
-  const int nx = p.nx, ny = p.ny, rows = p.rows;
-  const int tiles_x = (nx + 127) >> 7;
-  const int strips = tiles_x * ((ny + rows - 1) / rows);
-  const Scalars<R> sc(p);
-
-  double fx = 0.0, fy = 0.0;
-  bool touched = false, bad = false;
-
-  for (int s = blockIdx.x; s < strips; s += nblocks) {
-    const int tx = s % tiles_x;
-    const int y0 = (s / tiles_x) * rows;
-    const int y1 = min(y0 + rows, ny);
-    const int x = (tx << 7) + threadIdx.x;
-    if (x >= nx) continue;
-    const bool west = !p.x_periodic && x == 0;
-    const bool east = !p.x_periodic && x == nx - 1;
-    if (east && p.east_mode == EAST_EXTERNAL) continue;
-    const int xm = x == 0 ? nx - 1 : x - 1;
-    const int xp = x == nx - 1 ? 0 : x + 1;
-    const uint32_t* bits = p.solid_bits + (x >> 5);
-    const uint32_t bit = 1u << (x & 31);
-
-    R h[9];
-    uint32_t word;
-    {
-      const int ym = y0 == 0 ? ny - 1 : y0 - 1;
-      const int yp = y0 + 1 == ny ? 0 : y0 + 1;
-      pull_row<S, R>(A, plane, y0 * pitch, ym * pitch, yp * pitch, x, xm, xp, h);
-      word = __ldg(bits + y0 * p.words_per_row);
-    }
-    for (int y = y0; y < y1; ++y) {
-      R hn[9];
-      uint32_t word_n = 0;
-      const bool more = y + 1 < y1;
-      if (more) {
-        const int y2 = y + 1;
-        const int yp = y2 + 1 == ny ? 0 : y2 + 1;
-        pull_row<S, R>(A, plane, y2 * pitch, y * pitch, yp * pitch, x, xm, xp, hn);
-        word_n = __ldg(bits + y2 * p.words_per_row);
-      }
-      const int o = y * pitch + x;
-      if (word & bit) {
-        // solid: momentum exchange over counted links, then full-way bounce-back
-        const unsigned lk = __ldg(p.links + (int64_t)y * nx + x);
-        if (lk) {
-          touched = true;
+// Solid node: momentum exchange over counted links (FP64), then full-way
+// bounce-back store.  Shared by both kernel families.
+template <typename S, typename R>
+__device__ __forceinline__ void solid_node(const S* __restrict__ A, S* __restrict__ B,
+                                           const Member& m, int x, int y, int o, const R h[9],
+                                           double& fx, double& fy, bool& touched) {
+  const unsigned lk = __ldg(m.links + (int64_t)y * m.nx + x);
+  if (lk) {
+    touched = true;
 #pragma unroll
-          for (int i = 1; i < 9; ++i) {
-            if ((lk >> (i - 1)) & 1u) {
-              // f_i arriving now + f_ibar that bounce-back stored here last step
-              const double v = (double)h[i] + (double)to_r<R>(ldg(A + opp(i) * plane + o)) +
-                               2.0 * wgt<double>(i);
-              fx += cx(i) * v;
-              fy += cy(i) * v;
-            }
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) B[i * plane + o] = from_r<S>(h[opp(i)]);
-      } else {
-        if (west) {
-          const R v = (R)inlet_perturbation(p.seed, t, y, p.v_amp);
-          zouhe_west<R>(h, sc.u_in, v);
-        } else if (east) {
-          zouhe_east<R>(h, sc.rho_out);
-        }
-        R drho, ux, uy;
-        if (COLL == 0)
-          collide_bgk<R>(h, sc.omega, drho, ux, uy);
-        else
-          collide_mrt<R>(h, sc.mrt, drho, ux, uy);
-        bad |= nonfinite(drho);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) B[i * plane + o] = from_r<S>(h[i]);
-      }
-      if (more) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = hn[i];
-        word = word_n;
+    for (int i = 1; i < 9; ++i) {
+      if ((lk >> (i - 1)) & 1u) {
+        // f_i arriving now + f_ibar that bounce-back stored here last step
+        const double v = (double)h[i] + (double)to_r<R>(ldg(A + opp(i) * m.plane + o)) +
+                         2.0 * wgt<double>(i);
+        fx += cx(i) * v;
+        fy += cy(i) * v;
       }
     }
   }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[opp(i)]);
+}
 
-  if (bad) atomicOr(p.status, DEV_NONFINITE);
+// Fluid node: open boundaries, collision, store.
+template <typename S, typename R, int COLL>
+__device__ __forceinline__ void fluid_node(S* __restrict__ B, const Member& m,
+                                           const Scalars<R>& sc, int64_t t, bool west,
+                                           bool east, int y, int o, R h[9], bool& bad) {
+  if (west) {
+    const R v = (R)inlet_perturbation(m.seed, t, y, m.v_amp);
+    const R u = m.ramp_steps > 0 ? (R)inlet_velocity(m.u_in, m.ramp_steps, t) : sc.u_in;
+    zouhe_west<R>(h, u, v);
+  } else if (east) {
+    zouhe_east<R>(h, sc.rho_out);
+  }
+  R drho, ux, uy;
+  // COLL 0: BGK, 1: MRT, 2: the member's own choice (mixed batches)
+  if (COLL == 0 || (COLL == 2 && m.coll == LBM_BGK))
+    collide_bgk<R>(h, sc.omega, drho, ux, uy);
+  else
+    collide_mrt<R>(h, sc.mrt, drho, ux, uy);
+  bad |= nonfinite(drho);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[i]);
+}
 
-  // ---- block partial of the force (FP64 work only where links were hit) ---
+// Block partial of the force (FP64 shuffles only where a counted link was hit)
+// and one block-wide vote on non-finite densities.
+__device__ __forceinline__ void write_partial(const StepParams& p, int64_t t, double fx, double fy,
+                                              bool touched, bool bad, int* status) {
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, DEV_NONFINITE);
   double* part = p.partials + (size_t)(t & 1) * 2 * p.partial_stride;
   if (!__syncthreads_or(touched)) {
     if (threadIdx.x == 0) {
@@ -216,41 +175,321 @@ __global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
   }
 }
 
-__global__ void finalize_force_kernel(const StepParams p, int64_t tt, int nb) {
-  reduce_force(p, tt, nb);
+// ---- register-pipelined kernel ---------------------------------------------
+// Each thread walks its column down a strip and prefetches the next row's
+// populations and solid-mask word while the current row collides.  With one
+// member (p.persistent) blocks stride over its strips on a grid sized to the
+// resident capacity; otherwise each block handles exactly one strip of the
+// member given by the strip table.
+template <typename S, int COLL>
+__device__ __forceinline__ void reg_strip(const StepParams& p, const Member& m,
+                                          const Scalars<typename Compute<S>::R>& sc, int64_t t,
+                                          int s, double& fx, double& fy, bool& touched,
+                                          bool& bad) {
+  using R = typename Compute<S>::R;
+  const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
+  S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
+  const int plane = m.plane, pitch = m.pitch, nx = m.nx, ny = m.ny;
+  const int tx = s % m.tiles_x;
+  const int y0 = (s / m.tiles_x) * p.rows;
+  const int y1 = min(y0 + p.rows, ny);
+  const int x = (tx << 7) + threadIdx.x;
+  if (x >= nx) return;
+  const bool west = !m.x_periodic && x == 0;
+  const bool east = !m.x_periodic && x == nx - 1;
+  if (east && m.east_mode == EAST_EXTERNAL) return;
+  const int xm = x == 0 ? nx - 1 : x - 1;
+  const int xp = x == nx - 1 ? 0 : x + 1;
+  const uint32_t* bits = m.solid_bits + (x >> 5);
+  const uint32_t bit = 1u << (x & 31);
+
+  R h[9];
+  uint32_t word;
+  {
+    const int ym = y0 == 0 ? ny - 1 : y0 - 1;
+    const int yp = y0 + 1 == ny ? 0 : y0 + 1;
+    pull_row<S, R>(A, plane, y0 * pitch, ym * pitch, yp * pitch, x, xm, xp, h);
+    word = __ldg(bits + y0 * m.words_per_row);
+  }
+  for (int y = y0; y < y1; ++y) {
+    R hn[9];
+    uint32_t word_n = 0;
+    const bool more = y + 1 < y1;
+    if (more) {
+      const int y2 = y + 1;
+      const int yp = y2 + 1 == ny ? 0 : y2 + 1;
+      pull_row<S, R>(A, plane, y2 * pitch, y * pitch, yp * pitch, x, xm, xp, hn);
+      word_n = __ldg(bits + y2 * m.words_per_row);
+    }
+    const int o = y * pitch + x;
+    if (word & bit)
+      solid_node<S, R>(A, B, m, x, y, o, h, fx, fy, touched);
+    else
+      fluid_node<S, R, COLL>(B, m, sc, t, west, east, y, o, h, bad);
+    if (more) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i] = hn[i];
+      word = word_n;
+    }
+  }
+}
+
+template <typename S, int COLL, int MINB>
+__global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
+  using R = typename Compute<S>::R;
+  const int nblocks = gridDim.x - p.n_members;
+  const int64_t t = step_index(p);
+  if ((int)blockIdx.x >= nblocks) {
+    if (p.reduce_prev && t >= 1) reduce_force(p, (int)blockIdx.x - nblocks, t - 1);
+    return;
+  }
+  double fx = 0.0, fy = 0.0;
+  bool touched = false, bad = false;
+  if (p.n_members == 1) {
+    // the member lives in the parameter bank: no registers held for its fields
+    const Scalars<R> sc(p.m0);
+    const int strips = p.m0.strip_count;
+    const int stride = p.persistent ? nblocks : strips;
+    for (int s = blockIdx.x; s < strips; s += stride)
+      reg_strip<S, COLL>(p, p.m0, sc, t, s, fx, fy, touched, bad);
+    write_partial(p, t, fx, fy, touched, bad, p.m0.status);
+  } else {
+    const Member& m = p.members[p.strip_member[blockIdx.x]];
+    const Scalars<R> sc(m);
+    reg_strip<S, COLL>(p, m, sc, t, (int)blockIdx.x - m.strip_first, fx, fy, touched, bad);
+    write_partial(p, t, fx, fy, touched, bad, m.status);
+  }
+}
+
+__global__ void finalize_force_kernel(const StepParams p, int64_t tt) {
+  reduce_force(p, blockIdx.x, tt);
 }
 
 __global__ void set_t_kernel(int64_t* t_base, int64_t value) { *t_base = value; }
 
-void launch_finalize_force(const StepParams& p, int64_t tt, int blocks, cudaStream_t s) {
-  finalize_force_kernel<<<1, 128, 0, s>>>(p, tt, blocks);
+void launch_finalize_force(const StepParams& p, int64_t tt, cudaStream_t s) {
+  finalize_force_kernel<<<p.n_members, 128, 0, s>>>(p, tt);
 }
 
 void launch_set_t(int64_t* t_base, int64_t value, cudaStream_t s) {
   set_t_kernel<<<1, 1, 0, s>>>(t_base, value);
 }
 
-int step_blocks(int nx, int ny, int rows, int max_blocks) {
-  const int tiles_x = (nx + 127) / 128;
-  const int strips = tiles_x * ((ny + rows - 1) / rows);
-  return strips < max_blocks ? strips : max_blocks;
+// ---- bulk-copy staged kernel -------------------------------------------------
+// One block = one strip.  Thread 0 stages, for each output row, the nine
+// source row segments (rows y - c_iy, columns shifted by -c_ix) plus the row's
+// solid-mask words into a ring of NS shared-memory slots with cp.async.bulk
+// copies that complete on one mbarrier per slot; all threads collide from
+// shared memory and store coalesced rows.  Each staged segment starts A
+// elements (16 bytes) before the tile, so every copy is 16-byte aligned and
+// the x shifts become fixed offsets.  Waits are bounded: a wait that gives up
+// latches DEV_TIMEOUT and the block drains its copies before it exits.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
-// Register-budget variants of the step kernel: __launch_bounds__ minimum
-// resident blocks of 128 threads per SM (more blocks = fewer registers).
-constexpr int kVariants = 3;
-constexpr int kMinBlocks[kVariants] = {6, 8, 10};
+constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t k = 0; k < kWaitLimit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename S>
+struct BulkLayout {
+  static constexpr int A = 16 / (int)sizeof(S);      // 16 bytes in elements
+  static constexpr int SEG = 128 + A;                // staged elements per source row
+  static constexpr int SEG_BYTES = SEG * (int)sizeof(S);
+  static constexpr int STAGE_BYTES = 9 * SEG_BYTES + 16;   // + 4 solid-mask words
+  static constexpr uint32_t TX_BYTES = (uint32_t)STAGE_BYTES;
+};
+
+size_t step_bulk_smem(int prec, int stages) {
+  const int sb = prec == LBM_FP64 ? BulkLayout<double>::STAGE_BYTES
+               : prec == LBM_FP32 ? BulkLayout<float>::STAGE_BYTES
+                                  : BulkLayout<__half>::STAGE_BYTES;
+  return (size_t)stages * sb + (size_t)stages * 8 + 16;
+}
+
+template <typename S, int COLL, int NS>
+__device__ __forceinline__ void bulk_strip(const StepParams& p, const Member& m, int64_t t,
+                                           unsigned char* smem) {
+  using R = typename Compute<S>::R;
+  using Lay = BulkLayout<S>;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * Lay::STAGE_BYTES);
+  __shared__ int s_abort;
+  const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
+  S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
+  const int plane = m.plane, pitch = m.pitch;
+  const int nx = m.nx, ny = m.ny;
+  const int s = (int)blockIdx.x - m.strip_first;
+  const int tx = s % m.tiles_x;
+  const int y0 = (s / m.tiles_x) * p.rows;
+  const int nrows = min(p.rows, ny - y0);
+  const int x0 = tx << 7;
+  const int lx = threadIdx.x;
+  const int x = x0 + lx;
+  const int lead = tx == 0 ? 0 : Lay::A;     // elements staged before x0 (left-shifted rows)
+  const Scalars<R> sc(m);
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int k = 0; k < NS; ++k) mbar_init(&full[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  auto issue = [&](int r) {
+    const int y = y0 + r;
+    const int slot = r % NS;
+    unsigned char* st = smem + slot * Lay::STAGE_BYTES;
+    mbar_expect_tx(&full[slot], Lay::TX_BYTES);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      int sy = y - cy(i);
+      sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+      const int sx = cx(i) == 1 ? x0 - lead : x0;
+      bulk_copy_g2s(st + i * Lay::SEG_BYTES, A + i * plane + sy * pitch + sx,
+                    (uint32_t)Lay::SEG_BYTES, &full[slot]);
+    }
+    bulk_copy_g2s(st + 9 * Lay::SEG_BYTES, m.solid_bits + y * m.words_per_row + (x0 >> 5), 16u,
+                  &full[slot]);
+  };
+  if (threadIdx.x == 0)
+    for (int r = 0; r < NS && r < nrows; ++r) issue(r);
+
+  const bool active = x < nx;
+  const bool west = !m.x_periodic && x == 0;
+  const bool east = !m.x_periodic && x == nx - 1;
+  const bool skip = !active || (east && m.east_mode == EAST_EXTERNAL);
+  double fx = 0.0, fy = 0.0;
+  bool touched = false, bad = false;
+
+  int r_stop = nrows;
+  for (int r = 0; r < nrows; ++r) {
+    const int slot = r % NS;
+    const uint32_t parity = (uint32_t)((r / NS) & 1);
+    if (!mbar_wait_bounded(&full[slot], parity)) {
+      atomicOr(m.status, DEV_TIMEOUT);
+      s_abort = 1;
+    }
+    const unsigned char* st = smem + slot * Lay::STAGE_BYTES;
+    const int y = y0 + r;
+    if (!skip && !s_abort) {
+      const S* seg = reinterpret_cast<const S*>(st);
+      R h[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const int idx = cx(i) == 1 ? lx - 1 + lead : (cx(i) == 0 ? lx : lx + 1);
+        h[i] = to_r<R>(seg[i * Lay::SEG + (idx < 0 ? 0 : idx)]);
+      }
+      if (x == 0 || x == nx - 1) {
+        // periodic wrap of the x +- 1 neighbours at the lattice edges
+        const int ym = y == 0 ? ny - 1 : y - 1;
+        const int yp = y == ny - 1 ? 0 : y + 1;
+        if (x == 0) {
+          h[1] = to_r<R>(A[1 * plane + y * pitch + nx - 1]);
+          h[5] = to_r<R>(A[5 * plane + ym * pitch + nx - 1]);
+          h[8] = to_r<R>(A[8 * plane + yp * pitch + nx - 1]);
+        }
+        if (x == nx - 1) {
+          h[3] = to_r<R>(A[3 * plane + y * pitch]);
+          h[6] = to_r<R>(A[6 * plane + ym * pitch]);
+          h[7] = to_r<R>(A[7 * plane + yp * pitch]);
+        }
+      }
+      const uint32_t word = reinterpret_cast<const uint32_t*>(st + 9 * Lay::SEG_BYTES)[lx >> 5];
+      const int o = y * pitch + x;
+      if ((word >> (lx & 31)) & 1u)
+        solid_node<S, R>(A, B, m, x, y, o, h, fx, fy, touched);
+      else
+        fluid_node<S, R, COLL>(B, m, sc, t, west, east, y, o, h, bad);
+    }
+    __syncthreads();   // every thread is done with this slot
+    if (s_abort) {
+      r_stop = r;
+      break;
+    }
+    if (threadIdx.x == 0 && r + NS < nrows) issue(r + NS);
+  }
+  if (r_stop < nrows && threadIdx.x == 0) {
+    // a wait gave up at row r_stop: rows r_stop .. r_stop + NS - 1 may still be
+    // in flight (one outstanding phase per slot); wait for them, bounded, so
+    // no copy lands in shared memory after the block exits
+    const int issued = min(nrows, r_stop + NS);
+    for (int r = r_stop; r < issued; ++r)
+      mbar_wait_bounded(&full[r % NS], (uint32_t)((r / NS) & 1));
+  }
+  write_partial(p, t, fx, fy, touched, bad, m.status);
+}
+
+template <typename S, int COLL, int NS>
+__global__ void __launch_bounds__(128) step_bulk_kernel(const StepParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int nblocks = gridDim.x - p.n_members;
+  const int64_t t = step_index(p);
+  if ((int)blockIdx.x >= nblocks) {
+    if (p.reduce_prev && t >= 1) reduce_force(p, (int)blockIdx.x - nblocks, t - 1);
+    return;
+  }
+  if (p.n_members == 1)
+    bulk_strip<S, COLL, NS>(p, p.m0, t, smem);
+  else
+    bulk_strip<S, COLL, NS>(p, p.members[p.strip_member[blockIdx.x]], t, smem);
+}
+
+// ---- variants and launch ------------------------------------------------------
+int step_strips(int nx, int ny, int rows) {
+  return ((nx + 127) / 128) * ((ny + rows - 1) / rows);
+}
+
+// Variants 0-2: the register-pipelined kernel with __launch_bounds__ minimum
+// resident blocks of 128 threads per SM of 6, 8, 10.  Variants 3-4: the
+// bulk-copy staged kernel with 4 or 6 ring slots.
+constexpr int kVariants = 5;
+
+bool step_variant_is_bulk(int variant) { return variant >= 3; }
+
+int step_variants() { return kVariants; }
 
 template <typename S, int COLL>
-static cudaError_t occ(int variant, int* per_sm) {
+static cudaError_t occ(int variant, int* per_sm) {   // COLL 2 shares the MRT budget
   switch (variant) {
     case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 6>, 128, 0);
     case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 8>, 128, 0);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 10>, 128, 0);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 10>, 128, 0);
+    default: *per_sm = 1; return cudaSuccess;   // staged variants: one block per strip
   }
 }
-
-int step_variants() { return kVariants; }
 
 int step_max_blocks(int prec, int coll, int variant) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -267,26 +506,42 @@ int step_max_blocks(int prec, int coll, int variant) {
   return sms * per_sm;
 }
 
+template <typename S, int COLL, int NS>
+static void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
+  const int prec = sizeof(S) == 8 ? LBM_FP64 : (sizeof(S) == 4 ? LBM_FP32 : LBM_FP16DEV);
+  const size_t smem = step_bulk_smem(prec, NS);
+  static bool attr = false;   // one attribute call per instantiation
+  if (!attr) {
+    cudaFuncSetAttribute(step_bulk_kernel<S, COLL, NS>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  step_bulk_kernel<S, COLL, NS><<<blocks + p.n_members, 128, smem, s>>>(p);
+}
+
 template <typename S, int COLL>
 static void launch_v(const StepParams& p, int variant, int blocks, cudaStream_t s) {
+  const int g = blocks + p.n_members;
   switch (variant) {
-    case 0: step_kernel<S, COLL, 6><<<blocks + 1, 128, 0, s>>>(p); break;
-    case 1: step_kernel<S, COLL, 8><<<blocks + 1, 128, 0, s>>>(p); break;
-    default: step_kernel<S, COLL, 10><<<blocks + 1, 128, 0, s>>>(p); break;
+    case 0: step_kernel<S, COLL, 6><<<g, 128, 0, s>>>(p); break;
+    case 1: step_kernel<S, COLL, 8><<<g, 128, 0, s>>>(p); break;
+    case 2: step_kernel<S, COLL, 10><<<g, 128, 0, s>>>(p); break;
+    case 3: launch_bulk<S, COLL, 4>(p, blocks, s); break;
+    default: launch_bulk<S, COLL, 6>(p, blocks, s); break;
   }
 }
 
+template <typename S>
+static void launch_c(int coll, const StepParams& p, int variant, int blocks, cudaStream_t s) {
+  if (coll == LBM_BGK) launch_v<S, 0>(p, variant, blocks, s);
+  else if (coll == LBM_MRT) launch_v<S, 1>(p, variant, blocks, s);
+  else launch_v<S, 2>(p, variant, blocks, s);
+}
+
 void launch_step(int prec, int coll, const StepParams& p, int variant, int blocks, cudaStream_t s) {
-  if (prec == LBM_FP64) {
-    if (coll == LBM_BGK) launch_v<double, 0>(p, variant, blocks, s);
-    else launch_v<double, 1>(p, variant, blocks, s);
-  } else if (prec == LBM_FP32) {
-    if (coll == LBM_BGK) launch_v<float, 0>(p, variant, blocks, s);
-    else launch_v<float, 1>(p, variant, blocks, s);
-  } else {
-    if (coll == LBM_BGK) launch_v<__half, 0>(p, variant, blocks, s);
-    else launch_v<__half, 1>(p, variant, blocks, s);
-  }
+  if (prec == LBM_FP64) launch_c<double>(coll, p, variant, blocks, s);
+  else if (prec == LBM_FP32) launch_c<float>(coll, p, variant, blocks, s);
+  else launch_c<__half>(coll, p, variant, blocks, s);
 }
 
 // ---- geometry preparation --------------------------------------------------
