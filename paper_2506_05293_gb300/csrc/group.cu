@@ -90,6 +90,44 @@ void build_table(Group& g) {
     g.blocks = std::min(strip_total, cap);
     ms[0].part_first = 0;
     ms[0].part_count = g.blocks;
+  } else if (step_variant_streams(g.variant)) {
+    // streaming staged kernel: a resident-sized grid shared among the members
+    // in proportion to their strips; each member's blocks are contiguous
+    const int cap = std::max(1, g.max_blocks_v[g.variant]);
+    const int G = std::min(strip_total, cap);
+    std::vector<int> gk((size_t)n);
+    int used = 0;
+    for (int k = 0; k < n; ++k) {
+      const int want = (int)((int64_t)G * ms[(size_t)k].strip_count / std::max(1, strip_total));
+      gk[(size_t)k] = std::max(1, std::min(want, ms[(size_t)k].strip_count));
+      used += gk[(size_t)k];
+    }
+    // hand leftover blocks to the members with the most strips per block
+    while (used < G) {
+      int best = -1;
+      double most = 0.0;
+      for (int k = 0; k < n; ++k) {
+        if (gk[(size_t)k] >= ms[(size_t)k].strip_count) continue;
+        const double per = (double)ms[(size_t)k].strip_count / gk[(size_t)k];
+        if (per > most) { most = per; best = k; }
+      }
+      if (best < 0) break;
+      gk[(size_t)best]++;
+      used++;
+    }
+    int first = 0;
+    std::vector<int32_t> bm;
+    bm.reserve((size_t)used);
+    for (int k = 0; k < n; ++k) {
+      ms[(size_t)k].part_first = first;
+      ms[(size_t)k].part_count = gk[(size_t)k];
+      for (int j = 0; j < gk[(size_t)k]; ++j) bm.push_back(k);
+      first += gk[(size_t)k];
+    }
+    g.blocks = first;
+    if (n > 1)
+      ck(cudaMemcpyAsync(g.d_strip_member, bm.data(), bm.size() * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, g.stream), "block table copy");
   } else {
     g.blocks = strip_total;
     for (int k = 0; k < n; ++k) {
@@ -247,7 +285,7 @@ void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single) {
   const lbm_allocator* a = s0->have_alloc ? &s0->alloc : nullptr;
   int most = 0;
   for (int v = 0; v < step_variants(); ++v) {
-    g.max_blocks_v[v] = step_max_blocks(g.prec, mode == 2 ? 1 : mode, v);
+    g.max_blocks_v[v] = step_max_blocks(g.prec, mode, v);
     if (g.max_blocks_v[v] <= 0) throw CudaError{cudaGetLastError(), "occupancy query"};
     most = std::max(most, g.max_blocks_v[v]);
   }
@@ -399,7 +437,7 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
       ck(cudaStreamSynchronize(g.stream), "sync");
       g.pending = false;
     };
-    const int rows_c[] = {2, 4, 8, 16, 32};
+    const int rows_c[] = {2, 4, 8, 12, 16, 24, 32};
     float best = 1e30f;
     int best_rows = g.rows, best_var = g.variant;
     for (int v = 0; v < step_variants(); ++v) {

@@ -102,8 +102,9 @@ void launch_finalize_force(const StepParams& p, int64_t tt, cudaStream_t s);
 void launch_set_t(int64_t* t_base, int64_t value, cudaStream_t s);
 int step_strips(int nx, int ny, int rows);
 bool step_variant_is_bulk(int variant);
+bool step_variant_streams(int variant);   // staged variant on a resident-sized grid
 int step_variants();
-// resident blocks per GPU (occupancy x SMs) of a register-budget variant
+// resident blocks per GPU (occupancy x SMs) of a variant; coll 2 = per member
 int step_max_blocks(int prec, int coll, int variant);
 void launch_geometry_prep(const uint8_t* kind, int nx, int ny, int x_periodic, uint32_t* bits,
                           int words_per_row, uint8_t* links, cudaStream_t s);

@@ -134,7 +134,7 @@ __device__ __forceinline__ void fluid_node(S* __restrict__ B, const Member& m,
                                            const Scalars<R>& sc, int64_t t, bool west,
                                            bool east, int y, int o, R h[9], bool& bad) {
   if (west) {
-    const R v = (R)inlet_perturbation(m.seed, t, y, m.v_amp);
+    const R v = m.v_amp != 0.0 ? (R)inlet_perturbation(m.seed, t, y, m.v_amp) : R(0);
     const R u = m.ramp_steps > 0 ? (R)inlet_velocity(m.u_in, m.ramp_steps, t) : sc.u_in;
     zouhe_west<R>(h, u, v);
   } else if (east) {
@@ -297,13 +297,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or the hint (ns) elapses, instead of spinning
+constexpr uint32_t kSuspendHintNs = 1000000;   // 1 ms per attempt
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
       : "memory");
   return ok != 0;
 }
@@ -316,7 +320,7 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
       : "memory");
 }
 
-constexpr uint32_t kWaitLimit = 1u << 22;   // try_wait rounds before a wait gives up
+constexpr uint32_t kWaitLimit = 2000;   // attempts (x the 1 ms hint) before a wait gives up
 
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   for (uint32_t k = 0; k < kWaitLimit; ++k)
@@ -340,9 +344,13 @@ size_t step_bulk_smem(int prec, int stages) {
   return (size_t)stages * sb + (size_t)stages * 8 + 16;
 }
 
+// One block streams the rows of its strips (local strips lb, lb + gk, ... of
+// member m) through the ring: thread 0 keeps up to NS rows in flight, and the
+// ring carries on across strip boundaries, so a block pays the pipeline fill
+// once per launch rather than once per strip.
 template <typename S, int COLL, int NS>
-__device__ __forceinline__ void bulk_strip(const StepParams& p, const Member& m, int64_t t,
-                                           unsigned char* smem) {
+__device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, int64_t t, int lb,
+                                         int gk, unsigned char* smem) {
   using R = typename Compute<S>::R;
   using Lay = BulkLayout<S>;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * Lay::STAGE_BYTES);
@@ -350,15 +358,9 @@ __device__ __forceinline__ void bulk_strip(const StepParams& p, const Member& m,
   const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
   S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
   const int plane = m.plane, pitch = m.pitch;
-  const int nx = m.nx, ny = m.ny;
-  const int s = (int)blockIdx.x - m.strip_first;
-  const int tx = s % m.tiles_x;
-  const int y0 = (s / m.tiles_x) * p.rows;
-  const int nrows = min(p.rows, ny - y0);
-  const int x0 = tx << 7;
+  const int nx = m.nx, ny = m.ny, tiles_x = m.tiles_x, rows = p.rows;
+  const int strips = m.strip_count;
   const int lx = threadIdx.x;
-  const int x = x0 + lx;
-  const int lead = tx == 0 ? 0 : Lay::A;     // elements staged before x0 (left-shifted rows)
   const Scalars<R> sc(m);
 
   if (threadIdx.x == 0) {
@@ -368,48 +370,71 @@ __device__ __forceinline__ void bulk_strip(const StepParams& p, const Member& m,
   }
   __syncthreads();
 
-  auto issue = [&](int r) {
-    const int y = y0 + r;
-    const int slot = r % NS;
+  // strip geometry, recomputed only when a cursor moves to a new strip
+  struct Strip {
+    int y0, x0, lead, nrows;
+  };
+  auto strip_at = [&](int ls) {
+    Strip st;
+    st.y0 = (ls / tiles_x) * rows;
+    st.x0 = (ls % tiles_x) << 7;
+    st.lead = st.x0 == 0 ? 0 : Lay::A;
+    st.nrows = min(rows, ny - st.y0);
+    return st;
+  };
+
+  // producer cursor (thread 0): next (strip, row) to stage
+  int ps = lb, pr = 0;
+  Strip pst = strip_at(lb);
+  auto produce = [&](int slot) {
+    const int y = pst.y0 + pr;
     unsigned char* st = smem + slot * Lay::STAGE_BYTES;
     mbar_expect_tx(&full[slot], Lay::TX_BYTES);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       int sy = y - cy(i);
       sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-      const int sx = cx(i) == 1 ? x0 - lead : x0;
+      const int sx = cx(i) == 1 ? pst.x0 - pst.lead : pst.x0;
       bulk_copy_g2s(st + i * Lay::SEG_BYTES, A + i * plane + sy * pitch + sx,
                     (uint32_t)Lay::SEG_BYTES, &full[slot]);
     }
-    bulk_copy_g2s(st + 9 * Lay::SEG_BYTES, m.solid_bits + y * m.words_per_row + (x0 >> 5), 16u,
-                  &full[slot]);
+    bulk_copy_g2s(st + 9 * Lay::SEG_BYTES, m.solid_bits + y * m.words_per_row + (pst.x0 >> 5),
+                  16u, &full[slot]);
+    if (++pr == pst.nrows) {
+      pr = 0;
+      ps += gk;
+      if (ps < strips) pst = strip_at(ps);
+    }
   };
   if (threadIdx.x == 0)
-    for (int r = 0; r < NS && r < nrows; ++r) issue(r);
+    for (int k = 0; k < NS && ps < strips; ++k) produce(k);
 
-  const bool active = x < nx;
-  const bool west = !m.x_periodic && x == 0;
-  const bool east = !m.x_periodic && x == nx - 1;
-  const bool skip = !active || (east && m.east_mode == EAST_EXTERNAL);
   double fx = 0.0, fy = 0.0;
   bool touched = false, bad = false;
-
-  int r_stop = nrows;
-  for (int r = 0; r < nrows; ++r) {
-    const int slot = r % NS;
-    const uint32_t parity = (uint32_t)((r / NS) & 1);
-    if (!mbar_wait_bounded(&full[slot], parity)) {
+  int cs = lb, cr = 0;          // consumer cursor
+  Strip cst = strip_at(lb);
+  int x = cst.x0 + lx;
+  bool west = !m.x_periodic && x == 0;
+  bool east = !m.x_periodic && x == nx - 1;
+  bool skip = x >= nx || (east && m.east_mode == EAST_EXTERNAL);
+  int j = 0;                    // items consumed
+  bool aborted = false;
+  while (cs < strips) {
+    const int slot = j % NS;
+    const uint32_t parity = (uint32_t)((j / NS) & 1);
+    const bool ready = mbar_wait_bounded(&full[slot], parity);
+    if (!ready) {
       atomicOr(m.status, DEV_TIMEOUT);
       s_abort = 1;
     }
+    const int y = cst.y0 + cr;
     const unsigned char* st = smem + slot * Lay::STAGE_BYTES;
-    const int y = y0 + r;
-    if (!skip && !s_abort) {
+    if (!skip && ready) {
       const S* seg = reinterpret_cast<const S*>(st);
       R h[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        const int idx = cx(i) == 1 ? lx - 1 + lead : (cx(i) == 0 ? lx : lx + 1);
+        const int idx = cx(i) == 1 ? lx - 1 + cst.lead : (cx(i) == 0 ? lx : lx + 1);
         h[i] = to_r<R>(seg[i * Lay::SEG + (idx < 0 ? 0 : idx)]);
       }
       if (x == 0 || x == nx - 1) {
@@ -436,24 +461,35 @@ __device__ __forceinline__ void bulk_strip(const StepParams& p, const Member& m,
     }
     __syncthreads();   // every thread is done with this slot
     if (s_abort) {
-      r_stop = r;
+      aborted = true;
       break;
     }
-    if (threadIdx.x == 0 && r + NS < nrows) issue(r + NS);
+    if (threadIdx.x == 0 && ps < strips) produce(slot);   // item j + NS into the freed slot
+    ++j;
+    if (++cr == cst.nrows) {
+      cr = 0;
+      cs += gk;
+      if (cs < strips) {
+        cst = strip_at(cs);
+        x = cst.x0 + lx;
+        west = !m.x_periodic && x == 0;
+        east = !m.x_periodic && x == nx - 1;
+        skip = x >= nx || (east && m.east_mode == EAST_EXTERNAL);
+      }
+    }
   }
-  if (r_stop < nrows && threadIdx.x == 0) {
-    // a wait gave up at row r_stop: rows r_stop .. r_stop + NS - 1 may still be
-    // in flight (one outstanding phase per slot); wait for them, bounded, so
-    // no copy lands in shared memory after the block exits
-    const int issued = min(nrows, r_stop + NS);
-    for (int r = r_stop; r < issued; ++r)
-      mbar_wait_bounded(&full[r % NS], (uint32_t)((r / NS) & 1));
+  if (aborted && threadIdx.x == 0) {
+    // a wait gave up at item j: items j .. j + NS - 1 may still be in flight
+    // (one outstanding phase per slot); wait for them, bounded, so no copy
+    // lands in shared memory after the block exits
+    for (int k = j; k < j + NS; ++k)
+      mbar_wait_bounded(&full[k % NS], (uint32_t)((k / NS) & 1));
   }
   write_partial(p, t, fx, fy, touched, bad, m.status);
 }
 
 template <typename S, int COLL, int NS>
-__global__ void __launch_bounds__(128) step_bulk_kernel(const StepParams p) {
+__global__ void __launch_bounds__(128, 8) step_bulk_kernel(const StepParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nblocks = gridDim.x - p.n_members;
   const int64_t t = step_index(p);
@@ -461,10 +497,26 @@ __global__ void __launch_bounds__(128) step_bulk_kernel(const StepParams p) {
     if (p.reduce_prev && t >= 1) reduce_force(p, (int)blockIdx.x - nblocks, t - 1);
     return;
   }
-  if (p.n_members == 1)
-    bulk_strip<S, COLL, NS>(p, p.m0, t, smem);
-  else
-    bulk_strip<S, COLL, NS>(p, p.members[p.strip_member[blockIdx.x]], t, smem);
+  if (p.n_members == 1) {
+    // blocks part_count apart share the strips: part_count = strips gives one
+    // strip per block, fewer blocks make them stream several strips each
+    bulk_run<S, COLL, NS>(p, p.m0, t, (int)blockIdx.x, p.m0.part_count, smem);
+  } else {
+    // stage this block's member record in shared memory once (coalesced),
+    // instead of every thread chasing its fields in global memory
+    __shared__ __align__(16) Member s_member;
+    constexpr int kWords = (int)(sizeof(Member) / sizeof(uint64_t));
+    static_assert(sizeof(Member) % sizeof(uint64_t) == 0, "Member must be 8-byte sized");
+    if (threadIdx.x < 32) {
+      const uint64_t* src =
+          reinterpret_cast<const uint64_t*>(p.members + p.strip_member[blockIdx.x]);
+      uint64_t* dst = reinterpret_cast<uint64_t*>(&s_member);
+      for (int w = threadIdx.x; w < kWords; w += 32) dst[w] = src[w];
+    }
+    __syncthreads();
+    bulk_run<S, COLL, NS>(p, s_member, t, (int)blockIdx.x - s_member.part_first,
+                          s_member.part_count, smem);
+  }
 }
 
 // ---- variants and launch ------------------------------------------------------
@@ -474,20 +526,46 @@ int step_strips(int nx, int ny, int rows) {
 
 // Variants 0-2: the register-pipelined kernel with __launch_bounds__ minimum
 // resident blocks of 128 threads per SM of 6, 8, 10.  Variants 3-4: the
-// bulk-copy staged kernel with 4 or 6 ring slots.
-constexpr int kVariants = 5;
+// bulk-copy staged kernel with 4 or 6 ring slots, one block per strip.
+// Variants 5-6: the same kernel with 4 or 8 slots on a resident-sized grid,
+// each block streaming several strips through its ring.
+constexpr int kVariants = 7;
 
 bool step_variant_is_bulk(int variant) { return variant >= 3; }
+bool step_variant_streams(int variant) { return variant >= 5; }
+
+template <int V> struct BulkSlots;
+template <> struct BulkSlots<3> { static constexpr int NS = 4; };
+template <> struct BulkSlots<4> { static constexpr int NS = 6; };
+template <> struct BulkSlots<5> { static constexpr int NS = 4; };
+template <> struct BulkSlots<6> { static constexpr int NS = 8; };
 
 int step_variants() { return kVariants; }
 
+template <typename S>
+static constexpr int prec_of() {
+  return sizeof(S) == 8 ? LBM_FP64 : (sizeof(S) == 4 ? LBM_FP32 : LBM_FP16DEV);
+}
+
+template <typename S, int COLL, int NS>
+static cudaError_t occ_bulk(int* per_sm) {
+  const size_t smem = step_bulk_smem(prec_of<S>(), NS);
+  const cudaError_t e = cudaFuncSetAttribute(
+      step_bulk_kernel<S, COLL, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_bulk_kernel<S, COLL, NS>, 128,
+                                                       smem);
+}
+
 template <typename S, int COLL>
-static cudaError_t occ(int variant, int* per_sm) {   // COLL 2 shares the MRT budget
+static cudaError_t occ(int variant, int* per_sm) {
   switch (variant) {
     case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 6>, 128, 0);
     case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 8>, 128, 0);
     case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 10>, 128, 0);
-    default: *per_sm = 1; return cudaSuccess;   // staged variants: one block per strip
+    case 3: case 5: return occ_bulk<S, COLL, 4>(per_sm);
+    case 4: return occ_bulk<S, COLL, 6>(per_sm);
+    default: return occ_bulk<S, COLL, 8>(per_sm);
   }
 }
 
@@ -496,26 +574,23 @@ int step_max_blocks(int prec, int coll, int variant) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
-  if (prec == LBM_FP64)
-    e = coll == LBM_BGK ? occ<double, 0>(variant, &per_sm) : occ<double, 1>(variant, &per_sm);
-  else if (prec == LBM_FP32)
-    e = coll == LBM_BGK ? occ<float, 0>(variant, &per_sm) : occ<float, 1>(variant, &per_sm);
-  else
-    e = coll == LBM_BGK ? occ<__half, 0>(variant, &per_sm) : occ<__half, 1>(variant, &per_sm);
+  auto by_coll = [&](auto tag) {
+    using S = decltype(tag);
+    return coll == 0 ? occ<S, 0>(variant, &per_sm)
+                     : (coll == 1 ? occ<S, 1>(variant, &per_sm) : occ<S, 2>(variant, &per_sm));
+  };
+  if (prec == LBM_FP64) e = by_coll(double{});
+  else if (prec == LBM_FP32) e = by_coll(float{});
+  else e = by_coll(__half{});
   if (e != cudaSuccess || sms <= 0 || per_sm <= 0) return 0;
   return sms * per_sm;
 }
 
 template <typename S, int COLL, int NS>
 static void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
-  const int prec = sizeof(S) == 8 ? LBM_FP64 : (sizeof(S) == 4 ? LBM_FP32 : LBM_FP16DEV);
-  const size_t smem = step_bulk_smem(prec, NS);
-  static bool attr = false;   // one attribute call per instantiation
-  if (!attr) {
-    cudaFuncSetAttribute(step_bulk_kernel<S, COLL, NS>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  // the dynamic shared memory attribute is set by the occupancy query that
+  // every group runs at creation (occ_bulk)
+  const size_t smem = step_bulk_smem(prec_of<S>(), NS);
   step_bulk_kernel<S, COLL, NS><<<blocks + p.n_members, 128, smem, s>>>(p);
 }
 
@@ -526,8 +601,9 @@ static void launch_v(const StepParams& p, int variant, int blocks, cudaStream_t 
     case 0: step_kernel<S, COLL, 6><<<g, 128, 0, s>>>(p); break;
     case 1: step_kernel<S, COLL, 8><<<g, 128, 0, s>>>(p); break;
     case 2: step_kernel<S, COLL, 10><<<g, 128, 0, s>>>(p); break;
-    case 3: launch_bulk<S, COLL, 4>(p, blocks, s); break;
-    default: launch_bulk<S, COLL, 6>(p, blocks, s); break;
+    case 3: case 5: launch_bulk<S, COLL, 4>(p, blocks, s); break;
+    case 4: launch_bulk<S, COLL, 6>(p, blocks, s); break;
+    default: launch_bulk<S, COLL, 8>(p, blocks, s); break;
   }
 }
 
