@@ -427,7 +427,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cylinder_sweep_D40", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=sorted(BYTES_PER_NODE))
-    ap.add_argument("--cpu-steps", type=int, default=24)
+    ap.add_argument("--cpu-steps", type=int, default=120)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=0, help="fixed tiling instead of the autotuner")
     ap.add_argument("--variant", type=int, default=3)

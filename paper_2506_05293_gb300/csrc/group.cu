@@ -437,7 +437,7 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
       ck(cudaStreamSynchronize(g.stream), "sync");
       g.pending = false;
     };
-    const int rows_c[] = {2, 4, 8, 12, 16, 24, 32};
+    const int rows_c[] = {2, 4, 8, 12, 16, 20, 24, 32, 40, 48, 64};
     float best = 1e30f;
     int best_rows = g.rows, best_var = g.variant;
     for (int v = 0; v < step_variants(); ++v) {

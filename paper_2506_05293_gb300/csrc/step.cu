@@ -78,6 +78,14 @@ template <> struct Scalars<double> {
         mrt{m.mrt_se, m.mrt_seps, m.mrt_sq, m.mrt_snu} {}
 };
 
+// Programmatic dependent launch: a step kernel lets the next one be
+// scheduled early (it then does its set-up while this one drains) and waits
+// for the previous step's grid to complete before it touches populations.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ int64_t step_index(const StepParams& p) {
   return p.t_base ? *p.t_base + p.t_offset : p.t;
 }
@@ -85,7 +93,7 @@ __device__ __forceinline__ int64_t step_index(const StepParams& p) {
 // Fixed-order sum of member k's block partials of step tt into its force ring
 // (one block of 128 threads).
 __device__ void reduce_force(const StepParams& p, int k, int64_t tt) {
-  __shared__ double s_x[4], s_y[4];
+  __shared__ double s_x[8], s_y[8];
   const Member& m = p.members[k];
   const double* part = p.partials + (size_t)(tt & 1) * 2 * p.partial_stride;
   double ax = 0.0, ay = 0.0;
@@ -98,9 +106,11 @@ __device__ void reduce_force(const StepParams& p, int k, int64_t tt) {
   if (lane == 0) { s_x[warp] = ax; s_y[warp] = ay; }
   __syncthreads();
   if (threadIdx.x == 0) {
+    double bx = 0.0, by = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { bx += s_x[w]; by += s_y[w]; }
     const int64_t slot = tt % m.ring_cap;
-    m.ring[2 * slot] = (s_x[0] + s_x[1]) + (s_x[2] + s_x[3]);
-    m.ring[2 * slot + 1] = (s_y[0] + s_y[1]) + (s_y[2] + s_y[3]);
+    m.ring[2 * slot] = bx;
+    m.ring[2 * slot + 1] = by;
   }
 }
 
@@ -164,14 +174,16 @@ __device__ __forceinline__ void write_partial(const StepParams& p, int64_t t, do
     }
     return;
   }
-  __shared__ double s_fx[4], s_fy[4];
+  __shared__ double s_fx[8], s_fy[8];
   warp_sum2(fx, fy);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) { s_fx[warp] = fx; s_fy[warp] = fy; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = (s_fx[0] + s_fx[1]) + (s_fx[2] + s_fx[3]);
-    part[2 * blockIdx.x + 1] = (s_fy[0] + s_fy[1]) + (s_fy[2] + s_fy[3]);
+    double bx = 0.0, by = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { bx += s_fx[w]; by += s_fy[w]; }
+    part[2 * blockIdx.x] = bx;
+    part[2 * blockIdx.x + 1] = by;
   }
 }
 
@@ -237,6 +249,8 @@ __device__ __forceinline__ void reg_strip(const StepParams& p, const Member& m,
 template <typename S, int COLL, int MINB>
 __global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
   using R = typename Compute<S>::R;
+  pdl_launch_dependents();
+  pdl_wait();
   const int nblocks = gridDim.x - p.n_members;
   const int64_t t = step_index(p);
   if ((int)blockIdx.x >= nblocks) {
@@ -341,36 +355,49 @@ size_t step_bulk_smem(int prec, int stages) {
   const int sb = prec == LBM_FP64 ? BulkLayout<double>::STAGE_BYTES
                : prec == LBM_FP32 ? BulkLayout<float>::STAGE_BYTES
                                   : BulkLayout<__half>::STAGE_BYTES;
-  return (size_t)stages * sb + (size_t)stages * 8 + 16;
+  return (size_t)stages * sb + (size_t)stages * 16 + 16;   // ring + full/empty barriers
 }
 
 // One block streams the rows of its strips (local strips lb, lb + gk, ... of
-// member m) through the ring: thread 0 keeps up to NS rows in flight, and the
-// ring carries on across strip boundaries, so a block pays the pipeline fill
-// once per launch rather than once per strip.
+// member m) through an NS-slot ring with warp specialisation: warp 4 is the
+// producer -- its lane 0 waits until a slot is released ("empty" barrier,
+// one arrival per consumer warp), then stages the next row into it with
+// cp.async.bulk completing on the slot's "full" barrier -- and warps 0-3 are
+// consumers, each waiting on "full", colliding its 32 columns and releasing
+// the slot.  No block-wide barrier per row: warps run ahead independently.
+constexpr int kConsumerWarps = 4;
+constexpr int kBulkThreads = 32 * (kConsumerWarps + 1);
+
 template <typename S, int COLL, int NS>
-__device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, int64_t t, int lb,
-                                         int gk, unsigned char* smem) {
+__device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, int lb, int gk,
+                                         unsigned char* smem) {
   using R = typename Compute<S>::R;
   using Lay = BulkLayout<S>;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * Lay::STAGE_BYTES);
+  uint64_t* empty = full + NS;
   __shared__ int s_abort;
   const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
   S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
   const int plane = m.plane, pitch = m.pitch;
   const int nx = m.nx, ny = m.ny, tiles_x = m.tiles_x, rows = p.rows;
   const int strips = m.strip_count;
-  const int lx = threadIdx.x;
-  const Scalars<R> sc(m);
+  const int warp = threadIdx.x >> 5;
 
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int k = 0; k < NS; ++k) mbar_init(&full[k], 1);
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kConsumerWarps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // set-up done: wait for the previous step to complete before touching the
+  // populations (it may still be reading the buffer this step writes)
+  pdl_wait();
+  const int64_t t = step_index(p);
 
-  // strip geometry, recomputed only when a cursor moves to a new strip
+  // strip geometry
   struct Strip {
     int y0, x0, lead, nrows;
   };
@@ -383,124 +410,136 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
     return st;
   };
 
-  // producer cursor (thread 0): next (strip, row) to stage
-  int ps = lb, pr = 0;
-  Strip pst = strip_at(lb);
-  auto produce = [&](int slot) {
-    const int y = pst.y0 + pr;
-    unsigned char* st = smem + slot * Lay::STAGE_BYTES;
-    mbar_expect_tx(&full[slot], Lay::TX_BYTES);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      int sy = y - cy(i);
-      sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-      const int sx = cx(i) == 1 ? pst.x0 - pst.lead : pst.x0;
-      bulk_copy_g2s(st + i * Lay::SEG_BYTES, A + i * plane + sy * pitch + sx,
-                    (uint32_t)Lay::SEG_BYTES, &full[slot]);
-    }
-    bulk_copy_g2s(st + 9 * Lay::SEG_BYTES, m.solid_bits + y * m.words_per_row + (pst.x0 >> 5),
-                  16u, &full[slot]);
-    if (++pr == pst.nrows) {
-      pr = 0;
-      ps += gk;
-      if (ps < strips) pst = strip_at(ps);
-    }
-  };
-  if (threadIdx.x == 0)
-    for (int k = 0; k < NS && ps < strips; ++k) produce(k);
-
   double fx = 0.0, fy = 0.0;
   bool touched = false, bad = false;
-  int cs = lb, cr = 0;          // consumer cursor
-  Strip cst = strip_at(lb);
-  int x = cst.x0 + lx;
-  bool west = !m.x_periodic && x == 0;
-  bool east = !m.x_periodic && x == nx - 1;
-  bool skip = x >= nx || (east && m.east_mode == EAST_EXTERNAL);
-  int j = 0;                    // items consumed
-  bool aborted = false;
-  while (cs < strips) {
-    const int slot = j % NS;
-    const uint32_t parity = (uint32_t)((j / NS) & 1);
-    const bool ready = mbar_wait_bounded(&full[slot], parity);
-    if (!ready) {
-      atomicOr(m.status, DEV_TIMEOUT);
-      s_abort = 1;
-    }
-    const int y = cst.y0 + cr;
-    const unsigned char* st = smem + slot * Lay::STAGE_BYTES;
-    if (!skip && ready) {
-      const S* seg = reinterpret_cast<const S*>(st);
-      R h[9];
+
+  if (warp == kConsumerWarps) {
+    // ---------------- producer ----------------
+    if ((threadIdx.x & 31) == 0) {
+      int ps = lb, pr = 0, k = 0;
+      Strip pst = strip_at(lb);
+      while (ps < strips) {
+        const int slot = k % NS;
+        if (k >= NS && !mbar_wait_bounded(&empty[slot], (uint32_t)(((k / NS) - 1) & 1))) {
+          atomicOr(m.status, DEV_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        if (s_abort) break;
+        const int y = pst.y0 + pr;
+        unsigned char* st = smem + slot * Lay::STAGE_BYTES;
+        mbar_expect_tx(&full[slot], Lay::TX_BYTES);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const int idx = cx(i) == 1 ? lx - 1 + cst.lead : (cx(i) == 0 ? lx : lx + 1);
-        h[i] = to_r<R>(seg[i * Lay::SEG + (idx < 0 ? 0 : idx)]);
-      }
-      if (x == 0 || x == nx - 1) {
-        // periodic wrap of the x +- 1 neighbours at the lattice edges
-        const int ym = y == 0 ? ny - 1 : y - 1;
-        const int yp = y == ny - 1 ? 0 : y + 1;
-        if (x == 0) {
-          h[1] = to_r<R>(A[1 * plane + y * pitch + nx - 1]);
-          h[5] = to_r<R>(A[5 * plane + ym * pitch + nx - 1]);
-          h[8] = to_r<R>(A[8 * plane + yp * pitch + nx - 1]);
+        for (int i = 0; i < 9; ++i) {
+          int sy = y - cy(i);
+          sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+          const int sx = cx(i) == 1 ? pst.x0 - pst.lead : pst.x0;
+          bulk_copy_g2s(st + i * Lay::SEG_BYTES, A + i * plane + sy * pitch + sx,
+                        (uint32_t)Lay::SEG_BYTES, &full[slot]);
         }
-        if (x == nx - 1) {
-          h[3] = to_r<R>(A[3 * plane + y * pitch]);
-          h[6] = to_r<R>(A[6 * plane + ym * pitch]);
-          h[7] = to_r<R>(A[7 * plane + yp * pitch]);
+        bulk_copy_g2s(st + 9 * Lay::SEG_BYTES,
+                      m.solid_bits + y * m.words_per_row + (pst.x0 >> 5), 16u, &full[slot]);
+        ++k;
+        if (++pr == pst.nrows) {
+          pr = 0;
+          ps += gk;
+          if (ps < strips) pst = strip_at(ps);
         }
       }
-      const uint32_t word = reinterpret_cast<const uint32_t*>(st + 9 * Lay::SEG_BYTES)[lx >> 5];
-      const int o = y * pitch + x;
-      if ((word >> (lx & 31)) & 1u)
-        solid_node<S, R>(A, B, m, x, y, o, h, fx, fy, touched);
-      else
-        fluid_node<S, R, COLL>(B, m, sc, t, west, east, y, o, h, bad);
+      // no copy may land after the block exits: wait (bounded) for the last
+      // item staged into each slot
+      for (int kk = k > NS ? k - NS : 0; kk < k; ++kk)
+        mbar_wait_bounded(&full[kk % NS], (uint32_t)((kk / NS) & 1));
     }
-    __syncthreads();   // every thread is done with this slot
-    if (s_abort) {
-      aborted = true;
-      break;
-    }
-    if (threadIdx.x == 0 && ps < strips) produce(slot);   // item j + NS into the freed slot
-    ++j;
-    if (++cr == cst.nrows) {
-      cr = 0;
-      cs += gk;
-      if (cs < strips) {
-        cst = strip_at(cs);
-        x = cst.x0 + lx;
-        west = !m.x_periodic && x == 0;
-        east = !m.x_periodic && x == nx - 1;
-        skip = x >= nx || (east && m.east_mode == EAST_EXTERNAL);
+  } else {
+    // ---------------- consumers ----------------
+    const int lx = threadIdx.x;     // column within the 128-wide tile
+    const Scalars<R> sc(m);
+    int cs = lb, cr = 0, j = 0;
+    Strip cst = strip_at(lb);
+    int x = cst.x0 + lx;
+    bool west = !m.x_periodic && x == 0;
+    bool east = !m.x_periodic && x == nx - 1;
+    bool skip = x >= nx || (east && m.east_mode == EAST_EXTERNAL);
+    while (cs < strips) {
+      const int slot = j % NS;
+      // warp-uniform outcome, so the warp never diverges around __syncwarp
+      const bool ready = __all_sync(
+          0xffffffffu, !s_abort && mbar_wait_bounded(&full[slot], (uint32_t)((j / NS) & 1)));
+      if (!ready) {
+        atomicOr(m.status, DEV_TIMEOUT);
+        s_abort = 1;
+        break;
+      }
+      const int y = cst.y0 + cr;
+      const unsigned char* st = smem + slot * Lay::STAGE_BYTES;
+      if (!skip) {
+        const S* seg = reinterpret_cast<const S*>(st);
+        R h[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int idx = cx(i) == 1 ? lx - 1 + cst.lead : (cx(i) == 0 ? lx : lx + 1);
+          h[i] = to_r<R>(seg[i * Lay::SEG + (idx < 0 ? 0 : idx)]);
+        }
+        if (x == 0 || x == nx - 1) {
+          // periodic wrap of the x +- 1 neighbours at the lattice edges
+          const int ym = y == 0 ? ny - 1 : y - 1;
+          const int yp = y == ny - 1 ? 0 : y + 1;
+          if (x == 0) {
+            h[1] = to_r<R>(A[1 * plane + y * pitch + nx - 1]);
+            h[5] = to_r<R>(A[5 * plane + ym * pitch + nx - 1]);
+            h[8] = to_r<R>(A[8 * plane + yp * pitch + nx - 1]);
+          }
+          if (x == nx - 1) {
+            h[3] = to_r<R>(A[3 * plane + y * pitch]);
+            h[6] = to_r<R>(A[6 * plane + ym * pitch]);
+            h[7] = to_r<R>(A[7 * plane + yp * pitch]);
+          }
+        }
+        const uint32_t word =
+            reinterpret_cast<const uint32_t*>(st + 9 * Lay::SEG_BYTES)[lx >> 5];
+        const int o = y * pitch + x;
+        if ((word >> (lx & 31)) & 1u)
+          solid_node<S, R>(A, B, m, x, y, o, h, fx, fy, touched);
+        else
+          fluid_node<S, R, COLL>(B, m, sc, t, west, east, y, o, h, bad);
+      }
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot]))
+                     : "memory");
+      ++j;
+      if (++cr == cst.nrows) {
+        cr = 0;
+        cs += gk;
+        if (cs < strips) {
+          cst = strip_at(cs);
+          x = cst.x0 + lx;
+          west = !m.x_periodic && x == 0;
+          east = !m.x_periodic && x == nx - 1;
+          skip = x >= nx || (east && m.east_mode == EAST_EXTERNAL);
+        }
       }
     }
-  }
-  if (aborted && threadIdx.x == 0) {
-    // a wait gave up at item j: items j .. j + NS - 1 may still be in flight
-    // (one outstanding phase per slot); wait for them, bounded, so no copy
-    // lands in shared memory after the block exits
-    for (int k = j; k < j + NS; ++k)
-      mbar_wait_bounded(&full[k % NS], (uint32_t)((k / NS) & 1));
   }
   write_partial(p, t, fx, fy, touched, bad, m.status);
 }
 
-template <typename S, int COLL, int NS>
-__global__ void __launch_bounds__(128, 8) step_bulk_kernel(const StepParams p) {
+template <typename S, int COLL, int NS, int MINB>
+__global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const StepParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
+  pdl_launch_dependents();
   const int nblocks = gridDim.x - p.n_members;
-  const int64_t t = step_index(p);
   if ((int)blockIdx.x >= nblocks) {
+    pdl_wait();
+    const int64_t t = step_index(p);
     if (p.reduce_prev && t >= 1) reduce_force(p, (int)blockIdx.x - nblocks, t - 1);
     return;
   }
   if (p.n_members == 1) {
     // blocks part_count apart share the strips: part_count = strips gives one
     // strip per block, fewer blocks make them stream several strips each
-    bulk_run<S, COLL, NS>(p, p.m0, t, (int)blockIdx.x, p.m0.part_count, smem);
+    bulk_run<S, COLL, NS>(p, p.m0, (int)blockIdx.x, p.m0.part_count, smem);
   } else {
     // stage this block's member record in shared memory once (coalesced),
     // instead of every thread chasing its fields in global memory
@@ -514,7 +553,7 @@ __global__ void __launch_bounds__(128, 8) step_bulk_kernel(const StepParams p) {
       for (int w = threadIdx.x; w < kWords; w += 32) dst[w] = src[w];
     }
     __syncthreads();
-    bulk_run<S, COLL, NS>(p, s_member, t, (int)blockIdx.x - s_member.part_first,
+    bulk_run<S, COLL, NS>(p, s_member, (int)blockIdx.x - s_member.part_first,
                           s_member.part_count, smem);
   }
 }
@@ -525,20 +564,15 @@ int step_strips(int nx, int ny, int rows) {
 }
 
 // Variants 0-2: the register-pipelined kernel with __launch_bounds__ minimum
-// resident blocks of 128 threads per SM of 6, 8, 10.  Variants 3-4: the
-// bulk-copy staged kernel with 4 or 6 ring slots, one block per strip.
-// Variants 5-6: the same kernel with 4 or 8 slots on a resident-sized grid,
-// each block streaming several strips through its ring.
-constexpr int kVariants = 7;
+// resident blocks of 128 threads per SM of 6, 8, 10.  Variant 3: the
+// warp-specialised staged kernel (4-slot ring), one block per strip.
+// Variant 4: the same on a resident-sized grid, each block streaming several
+// strips through its ring.
+constexpr int kVariants = 5;
+constexpr int kBulkSlots = 4;
 
 bool step_variant_is_bulk(int variant) { return variant >= 3; }
-bool step_variant_streams(int variant) { return variant >= 5; }
-
-template <int V> struct BulkSlots;
-template <> struct BulkSlots<3> { static constexpr int NS = 4; };
-template <> struct BulkSlots<4> { static constexpr int NS = 6; };
-template <> struct BulkSlots<5> { static constexpr int NS = 4; };
-template <> struct BulkSlots<6> { static constexpr int NS = 8; };
+bool step_variant_streams(int variant) { return variant >= 4; }
 
 int step_variants() { return kVariants; }
 
@@ -547,14 +581,14 @@ static constexpr int prec_of() {
   return sizeof(S) == 8 ? LBM_FP64 : (sizeof(S) == 4 ? LBM_FP32 : LBM_FP16DEV);
 }
 
-template <typename S, int COLL, int NS>
+template <typename S, int COLL, int MINB>
 static cudaError_t occ_bulk(int* per_sm) {
-  const size_t smem = step_bulk_smem(prec_of<S>(), NS);
-  const cudaError_t e = cudaFuncSetAttribute(
-      step_bulk_kernel<S, COLL, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = step_bulk_smem(prec_of<S>(), kBulkSlots);
+  auto k = step_bulk_kernel<S, COLL, kBulkSlots, MINB>;
+  const cudaError_t e =
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_bulk_kernel<S, COLL, NS>, 128,
-                                                       smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, kBulkThreads, smem);
 }
 
 template <typename S, int COLL>
@@ -563,9 +597,7 @@ static cudaError_t occ(int variant, int* per_sm) {
     case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 6>, 128, 0);
     case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 8>, 128, 0);
     case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 10>, 128, 0);
-    case 3: case 5: return occ_bulk<S, COLL, 4>(per_sm);
-    case 4: return occ_bulk<S, COLL, 6>(per_sm);
-    default: return occ_bulk<S, COLL, 8>(per_sm);
+    default: return occ_bulk<S, COLL, 6>(per_sm);
   }
 }
 
@@ -586,24 +618,40 @@ int step_max_blocks(int prec, int coll, int variant) {
   return sms * per_sm;
 }
 
-template <typename S, int COLL, int NS>
+// Launch with programmatic stream serialisation (dependent launch).
+template <typename Kernel>
+static void launch_pdl(Kernel kernel, int grid, int threads, size_t smem, cudaStream_t s,
+                       const StepParams& p) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, p);
+}
+
+template <typename S, int COLL, int MINB>
 static void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
   // the dynamic shared memory attribute is set by the occupancy query that
   // every group runs at creation (occ_bulk)
-  const size_t smem = step_bulk_smem(prec_of<S>(), NS);
-  step_bulk_kernel<S, COLL, NS><<<blocks + p.n_members, 128, smem, s>>>(p);
+  const size_t smem = step_bulk_smem(prec_of<S>(), kBulkSlots);
+  launch_pdl(step_bulk_kernel<S, COLL, kBulkSlots, MINB>, blocks + p.n_members, kBulkThreads,
+             smem, s, p);
 }
 
 template <typename S, int COLL>
 static void launch_v(const StepParams& p, int variant, int blocks, cudaStream_t s) {
   const int g = blocks + p.n_members;
   switch (variant) {
-    case 0: step_kernel<S, COLL, 6><<<g, 128, 0, s>>>(p); break;
-    case 1: step_kernel<S, COLL, 8><<<g, 128, 0, s>>>(p); break;
-    case 2: step_kernel<S, COLL, 10><<<g, 128, 0, s>>>(p); break;
-    case 3: case 5: launch_bulk<S, COLL, 4>(p, blocks, s); break;
-    case 4: launch_bulk<S, COLL, 6>(p, blocks, s); break;
-    default: launch_bulk<S, COLL, 8>(p, blocks, s); break;
+    case 0: launch_pdl(step_kernel<S, COLL, 6>, g, 128, 0, s, p); break;
+    case 1: launch_pdl(step_kernel<S, COLL, 8>, g, 128, 0, s, p); break;
+    case 2: launch_pdl(step_kernel<S, COLL, 10>, g, 128, 0, s, p); break;
+    default: launch_bulk<S, COLL, 6>(p, blocks, s); break;
   }
 }
 
