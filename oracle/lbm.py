@@ -295,6 +295,24 @@ class Solver:
         self.forces = []          # (Fx, Fy) per step
         self.nn_fallbacks = 0
         self.cbc_state = None
+        self.capture = None       # (x_t, every) of the data-set capture, or None
+        self.captured = []        # captured blocks of rows, (ny, 84) each
+
+    def capture_plane(self, x_t, every):
+        """Record training rows of Sec. 3.1 at column ``x_t``: during every step
+        t -> t+1 with (t+1) % every == 0, after streaming, bounce-back and the
+        open boundaries and before collision, one row per lattice row y (in
+        order): the 81 inputs of Eq. 15 taken as if x_t were the outflow
+        column (``nn_features(g, x_t)``) followed by the post-stream
+        f_3, f_6, f_7 at (x_t, y), the values the network learns to rebuild."""
+        self.capture = (int(x_t), int(every))
+        self.captured = []
+
+    def dataset(self):
+        """All captured rows, float64 (n, 84), in capture order."""
+        if not self.captured:
+            return np.zeros((0, 84))
+        return np.vstack(self.captured)
 
     def init_equilibrium(self, rho=None, ux=None, uy=None):
         shape = (self.cfg.ny, self.cfg.nx)
@@ -352,6 +370,9 @@ class Solver:
             else:
                 raise ValueError(cfg.outflow)
             g[:, m, xb] = col[:, m]
+        if self.capture is not None and (self.t + 1) % self.capture[1] == 0:
+            x_t = self.capture[0]
+            self.captured.append(np.hstack([nn_features(g, x_t), g[list(NN_POPS), :, x_t].T]))
         post = self.collide(g)                                        # Eq. 2 / MRT
         g[:, fluid] = post[:, fluid]
         self.f = g

@@ -142,3 +142,65 @@ def test_dataset_stats_on_constructed_data():
     expect_std = np.where(b == 0, 1.0, b)
     assert np.allclose(std, expect_std, atol=1e-14)
     assert abs(out_scale - 0.003) < 1e-15
+
+
+# velocity set written out from the paper's numbering (east, north, west,
+# south, then the diagonals NE, NW, SW, SE)
+_C = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+_OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+
+
+def _post_stream_value(f, kind, i, x, y):
+    """f_i(x, y) just after streaming (f_i(x, t+1) = f*_i(x - c_i, t), periodic)
+    and bounce-back (a solid node reverses what arrived), by direct indexing."""
+    ny, nx = kind.shape
+    if kind[y, x] != 0:
+        i = _OPP[i]
+    cx, cy = _C[i]
+    return f[i, (y - cy) % ny, (x - cx) % nx]
+
+
+def test_capture_rows_follow_the_streaming_definition():
+    """Captured rows, checked entry by entry against the definition of the
+    pull step on a state whose every value is distinct (a solid node sits in
+    the capture window, so its reversal is exercised too)."""
+    ny, nx, x_t = 7, 9, 5
+    kind = np.zeros((ny, nx), np.uint8)
+    kind[3, 3] = 1
+    o = lbm.Solver(lbm.Config(nx=nx, ny=ny, tau=0.8, x_periodic=True), kind)
+    f = np.empty((9, ny, nx))
+    for i in range(9):
+        for y in range(ny):
+            for x in range(nx):
+                f[i, y, x] = 0.1 + 1e-3 * i + 1e-5 * y + 1e-7 * x
+    o.f = f.copy()
+    o.capture_plane(x_t, 1)
+    o.step(1)
+    rows = o.dataset()
+    assert rows.shape == (ny, 84)
+    for y in range(ny):
+        for k in range(3):
+            for j in range(3):
+                for i in range(9):
+                    want = _post_stream_value(f, kind, i, x_t - 1 - k, (y + j - 1) % ny)
+                    assert rows[y, k * 27 + j * 9 + i] == want
+        for n, i in enumerate((3, 6, 7)):
+            assert rows[y, 81 + n] == _post_stream_value(f, kind, i, x_t, y)
+
+
+def test_capture_every_and_uniform_state():
+    """Rows appear only on steps with (t+1) % every == 0; on a uniform
+    periodic equilibrium (a fixed point) every row is the equilibrium itself."""
+    ny, nx = 6, 10
+    o = lbm.Solver(lbm.Config(nx=nx, ny=ny, tau=0.7, x_periodic=True), np.zeros((ny, nx), np.uint8))
+    o.init_equilibrium(np.full((ny, nx), 1.02), np.full((ny, nx), 0.03), np.full((ny, nx), -0.01))
+    o.capture_plane(6, 3)
+    o.step(10)                       # captures during steps 2->3, 5->6, 8->9
+    rows = o.dataset()
+    assert rows.shape == (3 * ny, 84)
+    rho, u, v = 1.02, 0.03, -0.01
+    feq = np.array([w * rho * (1 + 3 * (cx * u + cy * v) + 4.5 * (cx * u + cy * v) ** 2
+                               - 1.5 * (u * u + v * v))
+                    for w, (cx, cy) in zip([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, _C)])
+    assert np.allclose(rows[:, :81], np.tile(feq, 9)[None, :], atol=1e-15, rtol=0)
+    assert np.allclose(rows[:, 81:], feq[[3, 6, 7]][None, :], atol=1e-15, rtol=0)
