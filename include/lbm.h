@@ -145,6 +145,76 @@ typedef struct {
 lbm_status lbm_set_outflow_nn(lbm_sim* sim, const lbm_mlp* net, double fallback_drho);
 lbm_status lbm_nn_fallbacks(lbm_sim* sim, int64_t* count);
 
+/* ---- Training data and training of the direct-reconstruction network ----
+ * (Sec. 3.1: the network learns, from long-domain runs, the populations 3, 6,
+ * 7 that cross a truncation plane; loss Eq. 16.)
+ *
+ * A data-set row is 84 floats: the 81 inputs of Eq. 15 (post-stream
+ * populations of columns x_t-1, x_t-2, x_t-3 at rows y-1, y, y+1, index
+ * k*27 + j*9 + i, rows wrapping periodically) followed by the post-stream
+ * f_3, f_6, f_7 at (x_t, y).  Rows live in DEVICE memory owned by the caller,
+ * row-major float[n][84]. */
+
+/* Capture training rows at column x_t (4 <= x_t <= nx-2): during every step
+ * t -> t+1 with (t+1) % every == 0 the library writes ny rows (y = 0..ny-1,
+ * in order) after streaming and bounce-back, before collision, into dev_rows
+ * (device float[cap_rows][84], caller-owned, must stay valid while capturing)
+ * starting at row lbm_capture_count.  Capturing stops once the next ny rows
+ * would pass cap_rows.  Resets the count.  dev_rows NULL stops capturing.
+ * In a batch each member captures on its own. */
+lbm_status lbm_capture_plane(lbm_sim* sim, int32_t x_t, int32_t every, float* dev_rows,
+                             int64_t cap_rows);
+/* Rows captured so far (complete once the sim's stream reaches them). */
+lbm_status lbm_capture_count(lbm_sim* sim, int64_t* rows);
+
+/* Normalisation of the network from a data set (device rows, n >= 1): per
+ * input the mean and the population standard deviation (a std below 1e-12
+ * becomes 1), and out_scale = the population standard deviation of the
+ * residual targets f_ref - f_{3,6,7}(x_t - 1) (inputs 12, 15, 16) pooled over
+ * the three outputs (same floor).  FP64 sums in a fixed order.  Outputs are
+ * host float[81], float[81], float[1].  Synchronous on stream (cudaStream_t,
+ * NULL = legacy default stream). */
+lbm_status lbm_nn_dataset_stats(const float* dev_rows, int64_t n_rows, void* stream,
+                                float* in_mean, float* in_std, float* out_scale);
+
+/* Options of lbm_nn_train / lbm_nn_loss_grad. */
+typedef struct {
+  int32_t batch_rows;   /* rows per Adam step; batch b = rows [b*batch_rows, (b+1)*batch_rows) */
+  double lr;            /* Adam (Kingma & Ba 2015): step size, default 1e-5 */
+  double beta1, beta2;  /* default 0.9, 0.999 */
+  double eps;           /* default 1e-8 */
+  int64_t adam_t0;      /* Adam steps already taken with the given moments (bias correction) */
+  int32_t max_cluster;  /* CTAs of the training cluster, 1..16; 0 = the largest that fits */
+  void* stream;         /* cudaStream_t; NULL = legacy default stream */
+} lbm_train_opts;
+
+/* batch_rows 0, lr 1e-5, beta1 0.9, beta2 0.999, eps 1e-8, adam_t0 0,
+ * max_cluster 0, stream NULL. */
+lbm_status lbm_train_opts_default(lbm_train_opts* opts);
+
+/* Train net (81 -> ... -> 3, hidden layers of 1..64 units, act tanh or leaky)
+ * with Eq. 16: L = mean over the batch and the three outputs of
+ * (f_{3,6,7}(x_t-1) + out_scale * o - f_ref)^2, one Adam step per entry of
+ * order (host int32[n_steps], batch indices, each in [0, n_rows/batch_rows)).
+ * net->in_mean / in_std / out_scale are used as given.  On return params_out
+ * (host float[n_params]) holds the trained parameters; adam_m / adam_v (host
+ * float[n_params], nullable = zeros in and not returned) are the first and
+ * second moments, in and out; loss_log (host double[n_steps], nullable) gets
+ * each batch's loss before its step.  FP32 arithmetic, FP64 loss sums.
+ * Synchronous.  Runs as one thread-block cluster; results are bitwise
+ * reproducible for a given cluster size. */
+lbm_status lbm_nn_train(const float* dev_rows, int64_t n_rows, const int32_t* order,
+                        int64_t n_steps, const lbm_train_opts* opts, const lbm_mlp* net,
+                        float* params_out, float* adam_m, float* adam_v, double* loss_log);
+
+/* Loss of Eq. 16 (host double[n_batches], required) and, if grads is not
+ * NULL, its gradient with respect to every parameter (host
+ * float[n_batches][n_params], the layout of lbm_mlp.params) for each batch
+ * index in order (host int32[n_batches]); no update.  Synchronous. */
+lbm_status lbm_nn_loss_grad(const float* dev_rows, int64_t n_rows, const int32_t* order,
+                            int64_t n_batches, const lbm_train_opts* opts, const lbm_mlp* net,
+                            double* losses, float* grads);
+
 /* Enqueue n time steps (n >= 0).  Each step: pull streaming (Eq. 1), momentum
  * exchange (Eqs. 13-14) and bounce-back (Eq. 11) at solid nodes, the west
  * inlet, the east outflow, and collision of all fluid nodes; the force on

@@ -40,6 +40,12 @@ class LbmMlp(Structure):
                 ("in_std", POINTER(c_float)), ("out_scale", c_float)]
 
 
+class LbmTrainOpts(Structure):
+    _fields_ = [("batch_rows", c_int32), ("lr", c_double), ("beta1", c_double),
+                ("beta2", c_double), ("eps", c_double), ("adam_t0", c_int64),
+                ("max_cluster", c_int32), ("stream", c_void_p)]
+
+
 # name -> (restype, argtypes); every function of include/lbm.h
 SIGNATURES = {
     "lbm_config_default": (c_int, [POINTER(LbmConfig)]),
@@ -51,6 +57,17 @@ SIGNATURES = {
     "lbm_set_outflow_zouhe": (c_int, [c_void_p, c_double]),
     "lbm_set_outflow_nn": (c_int, [c_void_p, POINTER(LbmMlp), c_double]),
     "lbm_nn_fallbacks": (c_int, [c_void_p, POINTER(c_int64)]),
+    "lbm_capture_plane": (c_int, [c_void_p, c_int32, c_int32, c_void_p, c_int64]),
+    "lbm_capture_count": (c_int, [c_void_p, POINTER(c_int64)]),
+    "lbm_nn_dataset_stats": (c_int, [c_void_p, c_int64, c_void_p, POINTER(c_float),
+                                     POINTER(c_float), POINTER(c_float)]),
+    "lbm_train_opts_default": (c_int, [POINTER(LbmTrainOpts)]),
+    "lbm_nn_train": (c_int, [c_void_p, c_int64, POINTER(c_int32), c_int64, POINTER(LbmTrainOpts),
+                             POINTER(LbmMlp), POINTER(c_float), POINTER(c_float),
+                             POINTER(c_float), POINTER(c_double)]),
+    "lbm_nn_loss_grad": (c_int, [c_void_p, c_int64, POINTER(c_int32), c_int64,
+                                 POINTER(LbmTrainOpts), POINTER(LbmMlp), POINTER(c_double),
+                                 POINTER(c_float)]),
     "lbm_step": (c_int, [c_void_p, c_int64]),
     "lbm_sync": (c_int, [c_void_p]),
     "lbm_time": (c_int, [c_void_p, POINTER(c_int64)]),

@@ -9,7 +9,7 @@ from ctypes import POINTER, byref, c_double, c_float, c_int64, c_uint8, c_void_p
 import numpy as np
 
 from . import _lib
-from ._lib import LbmConfig, LbmMlp
+from ._lib import LbmConfig, LbmMlp, LbmTrainOpts
 
 LBM_BGK, LBM_MRT = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV = 0, 1, 2
@@ -145,6 +145,112 @@ def lbm_nn_fallbacks(sim):
     c = c_int64()
     _check(_lib.load().lbm_nn_fallbacks(sim.handle, byref(c)))
     return c.value
+
+
+def _devptr(buf):
+    """Device address of a CUDA tensor (or a raw address given as an int)."""
+    if isinstance(buf, int):
+        return buf
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return buf.data_ptr()
+
+
+def lbm_capture_plane(sim, x_t, every, rows=None, cap_rows=None):
+    """Capture training rows at column x_t every ``every`` steps into ``rows``
+    (a contiguous float32 CUDA tensor of shape (cap_rows, 84)); rows=None stops."""
+    if rows is None:
+        _check(_lib.load().lbm_capture_plane(sim.handle, 0, 0, None, 0))
+        return
+    if cap_rows is None:
+        cap_rows = rows.shape[0]
+    _check(_lib.load().lbm_capture_plane(sim.handle, int(x_t), int(every),
+                                         c_void_p(_devptr(rows)), int(cap_rows)))
+
+
+def lbm_capture_count(sim):
+    c = c_int64()
+    _check(_lib.load().lbm_capture_count(sim.handle, byref(c)))
+    return c.value
+
+
+def lbm_nn_dataset_stats(rows, n_rows=None, stream=None):
+    """(in_mean[81], in_std[81], out_scale) of a device data set of rows."""
+    n = rows.shape[0] if n_rows is None else n_rows
+    mean = np.zeros(81, np.float32)
+    std = np.zeros(81, np.float32)
+    scale = c_float()
+    _check(_lib.load().lbm_nn_dataset_stats(c_void_p(_devptr(rows)), int(n),
+                                            c_void_p(int(stream)) if stream else None,
+                                            mean.ctypes.data_as(POINTER(c_float)),
+                                            std.ctypes.data_as(POINTER(c_float)), byref(scale)))
+    return mean, std, scale.value
+
+
+def lbm_train_opts_default(**kw):
+    o = LbmTrainOpts()
+    _check(_lib.load().lbm_train_opts_default(byref(o)))
+    for k, v in kw.items():
+        if k == "stream":
+            v = c_void_p(int(v)) if v else None
+        setattr(o, k, v)
+    return o
+
+
+def _order(order):
+    return np.ascontiguousarray(order, dtype=np.int32)
+
+
+def lbm_nn_train(rows, order, layers, act="tanh", in_mean=None, in_std=None, out_scale=1.0,
+                 adam_m=None, adam_v=None, n_rows=None, **opts):
+    """Adam steps of Eq. 16 on device rows, batch order[k] at step k.
+    Returns (layers, adam_m, adam_v, losses) with the trained layers as float32."""
+    o = lbm_train_opts_default(**opts)
+    m, keep = make_mlp(layers, act, in_mean, in_std, out_scale)
+    order = _order(order)
+    n = rows.shape[0] if n_rows is None else n_rows
+    out = np.zeros(m.n_params, np.float32)
+    am = np.zeros(m.n_params, np.float32) if adam_m is None else \
+        np.ascontiguousarray(adam_m, dtype=np.float32).copy()
+    av = np.zeros(m.n_params, np.float32) if adam_v is None else \
+        np.ascontiguousarray(adam_v, dtype=np.float32).copy()
+    losses = np.zeros(order.size, np.float64)
+    _check(_lib.load().lbm_nn_train(c_void_p(_devptr(rows)), int(n),
+                                    order.ctypes.data_as(POINTER(ctypes.c_int32)), order.size,
+                                    byref(o), byref(m), out.ctypes.data_as(POINTER(c_float)),
+                                    am.ctypes.data_as(POINTER(c_float)),
+                                    av.ctypes.data_as(POINTER(c_float)), _dptr(losses)))
+    del keep
+    return unflatten(out, layers), am, av, losses
+
+
+def lbm_nn_loss_grad(rows, order, layers, act="tanh", in_mean=None, in_std=None, out_scale=1.0,
+                     grads=True, n_rows=None, **opts):
+    """Loss of Eq. 16 per listed batch and (grads=True) the flat gradients,
+    shape (n_batches, n_params), in the parameter layout of make_mlp."""
+    o = lbm_train_opts_default(**opts)
+    m, keep = make_mlp(layers, act, in_mean, in_std, out_scale)
+    order = _order(order)
+    n = rows.shape[0] if n_rows is None else n_rows
+    losses = np.zeros(order.size, np.float64)
+    g = np.zeros((order.size, m.n_params), np.float32) if grads else None
+    _check(_lib.load().lbm_nn_loss_grad(c_void_p(_devptr(rows)), int(n),
+                                        order.ctypes.data_as(POINTER(ctypes.c_int32)),
+                                        order.size, byref(o), byref(m), _dptr(losses),
+                                        g.ctypes.data_as(POINTER(c_float)) if grads else None))
+    del keep
+    return (losses, g) if grads else losses
+
+
+def unflatten(flat, like):
+    """Split a flat parameter vector into [(W, b), ...] shaped like ``like``."""
+    out, off = [], 0
+    for W, b in like:
+        nw, nb = int(np.size(W)), int(np.size(b))
+        out.append((np.asarray(flat[off:off + nw]).reshape(np.shape(W)),
+                    np.asarray(flat[off + nw:off + nw + nb])))
+        off += nw + nb
+    return out
 
 
 def lbm_step(sim, n=1):

@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <exception>
@@ -102,6 +103,158 @@ void fft_inplace(std::vector<std::complex<double>>& a) {
 namespace lbm {
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace lbm
+
+namespace {
+
+// Device buffer freed when the scope ends (training calls own their memory).
+struct DevBuf {
+  void* p = nullptr;
+  explicit DevBuf(size_t bytes) { ck(cudaMalloc(&p, bytes ? bytes : 16), "cudaMalloc"); }
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+lbm_status check_train_net(const lbm_mlp* net, int64_t* n_params) {
+  if (!net || !net->params) return fail(LBM_ERR_ARG, "net and net->params must be non-NULL");
+  if (net->n_layers < 1 || net->n_layers > LBM_MLP_MAX_LAYERS)
+    return fail(LBM_ERR_ARG, "n_layers must be 1..4");
+  if (net->sizes[0] != 81 || net->sizes[net->n_layers] != 3)
+    return fail(LBM_ERR_ARG, "the direct-reconstruction net maps 81 inputs to 3 outputs");
+  int64_t np = 0;
+  for (int l = 0; l < net->n_layers; ++l) {
+    if (net->sizes[l + 1] < 1 || (l < net->n_layers - 1 && net->sizes[l + 1] > 64))
+      return fail(LBM_ERR_ARG, "hidden layers must have 1..64 units");
+    np += (int64_t)net->sizes[l] * net->sizes[l + 1] + net->sizes[l + 1];
+  }
+  if (net->n_params != np) return fail(LBM_ERR_ARG, "n_params does not match the layer sizes");
+  if (net->act != 0 && net->act != 1) return fail(LBM_ERR_ARG, "act must be 0 (tanh) or 1 (leaky)");
+  if (!std::isfinite(net->out_scale)) return fail(LBM_ERR_ARG, "out_scale must be finite");
+  for (int64_t k = 0; k < np; ++k)
+    if (!std::isfinite(net->params[k])) return fail(LBM_ERR_ARG, "non-finite network parameter");
+  for (int k = 0; k < 81; ++k) {
+    const float sd = net->in_std ? net->in_std[k] : 1.f;
+    if (!(sd > 0.f) || !std::isfinite(sd)) return fail(LBM_ERR_ARG, "in_std must be > 0");
+    if (net->in_mean && !std::isfinite(net->in_mean[k]))
+      return fail(LBM_ERR_ARG, "in_mean must be finite");
+  }
+  *n_params = np;
+  return LBM_OK;
+}
+
+lbm_status check_train_args(const float* rows, int64_t n_rows, const int32_t* order,
+                            int64_t n_steps, const lbm_train_opts* o) {
+  if (!rows || !order || !o) return fail(LBM_ERR_ARG, "rows, order and opts must be non-NULL");
+  if (o->batch_rows < 1) return fail(LBM_ERR_ARG, "batch_rows must be >= 1");
+  if (n_rows < o->batch_rows) return fail(LBM_ERR_ARG, "n_rows is below one batch");
+  if (n_steps < 0) return fail(LBM_ERR_ARG, "n_steps must be >= 0");
+  const int64_t n_batches = n_rows / o->batch_rows;
+  for (int64_t k = 0; k < n_steps; ++k)
+    if (order[k] < 0 || order[k] >= n_batches) return fail(LBM_ERR_ARG, "batch index out of range");
+  if (!(o->lr > 0.0) || !(o->eps > 0.0) || !(o->beta1 >= 0.0 && o->beta1 < 1.0) ||
+      !(o->beta2 >= 0.0 && o->beta2 < 1.0))
+    return fail(LBM_ERR_ARG, "Adam needs lr > 0, eps > 0, 0 <= beta1, beta2 < 1");
+  if (o->adam_t0 < 0) return fail(LBM_ERR_ARG, "adam_t0 must be >= 0");
+  if (o->max_cluster < 0 || o->max_cluster > 16)
+    return fail(LBM_ERR_ARG, "max_cluster must be 0..16");
+  return LBM_OK;
+}
+
+constexpr int64_t kTrainStepsPerLaunch = 4096;
+
+// Shared part of lbm_nn_train (mode 0) and lbm_nn_loss_grad (mode 1 or 2).
+lbm_status run_training(const float* rows, int64_t n_rows, const int32_t* order, int64_t n_steps,
+                        const lbm_train_opts* o, const lbm_mlp* net, int mode, float* params_out,
+                        float* adam_m, float* adam_v, double* losses, float* grads) {
+  int64_t np = 0;
+  if (lbm_status st = check_train_net(net, &np)) return st;
+  if (lbm_status st = check_train_args(rows, n_rows, order, n_steps, o)) return st;
+  if (n_steps == 0) {
+    if (params_out) memcpy(params_out, net->params, np * sizeof(float));
+    return LBM_OK;
+  }
+  LBM_GUARD_BEGIN
+  cudaStream_t stream = static_cast<cudaStream_t>(o->stream);
+  int dev = 0, smem_limit = 0;
+  ck(cudaGetDevice(&dev), "device");
+  ck(cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
+  lbm::TrainParams p{};
+  p.batch_rows = o->batch_rows;
+  p.n_layers = net->n_layers;
+  for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) p.sizes[l] = l <= net->n_layers ? net->sizes[l] : 0;
+  p.act = net->act;
+  p.out_scale = net->out_scale;
+  p.lr = (float)o->lr;
+  p.beta1 = (float)o->beta1;
+  p.beta2 = (float)o->beta2;
+  p.eps = (float)o->eps;
+  p.mode = mode;
+  p.rows = rows;
+  const int max_c = o->max_cluster > 0 ? o->max_cluster : 16;
+  p.chunk = lbm::train_max_chunk(p.sizes, p.n_layers, (o->batch_rows + max_c - 1) / max_c,
+                                 smem_limit);
+  if (p.chunk <= 0) return fail(LBM_ERR_UNSUPPORTED, "network too large for shared memory");
+  int cluster = lbm::train_cluster_size(p, max_c);
+  if (cluster <= 0) return fail(LBM_ERR_UNSUPPORTED, "no cluster of the training kernel fits");
+  p.chunk = lbm::train_max_chunk(p.sizes, p.n_layers, (o->batch_rows + cluster - 1) / cluster,
+                                 smem_limit);
+  if (p.chunk <= 0) return fail(LBM_ERR_UNSUPPORTED, "network too large for shared memory");
+
+  const int64_t per_launch = std::min<int64_t>(n_steps, kTrainStepsPerLaunch);
+  DevBuf d_params(np * sizeof(float)), d_m(np * sizeof(float)), d_v(np * sizeof(float));
+  DevBuf d_mean(81 * sizeof(float)), d_std(81 * sizeof(float));
+  DevBuf d_order(n_steps * sizeof(int32_t)), d_loss(per_launch * sizeof(double));
+  DevBuf d_grad(mode == 1 ? per_launch * np * sizeof(float) : 16);
+  std::vector<float> mean(81), sd(81);
+  for (int k = 0; k < 81; ++k) {
+    mean[k] = net->in_mean ? net->in_mean[k] : 0.f;
+    sd[k] = net->in_std ? net->in_std[k] : 1.f;
+  }
+  ck(cudaMemcpyAsync(d_params.p, net->params, np * 4, cudaMemcpyHostToDevice, stream), "copy");
+  ck(cudaMemcpyAsync(d_mean.p, mean.data(), 81 * 4, cudaMemcpyHostToDevice, stream), "copy");
+  ck(cudaMemcpyAsync(d_std.p, sd.data(), 81 * 4, cudaMemcpyHostToDevice, stream), "copy");
+  ck(cudaMemcpyAsync(d_order.p, order, n_steps * 4, cudaMemcpyHostToDevice, stream), "copy");
+  if (adam_m) ck(cudaMemcpyAsync(d_m.p, adam_m, np * 4, cudaMemcpyHostToDevice, stream), "copy");
+  else ck(cudaMemsetAsync(d_m.p, 0, np * 4, stream), "memset");
+  if (adam_v) ck(cudaMemcpyAsync(d_v.p, adam_v, np * 4, cudaMemcpyHostToDevice, stream), "copy");
+  else ck(cudaMemsetAsync(d_v.p, 0, np * 4, stream), "memset");
+  p.in_mean = d_mean.as<float>();
+  p.in_std = d_std.as<float>();
+  p.params = d_params.as<float>();
+  p.adam_m = d_m.as<float>();
+  p.adam_v = d_v.as<float>();
+  p.grad_out = d_grad.as<float>();
+  p.loss_log = d_loss.as<double>();
+  for (int64_t k0 = 0; k0 < n_steps; k0 += per_launch) {
+    p.n_steps = std::min(per_launch, n_steps - k0);
+    p.order = d_order.as<int32_t>() + k0;
+    p.adam_t0 = o->adam_t0 + k0;
+    ck(lbm::launch_train(p, cluster, stream), "training launch");
+    if (losses)
+      ck(cudaMemcpyAsync(losses + k0, d_loss.p, p.n_steps * sizeof(double),
+                         cudaMemcpyDeviceToHost, stream), "loss copy");
+    if (mode == 1 && grads)
+      ck(cudaMemcpyAsync(grads + k0 * np, d_grad.p, p.n_steps * np * sizeof(float),
+                         cudaMemcpyDeviceToHost, stream), "grad copy");
+    ck(cudaStreamSynchronize(stream), "training sync");
+  }
+  if (mode == 0) {
+    if (params_out)
+      ck(cudaMemcpy(params_out, d_params.p, np * 4, cudaMemcpyDeviceToHost), "copy");
+    if (adam_m) ck(cudaMemcpy(adam_m, d_m.p, np * 4, cudaMemcpyDeviceToHost), "copy");
+    if (adam_v) ck(cudaMemcpy(adam_v, d_v.p, np * 4, cudaMemcpyDeviceToHost), "copy");
+  }
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -352,6 +505,89 @@ lbm_status lbm_nn_fallbacks(lbm_sim* s, int64_t* count) {
   *count = (int64_t)c;
   return LBM_OK;
   LBM_GUARD_END
+}
+
+// ---- training rows and training (Sec. 3.1) ---------------------------------
+
+lbm_status lbm_capture_plane(lbm_sim* s, int32_t x_t, int32_t every, float* dev_rows,
+                             int64_t cap_rows) {
+  if (lbm_status st = check_sim(s)) return st;
+  if (!dev_rows) {
+    s->cap_every = 0;
+    s->cap_out = nullptr;
+    s->cap_capacity = 0;
+    s->cap_rows = 0;
+    return LBM_OK;
+  }
+  if (x_t < 4 || x_t > s->nx - 2) return fail(LBM_ERR_ARG, "x_t must be in [4, nx-2]");
+  if (every < 1) return fail(LBM_ERR_ARG, "every must be >= 1");
+  if (cap_rows < 0) return fail(LBM_ERR_ARG, "cap_rows must be >= 0");
+  s->cap_x = x_t;
+  s->cap_every = every;
+  s->cap_out = dev_rows;
+  s->cap_capacity = cap_rows;
+  s->cap_rows = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_capture_count(lbm_sim* s, int64_t* rows) {
+  if (lbm_status st = check_sim(s)) return st;
+  if (!rows) return fail(LBM_ERR_ARG, "rows is NULL");
+  *rows = s->cap_rows;
+  return LBM_OK;
+}
+
+
+lbm_status lbm_train_opts_default(lbm_train_opts* o) {
+  if (!o) return fail(LBM_ERR_ARG, "opts is NULL");
+  *o = lbm_train_opts{};
+  o->lr = 1e-5;
+  o->beta1 = 0.9;
+  o->beta2 = 0.999;
+  o->eps = 1e-8;
+  return LBM_OK;
+}
+
+lbm_status lbm_nn_dataset_stats(const float* rows, int64_t n, void* stream, float* in_mean,
+                                float* in_std, float* out_scale) {
+  if (!rows || !in_mean || !in_std || !out_scale) return fail(LBM_ERR_ARG, "NULL argument");
+  if (n < 1) return fail(LBM_ERR_ARG, "n_rows must be >= 1");
+  LBM_GUARD_BEGIN
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nd = lbm::dataset_stats_scratch_doubles();
+  DevBuf scratch(nd * sizeof(double));
+  lbm::dataset_stats(rows, n, scratch.as<double>(), st);
+  ck(cudaGetLastError(), "stats launch");
+  std::vector<double> mv(164);
+  ck(cudaMemcpyAsync(mv.data(), scratch.as<double>() + (nd - 164), 164 * sizeof(double),
+                     cudaMemcpyDeviceToHost, st), "stats copy");
+  ck(cudaStreamSynchronize(st), "stats sync");
+  constexpr double kMinStd = 1e-12;
+  for (int c = 0; c < 81; ++c) {
+    in_mean[c] = (float)mv[c];
+    const double sd = std::sqrt(mv[82 + c]);
+    in_std[c] = (float)(sd < kMinStd ? 1.0 : sd);
+  }
+  const double rs = std::sqrt(mv[82 + 81]);
+  *out_scale = (float)(rs < kMinStd ? 1.0 : rs);
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+lbm_status lbm_nn_train(const float* rows, int64_t n_rows, const int32_t* order, int64_t n_steps,
+                        const lbm_train_opts* opts, const lbm_mlp* net, float* params_out,
+                        float* adam_m, float* adam_v, double* loss_log) {
+  if (!params_out) return fail(LBM_ERR_ARG, "params_out is NULL");
+  return run_training(rows, n_rows, order, n_steps, opts, net, 0, params_out, adam_m, adam_v,
+                      loss_log, nullptr);
+}
+
+lbm_status lbm_nn_loss_grad(const float* rows, int64_t n_rows, const int32_t* order,
+                            int64_t n_batches, const lbm_train_opts* opts, const lbm_mlp* net,
+                            double* losses, float* grads) {
+  if (!losses) return fail(LBM_ERR_ARG, "losses is NULL");
+  return run_training(rows, n_rows, order, n_batches, opts, net, grads ? 1 : 2, nullptr, nullptr,
+                      nullptr, losses, grads);
 }
 
 lbm_status lbm_step(lbm_sim* s, int64_t n) {

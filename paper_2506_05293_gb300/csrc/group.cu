@@ -18,7 +18,8 @@ namespace lbm {
 
 namespace {
 
-constexpr int64_t kGraphChunk = 32;   // steps per captured graph (even)
+constexpr int64_t kGraphChunk = 32;   // steps per captured graph (longest)
+constexpr int64_t kMinGraphChunk = 4; // shorter runs of steps launch directly
 
 void fill_member(const lbm_sim* s, Member& m) {
   memset(&m, 0, sizeof(m));
@@ -252,6 +253,41 @@ void advance_members(Group& g, int64_t n) {
   }
 }
 
+// Steps from step index t (the step t -> t+1) to the next step that some
+// member captures training rows in: 0 = this step, -1 = none pending.
+int64_t steps_to_capture(const Group& g, int64_t t) {
+  int64_t best = -1;
+  for (const lbm_sim* s : g.sims) {
+    if (s->cap_every <= 0 || s->cap_rows + s->ny > s->cap_capacity) continue;
+    const int64_t e = s->cap_every;
+    const int64_t d = (e - (t + 1) % e) % e;
+    if (best < 0 || d < best) best = d;
+  }
+  return best;
+}
+
+// Capture kernels of the members whose capture falls on step t -> t+1; they
+// read the source buffer q before the step kernel runs.
+void enqueue_captures(Group& g, int q, int64_t t) {
+  for (lbm_sim* s : g.sims) {
+    if (s->cap_every <= 0 || (t + 1) % s->cap_every != 0) continue;
+    if (s->cap_rows + s->ny > s->cap_capacity) continue;
+    CaptureParams c{};
+    c.src = s->buf[q];
+    c.solid_bits = s->solid_bits;
+    c.words_per_row = s->words_per_row;
+    c.nx = s->nx;
+    c.ny = s->ny;
+    c.pitch = s->pitch;
+    c.plane = s->plane;
+    c.x_t = s->cap_x;
+    c.out = s->cap_out + s->cap_rows * kRowFloats;
+    launch_capture(s->prec, c, g.stream);
+    ck(cudaGetLastError(), "capture launch");
+    s->cap_rows += s->ny;
+  }
+}
+
 }  // namespace
 
 void* dev_alloc_raw(const lbm_allocator* a, size_t bytes) {
@@ -356,14 +392,19 @@ void group_step(Group& g, int64_t n) {
   while (n > 0) {
     const int q = g.sims[0]->cur;
     const int64_t t = g.sims[0]->t_host;
-    if (use_graphs && n >= kGraphChunk) {
-      cudaGraphExec_t ex = chunk_graph(g, kGraphChunk, q);
+    const int64_t dcap = steps_to_capture(g, t);
+    if (dcap == 0) enqueue_captures(g, q, t);
+    // steps that may run before the next capture
+    const int64_t room = dcap <= 0 ? n : std::min<int64_t>(n, dcap);
+    if (use_graphs && dcap != 0 && room >= kMinGraphChunk) {
+      const int64_t len = std::min<int64_t>(room, kGraphChunk);
+      cudaGraphExec_t ex = chunk_graph(g, len, q);
       group_finalize(g);
       launch_set_t(g.t_base, t, g.stream);
       ck(cudaGetLastError(), "set_t launch");
       ck(cudaGraphLaunch(ex, g.stream), "graph launch");
-      advance_members(g, kGraphChunk);
-      n -= kGraphChunk;
+      advance_members(g, len);
+      n -= len;
     } else {
       enqueue(g, q, t, -1, g.pending);
       advance_members(g, 1);

@@ -119,6 +119,49 @@ void launch_mass(int prec, const void* src, int nx, int ny, int64_t pitch, int64
                  double* partials, int n_partials, double* out, cudaStream_t s);
 void launch_nn_outflow(int prec, const NnParams& p, cudaStream_t s);
 
+// ---- training rows and training (train.cu) ----
+constexpr int kRowFloats = 84;   // 81 inputs of Eq. 15 + f_3, f_6, f_7 at the plane
+
+struct CaptureParams {
+  const void* src;                 // post-collision populations at t (pull source)
+  const uint32_t* solid_bits;
+  int32_t words_per_row;
+  int32_t nx, ny;
+  int64_t pitch, plane;
+  int32_t x_t;
+  float* out;                      // ny rows of kRowFloats
+};
+void launch_capture(int prec, const CaptureParams& p, cudaStream_t s);
+
+void dataset_stats(const float* rows, int64_t n, double* scratch, cudaStream_t s);
+int dataset_stats_scratch_doubles();
+
+struct TrainParams {
+  const float* rows;               // device [n_rows][kRowFloats]
+  const int32_t* order;            // device [n_steps] batch indices
+  int64_t n_steps;
+  int32_t batch_rows;
+  int32_t n_layers;
+  int32_t sizes[LBM_MLP_MAX_LAYERS + 1];
+  int32_t act;
+  const float* in_mean;            // device [81]
+  const float* in_std;             // device [81]
+  float out_scale;
+  float* params;                   // device [n_params], updated in place (mode 0)
+  float* adam_m;                   // device [n_params] (mode 0)
+  float* adam_v;
+  int64_t adam_t0;                 // Adam steps taken before this call
+  float lr, beta1, beta2, eps;
+  int32_t mode;                    // 0 Adam steps, 1 gradients, 2 losses only
+  float* grad_out;                 // device [n_steps][n_params] (mode 1)
+  double* loss_log;                // device [n_steps]
+  int32_t chunk;                   // samples per shared-memory chunk (multiple of 4)
+};
+int train_smem_bytes(const int* sizes, int n_layers, int chunk);
+int train_max_chunk(const int* sizes, int n_layers, int batch_per_cta, int smem_limit);
+int train_cluster_size(const TrainParams& p, int max_cluster);
+cudaError_t launch_train(const TrainParams& p, int cluster, cudaStream_t s);
+
 // message returned by lbm_last_error() on this thread
 void set_last_error(const std::string& msg);
 
@@ -186,6 +229,11 @@ struct lbm_sim {
   double rho_out = 1.0;
   lbm::DevMlp nn;
   double nn_drho = 0.05;
+  // training-row capture (lbm_capture_plane)
+  float* cap_out = nullptr;          // caller's device buffer of cap_capacity rows
+  int64_t cap_capacity = 0;
+  int64_t cap_rows = 0;              // rows written so far
+  int32_t cap_x = 0, cap_every = 0;  // cap_every 0: not capturing
   lbm::Group own;                    // this sim alone
   lbm::Group* last_group = nullptr;  // the group that launched its last step
   int batch_refs = 0;                // batches holding this sim

@@ -78,3 +78,29 @@ def test_strouhal_host_code_matches_oracle(L):
         assert abs(L.lbm_strouhal(cl, D, U) - post.strouhal(cl, D, U)) < 1e-9
     with pytest.raises(L.LbmError):
         L.lbm_strouhal(np.zeros(4), D, U)
+
+
+@pytest.mark.parametrize("bad", [dict(order=[0, 4]), dict(order=[-1]), dict(batch_rows=0),
+                                 dict(lr=0.0), dict(beta1=1.0), dict(max_cluster=17),
+                                 dict(n_rows=10), dict(adam_t0=-1)])
+def test_training_rejects_bad_arguments_before_touching_the_device(L, bad):
+    """Argument checks of lbm_nn_train run on the host before any device call;
+    the rows pointer is never dereferenced here."""
+    from synth import glorot_mlp
+    layers = glorot_mlp([81, 8, 3], 0)
+    kw = dict(batch_rows=16, n_rows=64, order=[0, 1, 3])
+    kw.update(bad)
+    order = kw.pop("order")
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_nn_train(0x1000, order, layers, "tanh", **kw)
+    assert ei.value.status == 1
+
+
+def test_training_rejects_bad_networks(L):
+    from synth import glorot_mlp
+    for sizes in ([80, 8, 3], [81, 8, 4], [81, 65, 3]):
+        with pytest.raises(L.LbmError) as ei:
+            L.lbm_nn_loss_grad(0x1000, [0], glorot_mlp(sizes, 0), "tanh", batch_rows=4, n_rows=8)
+        assert ei.value.status == 1
+    with pytest.raises(L.LbmError):
+        L.lbm_nn_dataset_stats(0x1000, n_rows=0)

@@ -56,7 +56,7 @@ def test_batch_matches_oracle_fp64(L, tiling):
     sims, setups = _make(L, "fp64", stream.cuda_stream)
     b = L.lbm_batch_create(sims)
     L.lbm_batch_set_tiling(b, *tiling)
-    L.lbm_batch_step(b, 45)                      # one 32-step graph chunk + 13 single steps
+    L.lbm_batch_step(b, 45)                      # graph chunks of 32 and 13 steps
     L.lbm_batch_sync(b)
     for i, (s, (kind, init)) in enumerate(zip(sims, setups)):
         nx, ny, tau, coll, u, walls = MEMBERS[i]

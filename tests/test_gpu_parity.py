@@ -264,7 +264,7 @@ def test_every_tiling_gives_the_same_populations(L, precision):
         L.lbm_set_tiling(sim, rows, variant)
         L.lbm_set_geometry(sim, kind)
         L.lbm_init_equilibrium(sim, *init)
-        L.lbm_step(sim, 45)           # one graph chunk of 32 + 13 single steps
+        L.lbm_step(sim, 45)           # graph chunks of 32 and 13 steps
         f = L.lbm_get_populations(sim)
         fx, fy = L.lbm_forces(sim)
         L.lbm_destroy(sim)
