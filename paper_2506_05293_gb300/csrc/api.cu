@@ -1,6 +1,6 @@
 // C ABI of the library (include/lbm.h): argument checking, device memory,
 // streams, CUDA-graph replay of chunks of steps, and host post-processing.
-// Every numerical step of the method runs in the kernels of step.cu and nn.cu.
+// Every numerical step of the method runs in the kernels of step.cu and train.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -463,8 +463,20 @@ lbm_status lbm_set_outflow_nn(lbm_sim* s, const lbm_mlp* net, double fallback_dr
   if (!std::isfinite(net->out_scale)) return fail(LBM_ERR_ARG, "out_scale must be finite");
   for (int64_t k = 0; k < np; ++k)
     if (!std::isfinite(net->params[k])) return fail(LBM_ERR_ARG, "non-finite network parameter");
-  std::vector<float> blob(np + 2 * 81);
-  memcpy(blob.data(), net->params, np * sizeof(float));
+  // device blob: per layer W transposed (row k = input k's weights to every
+  // unit) then b; then in_mean, in_std; padded to a multiple of 4 elements
+  const int64_t blob_n = (np + 2 * 81 + 3) / 4 * 4;
+  std::vector<float> blob(blob_n, 0.f);
+  {
+    int64_t off = 0;
+    for (int l = 0; l < net->n_layers; ++l) {
+      const int ni = net->sizes[l], no = net->sizes[l + 1];
+      for (int j = 0; j < no; ++j)
+        for (int k = 0; k < ni; ++k) blob[off + (int64_t)k * no + j] = net->params[off + (int64_t)j * ni + k];
+      for (int j = 0; j < no; ++j) blob[off + (int64_t)ni * no + j] = net->params[off + (int64_t)ni * no + j];
+      off += (int64_t)ni * no + no;
+    }
+  }
   for (int k = 0; k < 81; ++k) {
     blob[np + k] = net->in_mean ? net->in_mean[k] : 0.f;
     const float sd = net->in_std ? net->in_std[k] : 1.f;
@@ -472,7 +484,7 @@ lbm_status lbm_set_outflow_nn(lbm_sim* s, const lbm_mlp* net, double fallback_dr
     blob[np + 81 + k] = sd;
   }
   LBM_GUARD_BEGIN
-  if (!s->nn.params_f || s->nn.n_params != np) {
+  if (!s->nn.params_f || s->nn.blob_elems != (int32_t)blob_n) {
     s->nn.params_f = (float*)dev_alloc(s, blob.size() * sizeof(float));
     s->nn.params_d = (double*)dev_alloc(s, blob.size() * sizeof(double));
   }
@@ -486,6 +498,7 @@ lbm_status lbm_set_outflow_nn(lbm_sim* s, const lbm_mlp* net, double fallback_dr
   for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) s->nn.sizes[l] = l <= net->n_layers ? net->sizes[l] : 0;
   s->nn.act = net->act;
   s->nn.n_params = np;
+  s->nn.blob_elems = (int32_t)blob_n;
   s->nn.out_scale = net->out_scale;
   s->nn_drho = fallback_drho;
   s->east = lbm::EAST_EXTERNAL;

@@ -4,7 +4,7 @@
 // the current tiling), the force partials, the step index used by captured
 // graphs, and the CUDA graphs of chunks of steps.  A single lbm_sim is a group
 // of one; lbm_batch is a group of many sims of different sizes and parameters
-// in lockstep.  Every numerical step runs in step.cu / nn.cu.
+// in lockstep.  Every numerical step runs in step.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -64,7 +64,19 @@ void fill_member(const lbm_sim* s, Member& m) {
   m.ring = s->ring;
   m.ring_cap = s->ring_cap;
   m.status = s->status;
+  if (s->east == EAST_EXTERNAL && s->outflow == LBM_OUTFLOW_NN) {
+    // FP32 and FP16 storage compute in FP32: both use the FP32 blob
+    m.nn_net = s->prec == LBM_FP64 ? (const void*)s->nn.params_d : (const void*)s->nn.params_f;
+    m.nn_fallbacks = s->nn_fallbacks;
+    m.nn_out_scale = s->nn.out_scale;
+    m.nn_drho = s->nn_drho;
+    m.nn_layers = s->nn.n_layers;
+    m.nn_act = s->nn.act;
+    for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) m.nn_sizes[l] = s->nn.sizes[l];
+  }
 }
+
+bool has_nn(const lbm_sim* s) { return s->east == EAST_EXTERNAL && s->outflow == LBM_OUTFLOW_NN; }
 
 bool table_stale(const Group& g) {
   if (g.built_versions.size() != g.sims.size()) return true;
@@ -86,16 +98,42 @@ void build_table(Group& g) {
     ms[(size_t)k].strip_count = strips;
     strip_total += strips;
   }
+  // network blocks first in the grid, one range per member with a network outflow
+  std::vector<int32_t> nb;
+  for (int k = 0; k < n; ++k) {
+    if (!has_nn(g.sims[k])) continue;
+    ms[(size_t)k].nn_first = (int32_t)nb.size();
+    const int c = step_nn_blocks(g.sims[k]->ny, g.variant);
+    for (int j = 0; j < c; ++j) nb.push_back(k);
+  }
+  g.nn_blocks = (int)nb.size();
+  if (n > 1 && !nb.empty()) {
+    if ((int)nb.size() > g.nn_cap) {
+      const lbm_allocator* a = g.sims[0]->have_alloc ? &g.sims[0]->alloc : nullptr;
+      if (g.d_nn_block_member) {
+        ck(cudaStreamSynchronize(g.stream), "table sync");
+        dev_free_raw(a, g.d_nn_block_member);
+        g.owned.erase(std::remove(g.owned.begin(), g.owned.end(), (void*)g.d_nn_block_member),
+                      g.owned.end());
+      }
+      g.d_nn_block_member = (int32_t*)dev_alloc_raw(a, nb.size() * sizeof(int32_t));
+      g.owned.push_back(g.d_nn_block_member);
+      g.nn_cap = (int)nb.size();
+    }
+    ck(cudaMemcpyAsync(g.d_nn_block_member, nb.data(), nb.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, g.stream), "network table copy");
+  }
+  // resident capacity left to the stream-and-collide blocks
+  const int room = std::max(1, g.max_blocks_v[g.variant] - g.nn_blocks - n);
   if (g.persistent) {
-    const int cap = g.max_blocks_v[g.variant];
+    const int cap = room;
     g.blocks = std::min(strip_total, cap);
     ms[0].part_first = 0;
     ms[0].part_count = g.blocks;
   } else if (step_variant_streams(g.variant)) {
     // streaming staged kernel: a resident-sized grid shared among the members
     // in proportion to their strips; each member's blocks are contiguous
-    const int cap = std::max(1, g.max_blocks_v[g.variant]);
-    const int G = std::min(strip_total, cap);
+    const int G = std::min(strip_total, room);
     std::vector<int> gk((size_t)n);
     int used = 0;
     for (int k = 0; k < n; ++k) {
@@ -165,6 +203,8 @@ StepParams params(const Group& g, int q) {
   p.persistent = g.persistent ? 1 : 0;
   p.partials = g.partials;
   p.partial_stride = g.partial_stride;
+  p.nn_blocks = g.nn_blocks;
+  p.nn_block_member = g.d_nn_block_member;
   return p;
 }
 
@@ -182,37 +222,6 @@ void enqueue(Group& g, int q, int64_t t, int graph_k, bool reduce_prev) {
   }
   p.reduce_prev = reduce_prev ? 1 : 0;
   launch_step(g.prec, g.coll_mode, p, g.variant, g.blocks, g.stream);
-  for (lbm_sim* s : g.sims) {
-    if (s->east == EAST_EXTERNAL && s->outflow == LBM_OUTFLOW_NN) {
-      NnParams n{};
-      n.src = s->buf[q];
-      n.dst = s->buf[1 - q];
-      n.nx = s->nx;
-      n.ny = s->ny;
-      n.pitch = s->pitch;
-      n.plane = s->plane;
-      n.solid_bits = s->solid_bits;
-      n.words_per_row = s->words_per_row;
-      n.net = s->prec == LBM_FP64 ? (const void*)s->nn.params_d : (const void*)s->nn.params_f;
-      n.n_layers = s->nn.n_layers;
-      for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) n.sizes[l] = s->nn.sizes[l];
-      n.act = s->nn.act;
-      n.out_scale = s->nn.out_scale;
-      n.rho_out = s->rho_out;
-      n.fallback_drho = s->nn_drho;
-      Member m;
-      fill_member(s, m);
-      n.omega = m.omega;
-      n.mrt_se = m.mrt_se;
-      n.mrt_seps = m.mrt_seps;
-      n.mrt_sq = m.mrt_sq;
-      n.mrt_snu = m.mrt_snu;
-      n.collision = s->cfg.collision;
-      n.fallbacks = s->nn_fallbacks;
-      n.status = s->status;
-      launch_nn_outflow(s->prec, n, g.stream);
-    }
-  }
   ck(cudaGetLastError(), "step launch");
 }
 

@@ -42,6 +42,15 @@ struct Member {
   double* ring;           // 2 doubles per step
   int64_t ring_cap;
   int* status;
+  // NN direct-reconstruction outflow (east_mode EAST_EXTERNAL), else unused
+  const void* nn_net;     // compute-precision blob: per layer W^T then b, in_mean, in_std
+  unsigned long long* nn_fallbacks;
+  double nn_out_scale;
+  double nn_drho;
+  int32_t nn_layers;
+  int32_t nn_act;
+  int32_t nn_sizes[LBM_MLP_MAX_LAYERS + 1];
+  int32_t nn_first;       // first network block of this member in the launch
 };
 
 // Parameters of one launch of a step kernel.
@@ -58,6 +67,8 @@ struct StepParams {
   int32_t reduce_prev;           // extra blocks finalise the previous step's forces
   double* partials;              // [2 parities][partial_stride][2]
   int32_t partial_stride;
+  int32_t nn_blocks;             // network blocks (the first blocks of the grid)
+  const int32_t* nn_block_member;  // member of each network block (multi-member)
   Member m0;                     // copy of the only member when n_members == 1: the
                                  // kernels then read it from the parameter bank
 };
@@ -68,30 +79,12 @@ struct DevMlp {
   int sizes[LBM_MLP_MAX_LAYERS + 1] = {0};
   int act = 0;
   int64_t n_params = 0;
-  float* params_f = nullptr;   // W, b per layer, then in_mean[81], in_std[81]
+  int32_t blob_elems = 0;      // per layer W^T then b, then in_mean[81], in_std[81], padded
+  float* params_f = nullptr;
   double* params_d = nullptr;
   float out_scale = 1.f;
 };
 
-struct NnParams {
-  const void* src;
-  void* dst;
-  int32_t nx, ny;
-  int64_t pitch, plane;
-  const uint32_t* solid_bits;
-  int32_t words_per_row;
-  const void* net;        // float* or double* blob: layers, in_mean, in_std
-  int32_t n_layers;
-  int32_t sizes[LBM_MLP_MAX_LAYERS + 1];
-  int32_t act;
-  double out_scale;
-  double rho_out, fallback_drho;
-  double omega;
-  double mrt_se, mrt_seps, mrt_sq, mrt_snu;
-  int32_t collision;
-  unsigned long long* fallbacks;
-  int* status;
-};
 
 // launches blocks + n_members blocks: the extra ones finalise the previous
 // step's forces; coll 0 BGK, 1 MRT, 2 per member
@@ -100,7 +93,10 @@ void launch_step(int prec, int coll, const StepParams& p, int variant, int block
 // forces of step tt from the block partials into each member's ring
 void launch_finalize_force(const StepParams& p, int64_t tt, cudaStream_t s);
 void launch_set_t(int64_t* t_base, int64_t value, cudaStream_t s);
+void launch_step_nn(int prec, int coll, const StepParams& p, int variant, int blocks,
+                    cudaStream_t s);   // launches with network blocks (step_nn.cu)
 int step_strips(int nx, int ny, int rows);
+int step_nn_blocks(int ny, int variant);  // network blocks that one member's east column needs
 bool step_variant_is_bulk(int variant);
 bool step_variant_streams(int variant);   // staged variant on a resident-sized grid
 int step_variants();
@@ -117,7 +113,6 @@ void launch_import(int prec, void* dst, int nx, int ny, int64_t pitch, int64_t p
                    const double* f_in, cudaStream_t s);
 void launch_mass(int prec, const void* src, int nx, int ny, int64_t pitch, int64_t plane,
                  double* partials, int n_partials, double* out, cudaStream_t s);
-void launch_nn_outflow(int prec, const NnParams& p, cudaStream_t s);
 
 // ---- training rows and training (train.cu) ----
 constexpr int kRowFloats = 84;   // 81 inputs of Eq. 15 + f_3, f_6, f_7 at the plane
@@ -184,6 +179,9 @@ struct Group {
   Member* d_members = nullptr;   // device launch table
   Member h_member0{};            // host copy of member 0 (single-member launches)
   int32_t* d_strip_member = nullptr;
+  int32_t* d_nn_block_member = nullptr;   // member of each network block
+  int nn_cap = 0;                // entries of d_nn_block_member
+  int nn_blocks = 0;             // network blocks of the current table
   double* partials = nullptr;    // [2][partial_stride][2]
   int partial_stride = 0;
   int64_t* t_base = nullptr;

@@ -1,0 +1,40 @@
+// The step kernels with fused network blocks (NN direct-reconstruction
+// outflow, Sec. 3.1, Eq. 15): the same templates as step.cu, instantiated
+// with the network dispatch compiled in, in a translation unit of their own
+// so that launches without a network outflow run kernels without its code.
+#include "step_kernels.cuh"
+
+namespace lbm {
+
+namespace {
+
+template <typename S, int COLL>
+void set_bulk_smem_attr() {
+  using R = typename Compute<S>::R;
+  static bool done = false;
+  if (done) return;
+  const size_t ring = step_bulk_smem(prec_of<S>(), kBulkSlots);
+  const size_t nn = nn_smem_bytes<R>(kBulkThreads / 32);
+  cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(ring > nn ? ring : nn));
+  done = true;
+}
+
+template <typename S>
+void launch_nn_c(int coll, const StepParams& p, int variant, int blocks, cudaStream_t s) {
+  if (coll == LBM_BGK) set_bulk_smem_attr<S, 0>();
+  else if (coll == LBM_MRT) set_bulk_smem_attr<S, 1>();
+  else set_bulk_smem_attr<S, 2>();
+  launch_c<S, true>(coll, p, variant, blocks, s);
+}
+
+}  // namespace
+
+void launch_step_nn(int prec, int coll, const StepParams& p, int variant, int blocks,
+                    cudaStream_t s) {
+  if (prec == LBM_FP64) launch_nn_c<double>(coll, p, variant, blocks, s);
+  else if (prec == LBM_FP32) launch_nn_c<float>(coll, p, variant, blocks, s);
+  else launch_nn_c<__half>(coll, p, variant, blocks, s);
+}
+
+}  // namespace lbm

@@ -1,0 +1,216 @@
+"""The truncation study of Sec. 3 through the C ABI: a long-domain run of the
+cylinder (Fig. 2 geometry) that also captures training rows at the truncation
+plane, GPU training of the direct-reconstruction network (Eq. 16), and
+truncated runs with the Zou & He outflow and with the network, scored against
+the long-domain run by the errors of C_D mean, C_L RMS and St (Sec. 2.3).
+
+Every step runs in the CUDA library; this module only sequences calls.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import api as L
+
+
+@dataclass
+class Study:
+    D: int = 40                      # cylinder diameter (lattice units)
+    re: float = 100.0
+    collision: str = "bgk"
+    u: float = 0.05                  # inlet velocity
+    height_d: float = 16.0           # lattice height in D
+    centre_d: float = 8.0            # cylinder centre, D from the inlet
+    long_wake_d: float = 32.0        # long (reference) domain: wake length in D
+    short_wake_d: float = 4.0        # truncated domain: wake length in D
+    zh_wakes_d: tuple = (8.0, 16.0)  # longer Zou & He domains (cost of equal accuracy)
+    t_trans: int = 150_000           # steps before the statistics window
+    t_stat: int = 32_768             # steps of the statistics window
+    t_restart_skip: int = 16_384     # restarted runs: steps before their window
+    every: int = 10                  # capture every n steps
+    capture_from: int = 0            # first capture step of the long run
+    hidden: tuple = (64, 64)
+    epochs: int = 30
+    lr: float = 1e-3
+    train_frac: float = 0.9          # batches (captured columns) used for training
+    seed: int = 1
+    v_pert_amp: float = 1e-3
+    fallback_drho: float = 0.05
+    precision: str = "fp32"
+    stream: int = 0
+    timings: dict = field(default_factory=dict)
+
+    @property
+    def ny(self):
+        return int(round(self.height_d * self.D))
+
+    @property
+    def nx_long(self):
+        return int(round((self.centre_d + self.long_wake_d) * self.D))
+
+    @property
+    def nx_short(self):
+        return int(round((self.centre_d + self.short_wake_d) * self.D))
+
+    def nx_for(self, wake_d):
+        return int(round((self.centre_d + wake_d) * self.D))
+
+    @property
+    def tau(self):
+        return 3.0 * self.u * self.D / self.re + 0.5
+
+
+def cylinder_kind(nx, ny, xc, yc, d):
+    """Cell kinds of a cylinder of diameter d at (xc, yc): a node is solid iff
+    its squared distance to the centre is at most (d/2)^2."""
+    y, x = np.mgrid[0:ny, 0:nx]
+    return (((x - xc) ** 2 + (y - yc) ** 2) <= (d / 2.0) ** 2).astype(np.uint8)
+
+
+def make_sim(st: Study, nx):
+    kind = cylinder_kind(nx, st.ny, st.centre_d * st.D, st.ny / 2.0, st.D)
+    cfg = L.lbm_config_default(nx=nx, ny=st.ny, tau=st.tau, collision=st.collision,
+                               precision=st.precision, u_in=st.u, v_pert_amp=st.v_pert_amp,
+                               seed=st.seed, stream=st.stream)
+    s = L.lbm_create(cfg)
+    L.lbm_set_geometry(s, kind)
+    L.lbm_init_equilibrium(s, None, np.where(kind == 0, st.u, 0.0), None)
+    return s
+
+
+def coefficients(st: Study, fx, fy):
+    """C_D mean, C_L RMS (about its mean) and St of a force window (Eq. 12 with
+    rho = 1, U = inlet velocity, reference length D)."""
+    q = 0.5 * st.u * st.u * st.D
+    cd, cl = fx / q, fy / q
+    return {"cd": float(cd.mean()), "cl_rms": float(np.sqrt(np.mean((cl - cl.mean()) ** 2))),
+            "st": float(L.lbm_strouhal(cl, st.D, st.u))}
+
+
+def _window(st, sim, skip, n):
+    L.lbm_step(sim, skip)
+    L.lbm_sync(sim)
+    L.lbm_forces(sim)                  # drop the series before the window
+    L.lbm_step(sim, n)
+    L.lbm_sync(sim)
+    return coefficients(st, *L.lbm_forces(sim))
+
+
+def long_run(st: Study, rows):
+    """Reference run on the long domain.  Captures rows at the truncation
+    plane x_t = nx_short - 1 into the CUDA tensor ``rows``.  Returns the
+    reference coefficients, the number of rows and the developed populations
+    at t_trans (for restarts)."""
+    t0 = time.perf_counter()
+    s = make_sim(st, st.nx_long)
+    L.lbm_step(s, st.capture_from)
+    L.lbm_capture_plane(s, st.nx_short - 1, st.every, rows)
+    L.lbm_step(s, st.t_trans - st.capture_from)
+    L.lbm_sync(s)
+    L.lbm_forces(s)
+    f_dev = L.lbm_get_populations(s)
+    L.lbm_step(s, st.t_stat)
+    L.lbm_sync(s)
+    ref = coefficients(st, *L.lbm_forces(s))
+    n_rows = L.lbm_capture_count(s)
+    L.lbm_capture_plane(s, 0, 0, None)
+    L.lbm_destroy(s)
+    st.timings["long_run_s"] = time.perf_counter() - t0
+    return ref, n_rows, f_dev
+
+
+def capture_rows_needed(st: Study):
+    return ((st.t_trans + st.t_stat - st.capture_from) // st.every + 1) * st.ny
+
+
+def train(st: Study, rows, n_rows, init_layers):
+    """Normalisation from the training batches, then Adam over seeded
+    shuffled epochs.  Returns (layers, mean, std, scale, train/val losses)."""
+    ny = st.ny
+    n_b = n_rows // ny
+    n_train = max(1, int(n_b * st.train_frac))
+    mean, std, scale = L.lbm_nn_dataset_stats(rows, n_rows=n_train * ny)
+    rng = np.random.default_rng(st.seed + 17)
+    order = np.concatenate([rng.permutation(n_train) for _ in range(st.epochs)]).astype(np.int32)
+    t0 = time.perf_counter()
+    layers, _, _, losses = L.lbm_nn_train(rows, order, init_layers, "tanh", mean, std, scale,
+                                          n_rows=n_rows, batch_rows=ny, lr=st.lr,
+                                          stream=st.stream)
+    st.timings["train_s"] = time.perf_counter() - t0
+    st.timings["train_steps"] = int(order.size)
+    val_b = np.arange(n_train, n_b) if n_b > n_train else np.arange(n_train)
+    val = L.lbm_nn_loss_grad(rows, val_b, layers, "tanh", mean, std, scale, grads=False,
+                             n_rows=n_rows, batch_rows=ny, stream=st.stream)
+    zero = [(np.zeros_like(W), np.zeros_like(b)) for W, b in layers]
+    val0 = L.lbm_nn_loss_grad(rows, val_b, zero, "tanh", mean, std, scale, grads=False,
+                              n_rows=n_rows, batch_rows=ny, stream=st.stream)
+    info = {"train_loss_last_epoch": float(losses[-n_train:].mean()),
+            "val_loss": float(val.mean()), "val_loss_zero_gradient": float(val0.mean())}
+    return layers, mean, std, scale, info
+
+
+def truncated_runs(st: Study, ref, net, f_dev, starts=("rest", "restart")):
+    """Zou & He and NN outflow on the truncated domain, from rest (the same
+    start as the reference) and restarted from the reference's developed
+    state cropped to the truncated domain; then Zou & He from rest on the
+    longer domains of zh_wakes_d.  Errors are relative to ref; ms_per_step
+    is the wall time of the run divided by its steps."""
+    layers, mean, std, scale = net
+    out = {}
+
+    def one(name, nx, kind, start):
+        t0 = time.perf_counter()
+        s = make_sim(st, nx)
+        if kind == "nn":
+            L.lbm_set_outflow_nn(s, layers, "tanh", mean, std, scale, st.fallback_drho)
+        if start == "restart":
+            L.lbm_set_populations(s, np.ascontiguousarray(f_dev[:, :, :nx]))
+            skip = st.t_restart_skip
+        else:
+            skip = st.t_trans
+        r = _window(st, s, skip, st.t_stat)
+        r["err"] = {k: abs(r[k] - ref[k]) / abs(ref[k]) for k in ref}
+        if kind == "nn":
+            r["fallbacks"] = L.lbm_nn_fallbacks(s)
+        r["nx"] = nx
+        r["ms_per_step"] = (time.perf_counter() - t0) * 1e3 / (skip + st.t_stat)
+        L.lbm_destroy(s)
+        out[name] = r
+
+    for start in starts:
+        for kind in ("zouhe", "nn"):
+            one(f"{kind}_{start}", st.nx_short, kind, start)
+    for w in st.zh_wakes_d:
+        one(f"zouhe_rest_wake{w:g}D", st.nx_for(w), "zouhe", "rest")
+    return out
+
+
+def glorot_layers(sizes, seed):
+    """Glorot-uniform weights and zero biases, float32 (seeded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n_in, n_out in zip(sizes[:-1], sizes[1:]):
+        a = np.sqrt(6.0 / (n_in + n_out))
+        out.append((rng.uniform(-a, a, (n_out, n_in)).astype(np.float32),
+                    np.zeros(n_out, np.float32)))
+    return out
+
+
+def run_study(st: Study, starts=("rest", "restart")):
+    """The whole study; returns a JSON-ready dict."""
+    import torch
+    rows = torch.zeros((capture_rows_needed(st), 84), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    ref, n_rows, f_dev = long_run(st, rows)
+    init = glorot_layers([81, *st.hidden, 3], st.seed)
+    layers, mean, std, scale, info = train(st, rows, n_rows, init)
+    del rows
+    runs = truncated_runs(st, ref, (layers, mean, std, scale), f_dev, starts)
+    return {"D": st.D, "Re": st.re, "collision": st.collision,
+            "nx_long": st.nx_long, "nx_short": st.nx_short, "ny": st.ny,
+            "t_trans": st.t_trans, "t_stat": st.t_stat, "rows": int(n_rows),
+            "reference": ref, "training": info, "runs": runs,
+            "timings": dict(st.timings)}
