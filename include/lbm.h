@@ -145,6 +145,27 @@ typedef struct {
 lbm_status lbm_set_outflow_nn(lbm_sim* sim, const lbm_mlp* net, double fallback_drho);
 lbm_status lbm_nn_fallbacks(lbm_sim* sim, int64_t* count);
 
+/* Characteristic outflow (Sec. 4, Eqs. 17-28).  For every east fluid node
+ * (L, y), L = nx - 1, each step: rho, u, v (p = rho/3) of the state at t at
+ * (L, y), (L-1, y), (L-2, y), (L, y-1), (L, y+1); d/dx one-sided second order
+ * over L, L-1, L-2; d/dy central with y periodic (first order towards the
+ * fluid next to a solid row, 0 between two solid rows); wave amplitudes
+ * L5 = (u + c_s)(p_x + rho c_s u_x), L3 = u v_x and transverse terms T1, T3,
+ * T5 (Eqs. 20-25, with d rho/dx read as dp/dx); the incoming amplitude
+ * L1 = kappa1 (p - rho_out/3) - kappa2 T1 + T1 (Eq. 26, T1_exact = 0) with
+ * kappa1 = sigma (1 - mach^2) c_s / length (Eq. 27; length 0 = nx); one Euler
+ * step of Eqs. 17-19 gives the prescribed (rho, u, v) at t+1; the unknowns
+ * 3, 6, 7 follow by Zou & He with that state, then f_0 += rho - (rho0 +
+ * 2 rho+)/(1 + u) (Eq. 28), or, with exact_mass = 1, += rho (1 + u) - (rho0 +
+ * 2 rho+), which makes the node density exactly rho.  The node then collides.
+ * tuner (nullable, host memory, copied): an MLP of 1..3 layers mapping the six
+ * derivatives (p_x, u_x, v_x, p_y, u_y, v_y), z-scored by in_mean / in_std, to
+ * 1 or 2 outputs s (hidden layers of at most 32 units; out_scale ignored):
+ * sigma is then sigma * sigmoid(s_0) per node and, with a second output,
+ * kappa2 is kappa2 * sigmoid(s_1).  Needs nx >= 4 and an open x direction. */
+lbm_status lbm_set_outflow_cbc(lbm_sim* sim, double sigma, double kappa2, double mach,
+                               double length, const lbm_mlp* tuner, int32_t exact_mass);
+
 /* ---- Training data and training of the direct-reconstruction network ----
  * (Sec. 3.1: the network learns, from long-domain runs, the populations 3, 6,
  * 7 that cross a truncation plane; loss Eq. 16.)

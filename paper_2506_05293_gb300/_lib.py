@@ -57,6 +57,8 @@ SIGNATURES = {
     "lbm_set_outflow_zouhe": (c_int, [c_void_p, c_double]),
     "lbm_set_outflow_nn": (c_int, [c_void_p, POINTER(LbmMlp), c_double]),
     "lbm_nn_fallbacks": (c_int, [c_void_p, POINTER(c_int64)]),
+    "lbm_set_outflow_cbc": (c_int, [c_void_p, c_double, c_double, c_double, c_double,
+                                    POINTER(LbmMlp), c_int32]),
     "lbm_capture_plane": (c_int, [c_void_p, c_int32, c_int32, c_void_p, c_int64]),
     "lbm_capture_count": (c_int, [c_void_p, POINTER(c_int64)]),
     "lbm_nn_dataset_stats": (c_int, [c_void_p, c_int64, c_void_p, POINTER(c_float),

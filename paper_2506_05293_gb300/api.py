@@ -141,6 +141,19 @@ def lbm_set_outflow_nn(sim, layers, act="tanh", in_mean=None, in_std=None, out_s
     del keep
 
 
+def lbm_set_outflow_cbc(sim, sigma=0.0, kappa2=0.0, mach=0.0, length=0.0, tuner=None,
+                        act="leaky", in_mean=None, in_std=None, exact_mass=False):
+    """Characteristic outflow; ``tuner`` is [(W, b), ...] mapping 6 -> 1 or 2."""
+    keep = None
+    m = None
+    if tuner is not None:
+        m, keep = make_mlp(tuner, act, in_mean, in_std, 1.0)
+    _check(_lib.load().lbm_set_outflow_cbc(sim.handle, float(sigma), float(kappa2), float(mach),
+                                           float(length), byref(m) if m is not None else None,
+                                           int(bool(exact_mass))))
+    del keep
+
+
 def lbm_nn_fallbacks(sim):
     c = c_int64()
     _check(_lib.load().lbm_nn_fallbacks(sim.handle, byref(c)))

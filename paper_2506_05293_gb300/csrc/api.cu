@@ -256,6 +256,56 @@ lbm_status run_training(const float* rows, int64_t n_rows, const int32_t* order,
 
 }  // namespace
 
+namespace {
+
+// Copy a network to the device as the blob the boundary blocks read: per
+// layer W transposed (row k = input k's weights to every unit) then b; then
+// in_mean[n_in], in_std[n_in]; padded to a multiple of 4 elements; FP32 and
+// FP64 copies.  Layer sizes are checked by the caller.
+lbm_status upload_net(lbm_sim* s, const lbm_mlp* net, int n_in, int64_t np) {
+  for (int64_t k = 0; k < np; ++k)
+    if (!std::isfinite(net->params[k])) return fail(LBM_ERR_ARG, "non-finite network parameter");
+  const int64_t blob_n = (np + 2 * n_in + 3) / 4 * 4;
+  std::vector<float> blob(blob_n, 0.f);
+  int64_t off = 0;
+  for (int l = 0; l < net->n_layers; ++l) {
+    const int ni = net->sizes[l], no = net->sizes[l + 1];
+    for (int j = 0; j < no; ++j)
+      for (int k = 0; k < ni; ++k)
+        blob[off + (int64_t)k * no + j] = net->params[off + (int64_t)j * ni + k];
+    for (int j = 0; j < no; ++j) blob[off + (int64_t)ni * no + j] = net->params[off + (int64_t)ni * no + j];
+    off += (int64_t)ni * no + no;
+  }
+  for (int k = 0; k < n_in; ++k) {
+    blob[np + k] = net->in_mean ? net->in_mean[k] : 0.f;
+    const float sd = net->in_std ? net->in_std[k] : 1.f;
+    if (!(sd > 0.f) || !std::isfinite(sd)) return fail(LBM_ERR_ARG, "in_std must be > 0");
+    if (!std::isfinite(blob[np + k])) return fail(LBM_ERR_ARG, "in_mean must be finite");
+    blob[np + n_in + k] = sd;
+  }
+  LBM_GUARD_BEGIN
+  if (!s->nn.params_f || s->nn.blob_elems != (int32_t)blob_n) {
+    s->nn.params_f = (float*)dev_alloc(s, blob.size() * sizeof(float));
+    s->nn.params_d = (double*)dev_alloc(s, blob.size() * sizeof(double));
+  }
+  std::vector<double> blob_d(blob.begin(), blob.end());
+  ck(cudaMemcpyAsync(s->nn.params_f, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice,
+                     s->stream), "net copy");
+  ck(cudaMemcpyAsync(s->nn.params_d, blob_d.data(), blob_d.size() * 8, cudaMemcpyHostToDevice,
+                     s->stream), "net copy");
+  ck(cudaStreamSynchronize(s->stream), "net sync");
+  s->nn.n_layers = net->n_layers;
+  for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) s->nn.sizes[l] = l <= net->n_layers ? net->sizes[l] : 0;
+  s->nn.act = net->act;
+  s->nn.n_params = np;
+  s->nn.blob_elems = (int32_t)blob_n;
+  s->nn.out_scale = net->out_scale;
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* lbm_last_error(void) { return g_err.c_str(); }
@@ -461,51 +511,53 @@ lbm_status lbm_set_outflow_nn(lbm_sim* s, const lbm_mlp* net, double fallback_dr
   if (net->act != 0 && net->act != 1) return fail(LBM_ERR_ARG, "act must be 0 (tanh) or 1 (leaky)");
   if (!(fallback_drho > 0.0)) return fail(LBM_ERR_ARG, "fallback_drho must be > 0");
   if (!std::isfinite(net->out_scale)) return fail(LBM_ERR_ARG, "out_scale must be finite");
-  for (int64_t k = 0; k < np; ++k)
-    if (!std::isfinite(net->params[k])) return fail(LBM_ERR_ARG, "non-finite network parameter");
-  // device blob: per layer W transposed (row k = input k's weights to every
-  // unit) then b; then in_mean, in_std; padded to a multiple of 4 elements
-  const int64_t blob_n = (np + 2 * 81 + 3) / 4 * 4;
-  std::vector<float> blob(blob_n, 0.f);
-  {
-    int64_t off = 0;
-    for (int l = 0; l < net->n_layers; ++l) {
-      const int ni = net->sizes[l], no = net->sizes[l + 1];
-      for (int j = 0; j < no; ++j)
-        for (int k = 0; k < ni; ++k) blob[off + (int64_t)k * no + j] = net->params[off + (int64_t)j * ni + k];
-      for (int j = 0; j < no; ++j) blob[off + (int64_t)ni * no + j] = net->params[off + (int64_t)ni * no + j];
-      off += (int64_t)ni * no + no;
-    }
-  }
-  for (int k = 0; k < 81; ++k) {
-    blob[np + k] = net->in_mean ? net->in_mean[k] : 0.f;
-    const float sd = net->in_std ? net->in_std[k] : 1.f;
-    if (!(sd > 0.f) || !std::isfinite(sd)) return fail(LBM_ERR_ARG, "in_std must be > 0");
-    blob[np + 81 + k] = sd;
-  }
-  LBM_GUARD_BEGIN
-  if (!s->nn.params_f || s->nn.blob_elems != (int32_t)blob_n) {
-    s->nn.params_f = (float*)dev_alloc(s, blob.size() * sizeof(float));
-    s->nn.params_d = (double*)dev_alloc(s, blob.size() * sizeof(double));
-  }
-  std::vector<double> blob_d(blob.begin(), blob.end());
-  ck(cudaMemcpyAsync(s->nn.params_f, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice,
-                     s->stream), "net copy");
-  ck(cudaMemcpyAsync(s->nn.params_d, blob_d.data(), blob_d.size() * 8, cudaMemcpyHostToDevice,
-                     s->stream), "net copy");
-  ck(cudaStreamSynchronize(s->stream), "net sync");
-  s->nn.n_layers = net->n_layers;
-  for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) s->nn.sizes[l] = l <= net->n_layers ? net->sizes[l] : 0;
-  s->nn.act = net->act;
-  s->nn.n_params = np;
-  s->nn.blob_elems = (int32_t)blob_n;
-  s->nn.out_scale = net->out_scale;
+  if (lbm_status st = upload_net(s, net, 81, np)) return st;
   s->nn_drho = fallback_drho;
   s->east = lbm::EAST_EXTERNAL;
   s->outflow = LBM_OUTFLOW_NN;
   s->version++;
   return LBM_OK;
-  LBM_GUARD_END
+}
+
+lbm_status lbm_set_outflow_cbc(lbm_sim* s, double sigma, double kappa2, double mach, double length,
+                               const lbm_mlp* tuner, int32_t exact_mass) {
+  if (lbm_status st = check_sim(s)) return st;
+  if (s->cfg.x_periodic) return fail(LBM_ERR_STATE, "x is periodic: there is no outflow");
+  if (s->nx < 4) return fail(LBM_ERR_ARG, "the characteristic outflow needs nx >= 4");
+  if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(LBM_ERR_ARG, "sigma must be >= 0");
+  if (!std::isfinite(kappa2)) return fail(LBM_ERR_ARG, "kappa2 must be finite");
+  if (!(std::fabs(mach) < 1.0)) return fail(LBM_ERR_ARG, "|mach| must be < 1");
+  if (!(length >= 0.0) || !std::isfinite(length)) return fail(LBM_ERR_ARG, "length must be >= 0");
+  if (exact_mass != 0 && exact_mass != 1) return fail(LBM_ERR_ARG, "exact_mass must be 0 or 1");
+  if (tuner) {
+    if (!tuner->params) return fail(LBM_ERR_ARG, "tuner->params is NULL");
+    if (tuner->n_layers < 1 || tuner->n_layers > 3)
+      return fail(LBM_ERR_ARG, "the tuner has 1..3 layers");
+    if (tuner->sizes[0] != 6 || tuner->sizes[tuner->n_layers] < 1 ||
+        tuner->sizes[tuner->n_layers] > 2)
+      return fail(LBM_ERR_ARG, "the tuner maps 6 inputs to 1 or 2 outputs");
+    int64_t np = 0;
+    for (int l = 0; l < tuner->n_layers; ++l) {
+      if (tuner->sizes[l + 1] < 1 || tuner->sizes[l + 1] > 32)
+        return fail(LBM_ERR_ARG, "tuner layers must have 1..32 units");
+      np += (int64_t)tuner->sizes[l] * tuner->sizes[l + 1] + tuner->sizes[l + 1];
+    }
+    if (tuner->n_params != np) return fail(LBM_ERR_ARG, "n_params does not match the layer sizes");
+    if (tuner->act != 0 && tuner->act != 1)
+      return fail(LBM_ERR_ARG, "act must be 0 (tanh) or 1 (leaky)");
+    if (lbm_status st = upload_net(s, tuner, 6, np)) return st;
+  } else {
+    s->nn.n_layers = 0;
+  }
+  s->cbc_sigma = sigma;
+  s->cbc_kappa2 = kappa2;
+  s->cbc_mach = mach;
+  s->cbc_length = length;
+  s->cbc_exact = exact_mass;
+  s->east = lbm::EAST_EXTERNAL;
+  s->outflow = LBM_OUTFLOW_CBC;
+  s->version++;
+  return LBM_OK;
 }
 
 lbm_status lbm_nn_fallbacks(lbm_sim* s, int64_t* count) {

@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "sim.cuh"
@@ -64,19 +65,34 @@ void fill_member(const lbm_sim* s, Member& m) {
   m.ring = s->ring;
   m.ring_cap = s->ring_cap;
   m.status = s->status;
-  if (s->east == EAST_EXTERNAL && s->outflow == LBM_OUTFLOW_NN) {
-    // FP32 and FP16 storage compute in FP32: both use the FP32 blob
-    m.nn_net = s->prec == LBM_FP64 ? (const void*)s->nn.params_d : (const void*)s->nn.params_f;
+  if (s->east == EAST_EXTERNAL) {
+    m.ext_kind = s->outflow == LBM_OUTFLOW_NN ? 1 : 2;
+    // the network (NN outflow) or tuner (CBC); FP32 and FP16 storage compute in FP32
+    if (s->nn.n_layers > 0) {
+      m.nn_net = s->prec == LBM_FP64 ? (const void*)s->nn.params_d : (const void*)s->nn.params_f;
+      m.nn_layers = s->nn.n_layers;
+      m.nn_act = s->nn.act;
+      for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) m.nn_sizes[l] = s->nn.sizes[l];
+    }
     m.nn_fallbacks = s->nn_fallbacks;
     m.nn_out_scale = s->nn.out_scale;
     m.nn_drho = s->nn_drho;
-    m.nn_layers = s->nn.n_layers;
-    m.nn_act = s->nn.act;
-    for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) m.nn_sizes[l] = s->nn.sizes[l];
+    if (m.ext_kind == 2) {
+      const double cs = std::sqrt(1.0 / 3.0);
+      const double length = s->cbc_length > 0.0 ? s->cbc_length : (double)s->nx;
+      m.cbc_sigma = s->cbc_sigma;
+      m.cbc_kappa2 = s->cbc_kappa2;
+      m.cbc_kfac = (1.0 - s->cbc_mach * s->cbc_mach) * cs / length;
+      m.cbc_exact = s->cbc_exact;
+    }
   }
 }
 
-bool has_nn(const lbm_sim* s) { return s->east == EAST_EXTERNAL && s->outflow == LBM_OUTFLOW_NN; }
+// east column rebuilt by boundary blocks: 1 NN outflow, 2 CBC, 0 none
+int ext_kind(const lbm_sim* s) {
+  if (s->east != EAST_EXTERNAL) return 0;
+  return s->outflow == LBM_OUTFLOW_NN ? 1 : 2;
+}
 
 bool table_stale(const Group& g) {
   if (g.built_versions.size() != g.sims.size()) return true;
@@ -98,12 +114,13 @@ void build_table(Group& g) {
     ms[(size_t)k].strip_count = strips;
     strip_total += strips;
   }
-  // network blocks first in the grid, one range per member with a network outflow
+  // boundary blocks first in the grid, one range per member with a rebuilt east column
   std::vector<int32_t> nb;
   for (int k = 0; k < n; ++k) {
-    if (!has_nn(g.sims[k])) continue;
+    const int kind = ext_kind(g.sims[k]);
+    if (!kind) continue;
     ms[(size_t)k].nn_first = (int32_t)nb.size();
-    const int c = step_nn_blocks(g.sims[k]->ny, g.variant);
+    const int c = step_ext_blocks(g.sims[k]->ny, g.variant, kind);
     for (int j = 0; j < c; ++j) nb.push_back(k);
   }
   g.nn_blocks = (int)nb.size();

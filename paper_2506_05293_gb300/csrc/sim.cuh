@@ -42,7 +42,14 @@ struct Member {
   double* ring;           // 2 doubles per step
   int64_t ring_cap;
   int* status;
-  // NN direct-reconstruction outflow (east_mode EAST_EXTERNAL), else unused
+  // east column rebuilt by boundary blocks (east_mode EAST_EXTERNAL):
+  // ext_kind 1 = NN direct reconstruction, 2 = characteristic outflow (CBC)
+  int32_t ext_kind;
+  int32_t cbc_exact;      // CBC: f_0 correction that makes the density exact
+  double cbc_sigma;       // CBC: sigma of Eq. 27 (sigma_max with a tuner)
+  double cbc_kappa2;      // CBC: kappa2 of Eq. 26 (kappa2_max with a 2-output tuner)
+  double cbc_kfac;        // CBC: (1 - M^2) c_s / length, so kappa1 = sigma * cbc_kfac
+  // network of the NN outflow, or the CBC tuner (nn_layers 0: none)
   const void* nn_net;     // compute-precision blob: per layer W^T then b, in_mean, in_std
   unsigned long long* nn_fallbacks;
   double nn_out_scale;
@@ -50,7 +57,7 @@ struct Member {
   int32_t nn_layers;
   int32_t nn_act;
   int32_t nn_sizes[LBM_MLP_MAX_LAYERS + 1];
-  int32_t nn_first;       // first network block of this member in the launch
+  int32_t nn_first;       // first boundary block of this member in the launch
 };
 
 // Parameters of one launch of a step kernel.
@@ -67,8 +74,8 @@ struct StepParams {
   int32_t reduce_prev;           // extra blocks finalise the previous step's forces
   double* partials;              // [2 parities][partial_stride][2]
   int32_t partial_stride;
-  int32_t nn_blocks;             // network blocks (the first blocks of the grid)
-  const int32_t* nn_block_member;  // member of each network block (multi-member)
+  int32_t nn_blocks;             // boundary blocks (the first blocks of the grid)
+  const int32_t* nn_block_member;  // member of each boundary block (multi-member)
   Member m0;                     // copy of the only member when n_members == 1: the
                                  // kernels then read it from the parameter bank
 };
@@ -93,10 +100,10 @@ void launch_step(int prec, int coll, const StepParams& p, int variant, int block
 // forces of step tt from the block partials into each member's ring
 void launch_finalize_force(const StepParams& p, int64_t tt, cudaStream_t s);
 void launch_set_t(int64_t* t_base, int64_t value, cudaStream_t s);
-void launch_step_nn(int prec, int coll, const StepParams& p, int variant, int blocks,
-                    cudaStream_t s);   // launches with network blocks (step_nn.cu)
+void launch_step_ext(int prec, int coll, const StepParams& p, int variant, int blocks,
+                     cudaStream_t s);   // launches with boundary blocks (step_ext.cu)
 int step_strips(int nx, int ny, int rows);
-int step_nn_blocks(int ny, int variant);  // network blocks that one member's east column needs
+int step_ext_blocks(int ny, int variant, int ext_kind);  // boundary blocks of one member
 bool step_variant_is_bulk(int variant);
 bool step_variant_streams(int variant);   // staged variant on a resident-sized grid
 int step_variants();
@@ -225,8 +232,10 @@ struct lbm_sim {
   int east = lbm::EAST_ZOUHE;
   int outflow = LBM_OUTFLOW_ZOUHE;
   double rho_out = 1.0;
-  lbm::DevMlp nn;
+  lbm::DevMlp nn;                    // NN outflow network, or the CBC tuner
   double nn_drho = 0.05;
+  double cbc_sigma = 0.0, cbc_kappa2 = 0.0, cbc_mach = 0.0, cbc_length = 0.0;
+  int cbc_exact = 0;
   // training-row capture (lbm_capture_plane)
   float* cap_out = nullptr;          // caller's device buffer of cap_capacity rows
   int64_t cap_capacity = 0;

@@ -11,8 +11,9 @@
 //     momentum exchange (Eqs. 13-14) to an FP64 force accumulator;
 //   - west column (open x): Zou & He velocity inlet, then collision;
 //   - east column (open x): Zou & He pressure outflow (Eqs. 5-10) then
-//     collision, or, with the NN outflow, rebuilt by network blocks of the same
-//     launch (Sec. 3.1, Eq. 15) that run beside the stream-and-collide blocks;
+//     collision, or, with the NN or characteristic outflow, rebuilt by
+//     boundary blocks of the same launch (Sec. 3.1, Eq. 15; Sec. 4, Eqs.
+//     17-28) that run beside the stream-and-collide blocks (step_ext.cu);
 //   - all other fluid nodes: BGK (Eq. 2) or MRT collision.
 // The lattice is cut into strips of 128 columns x `rows` rows.  A launch table
 // lists the member lattices (one simulation, or a batch of simulations of
@@ -58,12 +59,11 @@ int step_strips(int nx, int ny, int rows) {
   return ((nx + 127) / 128) * ((ny + rows - 1) / rows);
 }
 
-int step_nn_blocks(int ny, int variant) {
-  (void)variant;
-  return (ny + kNnNodes - 1) / kNnNodes;
+int step_ext_blocks(int ny, int variant, int ext_kind) {
+  // NN: kNnNodes nodes per block; CBC: one node per thread
+  const int per = ext_kind == 1 ? kNnNodes : (step_variant_is_bulk(variant) ? kBulkThreads : 128);
+  return (ny + per - 1) / per;
 }
-
-
 
 bool step_variant_is_bulk(int variant) { return variant >= 3; }
 bool step_variant_streams(int variant) { return variant >= 4; }
@@ -108,13 +108,9 @@ int step_max_blocks(int prec, int coll, int variant) {
   return sms * per_sm;
 }
 
-
-
-
-
 void launch_step(int prec, int coll, const StepParams& p, int variant, int blocks, cudaStream_t s) {
   if (p.nn_blocks > 0) {
-    launch_step_nn(prec, coll, p, variant, blocks, s);   // step_nn.cu
+    launch_step_ext(prec, coll, p, variant, blocks, s);   // step_ext.cu
     return;
   }
   if (prec == LBM_FP64) launch_c<double, false>(coll, p, variant, blocks, s);

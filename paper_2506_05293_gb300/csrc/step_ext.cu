@@ -1,7 +1,8 @@
-// The step kernels with fused network blocks (NN direct-reconstruction
-// outflow, Sec. 3.1, Eq. 15): the same templates as step.cu, instantiated
-// with the network dispatch compiled in, in a translation unit of their own
-// so that launches without a network outflow run kernels without its code.
+// The step kernels with fused boundary blocks for the east column (NN direct
+// reconstruction, Sec. 3.1, Eq. 15; characteristic outflow, Sec. 4, Eqs.
+// 17-28): the same templates as step.cu, instantiated with the boundary
+// dispatch compiled in, in a translation unit of their own so that launches
+// with the Zou & He outflow run kernels without that code.
 #include "step_kernels.cuh"
 
 namespace lbm {
@@ -30,8 +31,8 @@ void launch_nn_c(int coll, const StepParams& p, int variant, int blocks, cudaStr
 
 }  // namespace
 
-void launch_step_nn(int prec, int coll, const StepParams& p, int variant, int blocks,
-                    cudaStream_t s) {
+void launch_step_ext(int prec, int coll, const StepParams& p, int variant, int blocks,
+                     cudaStream_t s) {
   if (prec == LBM_FP64) launch_nn_c<double>(coll, p, variant, blocks, s);
   else if (prec == LBM_FP32) launch_nn_c<float>(coll, p, variant, blocks, s);
   else launch_nn_c<__half>(coll, p, variant, blocks, s);

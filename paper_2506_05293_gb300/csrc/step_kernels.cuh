@@ -420,24 +420,169 @@ __device__ __noinline__ void nn_block(const StepParams& p, const Member& m, int 
   for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[i]);
 }
 
-template <typename S>
-__device__ __forceinline__ void nn_dispatch(const StepParams& p, int blk, unsigned char* smem) {
-  if (p.n_members == 1) {
-    nn_block<S>(p, p.m0, blk, smem);
-  } else {
-    const Member& m = p.members[p.nn_block_member[blk]];
-    nn_block<S>(p, m, blk - m.nn_first, smem);
-  }
+// ---- characteristic outflow blocks (Sec. 4, Eqs. 17-28) ----------------------
+// One thread per east node (L, y), L = nx - 1.  From the post-collision state
+// at t (the source buffer): rho, u, v at (L, y), (L-1, y), (L-2, y),
+// (L, y -+ 1); p = c_s^2 rho; d/dx second-order one-sided backward, d/dy
+// central (periodic) or first-order towards the fluid next to a solid row.
+// Optional tuner: the six derivatives (p_x, u_x, v_x, p_y, u_y, v_y),
+// z-scored, through a small MLP; sigma = sigma_max sigmoid(s_0), and with a
+// second output kappa2 = kappa2_max sigmoid(s_1).  Wave amplitudes L5, L3
+// (Eqs. 20-22), transverse terms T1, T3, T5 (Eqs. 23-25), incoming L1 of
+// Eq. 26 with kappa1 of Eq. 27, time derivatives (Eqs. 17-19) and one Euler
+// step give the prescribed (rho, u, v) at t+1; the unknowns 3, 6, 7 of the
+// post-stream node follow by Zou & He with that state and f_0 takes the
+// correction of Eq. 28; then the node collides like any fluid node.
+constexpr int kTunerMaxW = 32;    // widest hidden layer of the CBC tuner
+
+// rho - 1, u, v of the stored (post-collision) populations of node (x, y);
+// differences are taken on rho - 1, which FP32 holds to full relative precision
+template <typename S, typename R>
+__device__ __forceinline__ void node_macros(const S* __restrict__ A, const Member& m, int x, int y,
+                                            R& drho, R& u, R& v) {
+  R h[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) h[i] = to_r<R>(ldg(A + i * m.plane + y * m.pitch + x));
+  R jx, jy;
+  moments_shifted(h, drho, jx, jy);
+  const R rho = R(1) + drho;
+  u = jx / rho;
+  v = jy / rho;
 }
 
-template <typename S, int COLL, int MINB, bool NN>
+template <typename R>
+__device__ __forceinline__ R sigmoid_r(R s) { return R(1) / (R(1) + exp(-s)); }
+
+// tuner outputs s[0..1] (s[1] = 0 with one output) for six inputs
+template <typename R>
+__device__ void tuner_eval(const Member& m, const R x_in[6], R s_out[2]) {
+  const R* __restrict__ net = static_cast<const R*>(m.nn_net);
+  int n_params = 0;
+  for (int l = 0; l < m.nn_layers; ++l)
+    n_params += m.nn_sizes[l] * m.nn_sizes[l + 1] + m.nn_sizes[l + 1];
+  const R* in_mean = net + n_params;
+  const R* in_std = in_mean + 6;
+  R a[kTunerMaxW], b[kTunerMaxW];
+  for (int k = 0; k < 6; ++k) a[k] = (x_in[k] - ldg(in_mean + k)) / ldg(in_std + k);
+  int off = 0;
+  for (int l = 0; l < m.nn_layers; ++l) {
+    const int n_in = m.nn_sizes[l], n_out = m.nn_sizes[l + 1];
+    const R* Wt = net + off;
+    const bool last = l == m.nn_layers - 1;
+    for (int j = 0; j < n_out; ++j) {
+      R acc = ldg(Wt + n_in * n_out + j);
+      for (int k = 0; k < n_in; ++k) acc = fma(ldg(Wt + k * n_out + j), a[k], acc);
+      b[j] = last ? acc : act_hidden<R>(acc, m.nn_act);
+    }
+    for (int j = 0; j < n_out; ++j) a[j] = b[j];
+    off += n_in * n_out + n_out;
+  }
+  s_out[0] = a[0];
+  s_out[1] = m.nn_sizes[m.nn_layers] > 1 ? a[1] : R(0);
+}
+
+template <typename S>
+__device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int local_block) {
+  using R = typename Compute<S>::R;
+  const int y = local_block * (int)blockDim.x + (int)threadIdx.x;
+  if (y >= m.ny) return;
+  const int L = m.nx - 1;
+  auto solid = [&](int x, int yy) -> bool {
+    return (__ldg(m.solid_bits + yy * m.words_per_row + (x >> 5)) >> (x & 31)) & 1u;
+  };
+  if (solid(L, y)) return;   // the stream-and-collide blocks handle solid nodes
+  const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
+  S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
+  const int ym = y == 0 ? m.ny - 1 : y - 1;
+  const int yp = y == m.ny - 1 ? 0 : y + 1;
+  const R cs2 = R(1) / R(3);
+  const R cs = sqrt(cs2);
+  R r0, u0, v0, r1, u1, v1, r2, u2, v2, rm, um, vm, rp, up, vp;
+  node_macros<S, R>(A, m, L, y, r0, u0, v0);
+  node_macros<S, R>(A, m, L - 1, y, r1, u1, v1);
+  node_macros<S, R>(A, m, L - 2, y, r2, u2, v2);
+  node_macros<S, R>(A, m, L, ym, rm, um, vm);
+  node_macros<S, R>(A, m, L, yp, rp, up, vp);
+  // r* hold rho - 1 here; p - 1/3 = c_s^2 (rho - 1)
+  const R px = cs2 * (R(0.5) * (R(3) * r0 - R(4) * r1 + r2));
+  const R ux = R(0.5) * (R(3) * u0 - R(4) * u1 + u2);
+  const R vx = R(0.5) * (R(3) * v0 - R(4) * v1 + v2);
+  const bool s_dn = solid(L, ym), s_up = solid(L, yp);
+  auto ddy = [&](R qm, R q0, R qp) -> R {
+    if (!s_up && !s_dn) return R(0.5) * (qp - qm);
+    if (!s_up) return qp - q0;
+    if (!s_dn) return q0 - qm;
+    return R(0);
+  };
+  const R py = cs2 * ddy(rm, r0, rp);
+  const R uy = ddy(um, u0, up);
+  const R vy = ddy(vm, v0, vp);
+  R sigma = (R)m.cbc_sigma, kappa2 = (R)m.cbc_kappa2;
+  if (m.nn_layers > 0) {
+    const R feats[6] = {px, ux, vx, py, uy, vy};
+    R s[2];
+    tuner_eval<R>(m, feats, s);
+    sigma = sigma * sigmoid_r(s[0]);
+    if (m.nn_sizes[m.nn_layers] > 1) kappa2 = kappa2 * sigmoid_r(s[1]);
+  }
+  // Eqs. 20-27 and the Euler step of Eqs. 17-19
+  const R rho = R(1) + r0;
+  const R pL = cs2 * rho;
+  const R L5 = (u0 + cs) * (px + rho * cs * ux);
+  const R L3 = u0 * vx;
+  const R T1 = -(v0 * py + pL * vy - rho * cs * v0 * vy);
+  const R T3 = -(v0 * vy + py / rho);
+  const R T5 = -(v0 * py + pL * vy + rho * cs * v0 * vy);
+  const R kappa1 = sigma * (R)m.cbc_kfac;
+  const R L1 = kappa1 * (cs2 * (r0 - (R)(m.rho_out - 1.0))) - kappa2 * T1 + T1;
+  const R dr = r0 + (-(L5 + L1) / (R(2) * cs2) + (T5 + T1) / (R(2) * cs2));   // rho - 1 at t+1
+  const R un = u0 + (-(L5 - L1) / (R(2) * rho * cs) + (T5 - T1) / (R(2) * rho * cs));
+  const R vn = v0 + (-L3 + T3);
+  // post-stream node (the pulls from x = L + 1 are rebuilt below)
+  const int rc = y * m.pitch, rmo = ym * m.pitch, rpo = yp * m.pitch;
+  R h[9];
+  h[0] = to_r<R>(ldg(A + 0 * m.plane + rc + L));
+  h[1] = to_r<R>(ldg(A + 1 * m.plane + rc + L - 1));
+  h[2] = to_r<R>(ldg(A + 2 * m.plane + rmo + L));
+  h[4] = to_r<R>(ldg(A + 4 * m.plane + rpo + L));
+  h[5] = to_r<R>(ldg(A + 5 * m.plane + rmo + L - 1));
+  h[8] = to_r<R>(ldg(A + 8 * m.plane + rpo + L - 1));
+  // Zou & He with the prescribed state, then Eq. 28 on f_0
+  const R sknown = (h[0] + h[2] + h[4]) + R(2) * (h[1] + h[5] + h[8]);   // rho0 + 2 rho+ - 1
+  R heq[9];
+  heq_sym(dr, un, vn, heq);
+  const R half_t = R(0.5) * ((h[4] - heq[4]) - (h[2] - heq[2]));
+  h[3] = heq[3] + (h[1] - heq[1]);
+  h[6] = heq[6] + (h[8] - heq[8]) + half_t;
+  h[7] = heq[7] + (h[5] - heq[5]) - half_t;
+  const R excess = dr + un + dr * un - sknown;          // rho (1 + u) - (rho0 + 2 rho+)
+  h[0] += m.cbc_exact ? excess : excess / (R(1) + un);
+  const Scalars<R> sc(m);
+  R drho, uxo, uyo;
+  if (m.coll == LBM_BGK) collide_bgk<R>(h, sc.omega, drho, uxo, uyo);
+  else collide_mrt<R>(h, sc.mrt, drho, uxo, uyo);
+  if (nonfinite(drho)) atomicOr(m.status, DEV_NONFINITE);
+  const int o = rc + L;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[i]);
+}
+
+template <typename S>
+__device__ __forceinline__ void ext_dispatch(const StepParams& p, int blk, unsigned char* smem) {
+  const Member& m = p.n_members == 1 ? p.m0 : p.members[p.nn_block_member[blk]];
+  const int local = p.n_members == 1 ? blk : blk - m.nn_first;
+  if (m.ext_kind == 1) nn_block<S>(p, m, local, smem);
+  else cbc_block<S>(p, m, local);
+}
+
+template <typename S, int COLL, int MINB, bool EXT>
 __global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
   using R = typename Compute<S>::R;
-  extern __shared__ __align__(16) unsigned char nn_smem[];   // network blocks only
+  extern __shared__ __align__(16) unsigned char nn_smem[];   // boundary blocks only
   pdl_launch_dependents();
   pdl_wait();
-  if (NN && (int)blockIdx.x < p.nn_blocks) {
-    nn_dispatch<S>(p, (int)blockIdx.x, nn_smem);
+  if (EXT && (int)blockIdx.x < p.nn_blocks) {
+    ext_dispatch<S>(p, (int)blockIdx.x, nn_smem);
     return;
   }
   const int b = (int)blockIdx.x - p.nn_blocks;             // stream-and-collide block
@@ -698,13 +843,13 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
   write_partial(p, t, slot, fx, fy, touched, bad, m.status);
 }
 
-template <typename S, int COLL, int NS, int MINB, bool NN>
+template <typename S, int COLL, int NS, int MINB, bool EXT>
 __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const StepParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   pdl_launch_dependents();
-  if (NN && (int)blockIdx.x < p.nn_blocks) {
+  if (EXT && (int)blockIdx.x < p.nn_blocks) {
     pdl_wait();
-    nn_dispatch<S>(p, (int)blockIdx.x, smem);
+    ext_dispatch<S>(p, (int)blockIdx.x, smem);
     return;
   }
   const int b = (int)blockIdx.x - p.nn_blocks;             // stream-and-collide block
@@ -767,36 +912,36 @@ inline void launch_pdl(Kernel kernel, int grid, int threads, size_t smem, cudaSt
   cudaLaunchKernelEx(&cfg, kernel, p);
 }
 
-template <typename S, int COLL, int MINB, bool NN>
+template <typename S, int COLL, int MINB, bool EXT>
 void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
   // the dynamic shared memory attribute is set by the occupancy query that
   // every group runs at creation (occ_bulk), or for the network kernels at
   // their first launch
   using R = typename Compute<S>::R;
   size_t smem = step_bulk_smem(prec_of<S>(), kBulkSlots);
-  if (NN) smem = smem > nn_smem_bytes<R>(kBulkThreads / 32) ? smem : nn_smem_bytes<R>(kBulkThreads / 32);
-  launch_pdl(step_bulk_kernel<S, COLL, kBulkSlots, MINB, NN>, p.nn_blocks + blocks + p.n_members,
+  if (EXT) smem = smem > nn_smem_bytes<R>(kBulkThreads / 32) ? smem : nn_smem_bytes<R>(kBulkThreads / 32);
+  launch_pdl(step_bulk_kernel<S, COLL, kBulkSlots, MINB, EXT>, p.nn_blocks + blocks + p.n_members,
              kBulkThreads, smem, s, p);
 }
 
-template <typename S, int COLL, bool NN>
+template <typename S, int COLL, bool EXT>
 void launch_v(const StepParams& p, int variant, int blocks, cudaStream_t s) {
   using R = typename Compute<S>::R;
   const int g = p.nn_blocks + blocks + p.n_members;
-  const size_t dyn = NN ? nn_smem_bytes<R>(4) : 0;
+  const size_t dyn = EXT ? nn_smem_bytes<R>(4) : 0;
   switch (variant) {
-    case 0: launch_pdl(step_kernel<S, COLL, 6, NN>, g, 128, dyn, s, p); break;
-    case 1: launch_pdl(step_kernel<S, COLL, 8, NN>, g, 128, dyn, s, p); break;
-    case 2: launch_pdl(step_kernel<S, COLL, 10, NN>, g, 128, dyn, s, p); break;
-    default: launch_bulk<S, COLL, 6, NN>(p, blocks, s); break;
+    case 0: launch_pdl(step_kernel<S, COLL, 6, EXT>, g, 128, dyn, s, p); break;
+    case 1: launch_pdl(step_kernel<S, COLL, 8, EXT>, g, 128, dyn, s, p); break;
+    case 2: launch_pdl(step_kernel<S, COLL, 10, EXT>, g, 128, dyn, s, p); break;
+    default: launch_bulk<S, COLL, 6, EXT>(p, blocks, s); break;
   }
 }
 
-template <typename S, bool NN>
+template <typename S, bool EXT>
 void launch_c(int coll, const StepParams& p, int variant, int blocks, cudaStream_t s) {
-  if (coll == LBM_BGK) launch_v<S, 0, NN>(p, variant, blocks, s);
-  else if (coll == LBM_MRT) launch_v<S, 1, NN>(p, variant, blocks, s);
-  else launch_v<S, 2, NN>(p, variant, blocks, s);
+  if (coll == LBM_BGK) launch_v<S, 0, EXT>(p, variant, blocks, s);
+  else if (coll == LBM_MRT) launch_v<S, 1, EXT>(p, variant, blocks, s);
+  else launch_v<S, 2, EXT>(p, variant, blocks, s);
 }
 
 }  // namespace lbm
