@@ -214,3 +214,94 @@ def run_study(st: Study, starts=("rest", "restart")):
             "t_trans": st.t_trans, "t_stat": st.t_stat, "rows": int(n_rows),
             "reference": ref, "training": info, "runs": runs,
             "timings": dict(st.timings)}
+
+
+# --------------------------------------------------------------------------- #
+# Convected vortex (Sec. 4.1): outflow treatments against a longer domain
+# --------------------------------------------------------------------------- #
+CS = (1.0 / 3.0) ** 0.5
+
+
+@dataclass
+class VortexCase:
+    nx: int
+    ny: int
+    strength: float                  # beta u0 / c_s
+    mach: float = 0.1                # u0 / c_s
+    re: float = 750.0                # Re = u0 nx / nu
+    x0_frac: float = 0.75            # vortex centre at x0 = x0_frac nx, y0 = ny / 2
+    rc_frac: float = 0.1             # core radius R_c = rc_frac ny
+    ref_factor: int = 4              # reference domain length in units of nx
+
+    @property
+    def u0(self):
+        return self.mach * CS
+
+    @property
+    def tau(self):
+        return 3.0 * self.u0 * self.nx / self.re + 0.5
+
+
+def vortex_fields(case: VortexCase, nx):
+    """Isothermal vortex of Sec. 4.1 (read with a dimensionless Gaussian,
+    gamma = 2, C_v = c_s^2) on a lattice nx wide, centred at the case's x0."""
+    y, x = np.mgrid[0:case.ny, 0:nx].astype(np.float64)
+    x0, y0, rc = case.x0_frac * case.nx, case.ny / 2.0, case.rc_frac * case.ny
+    r2 = (x - x0) ** 2 + (y - y0) ** 2
+    g = np.exp(-r2 / (2.0 * rc * rc))
+    bu = case.strength * CS
+    u = case.u0 - bu * (y - y0) / rc * g
+    v = bu * (x - x0) / rc * g
+    rho = 1.0 - bu * bu / (2.0 * CS * CS) * np.exp(-r2 / (rc * rc))
+    return rho, u, v
+
+
+def vortex_sim(case: VortexCase, nx, outflow, stream=0, precision="fp32"):
+    """One vortex run: west Zou & He inlet at u0, periodic y, BGK; outflow
+    ("zouhe" or ("cbc", sigma, kappa2))."""
+    cfg = L.lbm_config_default(nx=nx, ny=case.ny, tau=case.tau, collision="bgk",
+                               precision=precision, u_in=case.u0, stream=stream)
+    s = L.lbm_create(cfg)
+    L.lbm_set_geometry(s, np.zeros((case.ny, nx), np.uint8))
+    L.lbm_init_equilibrium(s, *vortex_fields(case, nx))
+    if outflow != "zouhe":
+        _, sigma, kappa2 = outflow
+        L.lbm_set_outflow_cbc(s, sigma, kappa2, case.mach, 0.0)
+    return s
+
+
+def vortex_study(cases, outflows, eval_steps, stream=0, precision="fp32"):
+    """Every case truncated at nx with each outflow, and once on its reference
+    domain (ref_factor x longer, Zou & He far away), each group advanced as
+    one batch.  Returns, per outflow, the L2 density error over the truncated
+    domain against the reference at each of eval_steps, per case."""
+    if not stream:
+        import torch
+        keep_stream = torch.cuda.Stream()      # a batch shares one stream
+        stream = keep_stream.cuda_stream
+    groups = {"reference": [vortex_sim(c, c.ref_factor * c.nx, "zouhe", stream, precision)
+                            for c in cases]}
+    names = {}
+    for o in outflows:
+        name = o if isinstance(o, str) else f"cbc_s{o[1]:g}_k{o[2]:g}"
+        names[name] = o
+        groups[name] = [vortex_sim(c, c.nx, o, stream, precision) for c in cases]
+    batches = {k: L.lbm_batch_create(v) for k, v in groups.items()}
+    errors = {k: [] for k in names}
+    done = 0
+    for t in eval_steps:
+        for k, b in batches.items():
+            L.lbm_batch_step(b, t - done)
+        done = t
+        ref = [L.lbm_fields(s)[0] for s in groups["reference"]]
+        for k in names:
+            row = []
+            for c, s, r in zip(cases, groups[k], ref):
+                rho = L.lbm_fields(s)[0]
+                row.append(float(np.sqrt(np.mean((rho - r[:, :c.nx]) ** 2))))
+            errors[k].append(row)
+    for k, b in batches.items():
+        L.lbm_batch_destroy(b)
+        for s in groups[k]:
+            L.lbm_destroy(s)
+    return {k: np.array(v) for k, v in errors.items()}
