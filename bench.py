@@ -72,7 +72,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("step.cu", "lattice.cuh", "sim.cuh"):
+    for f in ("step_kernels.cuh", "step.cu", "lattice.cuh", "sim.cuh"):
         with open(os.path.join(ROOT, "paper_2506_05293_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -146,6 +146,34 @@ def test_c1_bgk_re20_fp32_2000(L, c1_bgk_re20_oracle):
     _assert_fp32(g, c1_bgk_re20_oracle, C1_KIND, 0.05, 10, u_l2=2e-5, u_max=2e-4)
 
 
+def fp16_errors(g, o, kind, U, D):
+    """Per-result error of a run against the FP64 oracle: max relative density,
+    relative L2 and max (over U) velocity, mean C_D relative, C_L over its RMS."""
+    fl = kind == 0
+    drho = (np.abs(g["rho"] - o["rho"])[fl] / o["rho"][fl]).max()
+    du = np.hypot(g["ux"] - o["ux"], g["uy"] - o["uy"])[fl]
+    un = np.hypot(o["ux"], o["uy"])[fl]
+    cd_g, cl_g = post.coefficients(g["F"], 1.0, U, D)
+    cd_o, cl_o = post.coefficients(o["F"], 1.0, U, D)
+    half = len(cd_o) // 2
+    rms = np.sqrt((cl_o[half:] ** 2).mean())
+    return dict(rho=float(drho), u_l2=float(np.linalg.norm(du) / np.linalg.norm(un)),
+                u_max=float(du.max() / U),
+                cd=float(abs(cd_g[half:].mean() / cd_o[half:].mean() - 1)),
+                cl=float(np.abs(cl_g[half:] - cl_o[half:]).max() / rms))
+
+
+def test_c1_mrt_re100_fp16dev(L, c1_mrt_re100_oracle):
+    """FP16-deviation storage (f - w_i rounded to FP16, collided in FP32) against
+    the FP64 oracle over 2000 steps of the plain cylinder at Re 100 (MRT)."""
+    g = _gpu_run(L, C1_KIND, 2000, "fp16dev", tau=lbm.tau_from_re(0.05, 10, 100), collision=1,
+                 **C1)
+    e = fp16_errors(g, c1_mrt_re100_oracle, C1_KIND, 0.05, 10)
+    print("fp16dev errors", e)
+    assert e["rho"] < 1e-3 and e["u_l2"] < 1e-2 and e["u_max"] < 5e-2
+    assert e["cd"] < 1e-2 and e["cl"] < 5e-2
+
+
 # --------------------------------------------------------------------------- #
 # ragged sizes spanning several tiles, periodic boxes, edge cases
 # --------------------------------------------------------------------------- #
