@@ -156,22 +156,29 @@ def fp16_errors(g, o, kind, U, D):
     cd_g, cl_g = post.coefficients(g["F"], 1.0, U, D)
     cd_o, cl_o = post.coefficients(o["F"], 1.0, U, D)
     half = len(cd_o) // 2
-    rms = np.sqrt((cl_o[half:] ** 2).mean())
+    rms_o = np.sqrt((cl_o[half:] ** 2).mean())
+    rms_g = np.sqrt((cl_g[half:] ** 2).mean())
     return dict(rho=float(drho), u_l2=float(np.linalg.norm(du) / np.linalg.norm(un)),
                 u_max=float(du.max() / U),
                 cd=float(abs(cd_g[half:].mean() / cd_o[half:].mean() - 1)),
-                cl=float(np.abs(cl_g[half:] - cl_o[half:]).max() / rms))
+                cl_rms=float(abs(rms_g / rms_o - 1)),
+                cl_pointwise=float(np.abs(cl_g[half:] - cl_o[half:]).max() / rms_o))
 
 
 def test_c1_mrt_re100_fp16dev(L, c1_mrt_re100_oracle):
     """FP16-deviation storage (f - w_i rounded to FP16, collided in FP32) against
-    the FP64 oracle over 2000 steps of the plain cylinder at Re 100 (MRT)."""
+    the FP64 oracle over 2000 steps of the plain cylinder at Re 100 (MRT).
+    Measured on GB300: rho 3.2e-4 relative, u 1.4e-3 relative L2 and 4.0e-2 U
+    at the worst node, mean C_D 5.1e-4.  The lift grows from the seeded 1e-3
+    inlet perturbation, which FP16 rounding (about 1e-4 of the populations)
+    perturbs as well: its phase differs (pointwise 0.83 of its RMS), so the
+    lift is compared by its RMS."""
     g = _gpu_run(L, C1_KIND, 2000, "fp16dev", tau=lbm.tau_from_re(0.05, 10, 100), collision=1,
                  **C1)
     e = fp16_errors(g, c1_mrt_re100_oracle, C1_KIND, 0.05, 10)
     print("fp16dev errors", e)
-    assert e["rho"] < 1e-3 and e["u_l2"] < 1e-2 and e["u_max"] < 5e-2
-    assert e["cd"] < 1e-2 and e["cl"] < 5e-2
+    assert e["rho"] < 6e-4 and e["u_l2"] < 3e-3 and e["u_max"] < 8e-2
+    assert e["cd"] < 1e-3 and e["cl_rms"] < 0.2
 
 
 # --------------------------------------------------------------------------- #
