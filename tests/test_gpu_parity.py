@@ -172,13 +172,13 @@ def test_c1_mrt_re100_fp16dev(L, c1_mrt_re100_oracle):
     at the worst node, mean C_D 5.1e-4.  The lift grows from the seeded 1e-3
     inlet perturbation, which FP16 rounding (about 1e-4 of the populations)
     perturbs as well: its phase differs (pointwise 0.83 of its RMS), so the
-    lift is compared by its RMS."""
+    lift is compared by its RMS (measured 2.4e-2 relative)."""
     g = _gpu_run(L, C1_KIND, 2000, "fp16dev", tau=lbm.tau_from_re(0.05, 10, 100), collision=1,
                  **C1)
     e = fp16_errors(g, c1_mrt_re100_oracle, C1_KIND, 0.05, 10)
     print("fp16dev errors", e)
     assert e["rho"] < 6e-4 and e["u_l2"] < 3e-3 and e["u_max"] < 8e-2
-    assert e["cd"] < 1e-3 and e["cl_rms"] < 0.2
+    assert e["cd"] < 1e-3 and e["cl_rms"] < 5e-2
 
 
 # --------------------------------------------------------------------------- #
