@@ -165,6 +165,23 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+def max_over_ranks(x, device):
+    """The largest value of x over the ranks of the process group (the slowest
+    replica's time); x itself when there is no group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_glups(world, nodes, steps, max_ms):
+    """Whole-job throughput: every replica advances `nodes` nodes per step."""
+    return world * nodes * steps / (max_ms * 1e-3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -329,10 +346,8 @@ def run_ours(args):
             diverged.append(f"{m['nx']}x{m['ny']} Re{m['Re']} {m['collision']}")
 
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * nodes * args.steps / (total_ms * 1e-3) / 1e9
+        total_ms = max_over_ranks(total_ms, "cuda")
+    value = job_glups(world, nodes, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
     L.lbm_batch_destroy(batch)
     for s in sims:
