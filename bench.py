@@ -12,7 +12,11 @@ step of every lattice (one kernel launch).
 
 Other workloads: ``cylinder_D40_L32D_Re100`` (the 1600 x 640 lattice alone;
 its 74 MB fit in L2, so a 256 MB write flushes L2 before each timed step and
-steps are timed one by one) and ``cylinder_D160_8192x4096``.
+steps are timed one by one), ``cylinder_D160_8192x4096``,
+``naca0012_4000x1600_aoa4`` (chord 400, leading edge one chord from the inlet,
+angle of attack 4 degrees, Re 1000, U = 0.04, MRT) and ``vortex_batch_256``
+(256 convected-vortex lattices of uneven sizes, 49,153,467 nodes, with the
+characteristic outflow, sigma 0.25, kappa2 = Ma = 0.1, Re 750).
 
 Prints one JSON line.
 """
@@ -37,24 +41,69 @@ L2_BYTES = 129 * 1024 * 1024
 
 
 def _cyl(D, height_D, wake_D, re_, coll, U=0.05):
-    return dict(D=D, ny=int(round(height_D * D)), nx=int(round(8 * D + wake_D * D)), Re=re_,
-                U=U, collision=coll)
+    return dict(shape="cylinder", D=D, ny=int(round(height_D * D)),
+                nx=int(round(8 * D + wake_D * D)), Re=re_, U=U, collision=coll, outflow="zouhe")
 
+
+def _naca(aoa, nx=4000, ny=1600, chord=400, re_=1000.0, U=0.04):
+    return dict(shape="naca", chord=chord, aoa=aoa, nx=nx, ny=ny, Re=re_, U=U, collision="mrt",
+                outflow="zouhe")
+
+
+def _vortex_batch(n, seed=7, mach=0.1, re_=750.0):
+    """Convected-vortex lattices of uneven sizes: nx ~ U[128, 1024], ny ~ U[128, 512],
+    strength beta u0 / c_s ~ U[0.01, 0.1]; CBC outflow (sigma 0.25, kappa2 = Ma)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = int(rng.integers(128, 1025))
+        ny = int(rng.integers(128, 513))
+        out.append(dict(shape="vortex", nx=nx, ny=ny, strength=float(rng.uniform(0.01, 0.1)),
+                        mach=mach, Re=re_, U=mach * CS, collision="bgk", outflow="cbc"))
+    return out
+
+
+CS = (1.0 / 3.0) ** 0.5
 
 WORKLOADS = {
     "cylinder_sweep_D40": [_cyl(40, 16, L, re_, c) for c in ("bgk", "mrt") for re_ in (100, 200)
                            for L in (4, 8, 32)],
     "cylinder_D40_L32D_Re100": [_cyl(40, 16, 32, 100, "bgk")],
     "cylinder_D160_8192x4096": [_cyl(160, 25.6, 43.2, 100, "bgk")],
+    "naca0012_4000x1600_aoa4": [_naca(4.0)],
+    "vortex_batch_256": _vortex_batch(256),
 }
 
 
 def member_geometry(m):
-    """Cell kinds and tau of one workload member (cylinder at (8D, ny/2))."""
-    from synth import cylinder_mask
-    kind = cylinder_mask(m["nx"], m["ny"], 8 * m["D"], m["ny"] / 2, m["D"])
-    tau = 3 * m["U"] * m["D"] / m["Re"] + 0.5
-    return kind, tau
+    """Cell kinds, tau and initial fields (rho, ux, uy; None = 1 or 0) of one
+    workload member: a cylinder at (8D, ny/2) or a NACA0012 with its leading
+    edge one chord from the inlet at mid-height, started from f^eq(1, (U, 0)) on
+    fluid nodes; or a convected vortex (centre at 0.75 nx, R_c = 0.1 ny)."""
+    import numpy as np
+    from synth import convected_vortex, cylinder_mask, naca0012_mask
+    if m["shape"] == "cylinder":
+        kind = cylinder_mask(m["nx"], m["ny"], 8 * m["D"], m["ny"] / 2, m["D"])
+        tau = 3 * m["U"] * m["D"] / m["Re"] + 0.5
+        return kind, tau, (None, np.where(kind == 0, m["U"], 0.0), None)
+    if m["shape"] == "naca":
+        kind = naca0012_mask(m["nx"], m["ny"], m["chord"], m["chord"], m["ny"] / 2, m["aoa"])
+        tau = 3 * m["U"] * m["chord"] / m["Re"] + 0.5
+        return kind, tau, (None, np.where(kind == 0, m["U"], 0.0), None)
+    kind = np.zeros((m["ny"], m["nx"]), np.uint8)
+    tau = 3 * m["U"] * m["nx"] / m["Re"] + 0.5
+    init = convected_vortex(m["nx"], m["ny"], 0.75 * m["nx"], m["ny"] / 2, 0.1 * m["ny"],
+                            m["strength"] * CS, m["U"])
+    return kind, tau, init
+
+
+def member_label(m):
+    if m["shape"] == "cylinder":
+        return f"{m['nx']}x{m['ny']} Re{m['Re']} {m['collision']}"
+    if m["shape"] == "naca":
+        return f"{m['nx']}x{m['ny']} naca0012 aoa{m['aoa']:g} Re{m['Re']:g} {m['collision']}"
+    return f"{m['nx']}x{m['ny']} vortex {m['strength']:.3f}"
 
 
 def workload_nodes(wl):
@@ -189,22 +238,30 @@ def dist_env():
     return rank, world, local
 
 
+ORACLE_MEMBERS = 12   # lattices the CPU sample cycles through (bounds its memory)
+
+
 def cpu_oracle_sample(wl, steps, warmup=1):
     """Time the FP64 oracle on the workload in a single-threaded child process:
-    bench step k advances member k mod n by one time step (a bounded sample of
-    the batch step).  Returns (GLUPS, total seconds, per-step seconds, nodes)."""
+    bench step k advances member k mod n (of the first ORACLE_MEMBERS lattices)
+    by one time step, a bounded sample of the batch step.  Returns (GLUPS,
+    total seconds, per-step seconds, nodes)."""
     code = (
         "import sys, time, json; sys.path.insert(0, %r)\n"
-        "from bench import WORKLOADS, member_geometry\n"
-        "from oracle import lbm\n"
+        "from bench import WORKLOADS, member_geometry, CS\n"
+        "from oracle import lbm, cbc\n"
         "import numpy as np\n"
-        "ms = WORKLOADS[%r]\n"
+        "ms = WORKLOADS[%r][:%d]\n"
         "sims = []\n"
         "for m in ms:\n"
-        "    kind, tau = member_geometry(m)\n"
+        "    kind, tau, init = member_geometry(m)\n"
+        "    extra = {}\n"
+        "    if m['outflow'] == 'cbc':\n"
+        "        extra = dict(outflow='cbc', cbc=cbc.CBCOutflow(sigma=0.25, kappa2=m['mach'],"
+        " mach=m['mach']))\n"
         "    s = lbm.Solver(lbm.Config(nx=m['nx'], ny=m['ny'], tau=tau, collision=m['collision'],"
-        " u_in=m['U']), kind)\n"
-        "    s.init_equilibrium(None, np.where(kind == 0, m['U'], 0.0), None)\n"
+        " u_in=m['U'], **extra), kind)\n"
+        "    s.init_equilibrium(*init)\n"
         "    sims.append((s, m['nx'] * m['ny']))\n"
         "for k in range(%d):\n"
         "    sims[k %% len(sims)][0].step(1)\n"
@@ -212,7 +269,8 @@ def cpu_oracle_sample(wl, steps, warmup=1):
         "for k in range(%d):\n"
         "    s, n = sims[k %% len(sims)]\n"
         "    t0 = time.perf_counter(); s.step(1); dts.append(time.perf_counter() - t0); nodes += n\n"
-        "print(json.dumps({'dts': dts, 'nodes': nodes}))\n" % (ROOT, wl, warmup, steps))
+        "print(json.dumps({'dts': dts, 'nodes': nodes}))\n" % (ROOT, wl, ORACLE_MEMBERS, warmup,
+                                                             steps))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
@@ -231,14 +289,15 @@ def run_reference(args):
     wl = args.workload
     value, total, per_step, nodes = cpu_oracle_sample(wl, args.steps, args.warmup)
     sample = (f"{args.steps} oracle time steps, one member lattice of {wl} per bench step "
-              f"(round robin over its {len(WORKLOADS[wl])} lattices), numpy FP64, 1 thread")
+              f"(round robin over its first {min(ORACLE_MEMBERS, len(WORKLOADS[wl]))} lattices), "
+              f"numpy FP64, 1 thread")
     line = {
         "impl": "reference", "metric": "GLUPS", "value": value, "unit": "GLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl, "lattices": len(WORKLOADS[wl]), "nodes": workload_nodes(wl),
-                   "outflow": "zouhe", "sample": sample},
+                   "outflow": workload_outflow(wl), "sample": sample},
         "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -247,28 +306,35 @@ def run_reference(args):
     return 0
 
 
+def workload_outflow(wl):
+    return "+".join(sorted({m["outflow"] for m in WORKLOADS[wl]}))
+
+
 def _make_members(L, wl, prec, stream):
-    import numpy as np
-    sims, kinds, ux0s = [], [], []
+    sims, kinds, inits = [], [], []
     for m in WORKLOADS[wl]:
-        kind, tau = member_geometry(m)
+        kind, tau, init = member_geometry(m)
         cfg = L.lbm_config_default(nx=m["nx"], ny=m["ny"], tau=tau, precision=prec,
                                    collision=m["collision"], u_in=m["U"], stream=stream)
-        sims.append(L.lbm_create(cfg))
+        s = L.lbm_create(cfg)
+        if m["outflow"] == "cbc":
+            L.lbm_set_outflow_cbc(s, 0.25, m["mach"], m["mach"], 0.0)
+        sims.append(s)
         kinds.append(kind)
-        ux0s.append(np.where(kind == 0, m["U"], 0.0))
-    return sims, kinds, ux0s
+        inits.append(init)
+    return sims, kinds, inits
 
 
 def _drain(L, sim, call):
-    """Run a data-returning call; a lattice that went non-finite still returns
-    its data (the status is reported separately)."""
+    """Run a data-returning call; a lattice that went non-finite transfers its
+    data all the same but reports LBM_ERR_NONFINITE, which is recorded instead
+    of raised (returns None then)."""
     try:
         return call()
     except L.LbmError as ex:
         if ex.status != 5:
             raise
-        return call()
+        return None
 
 
 def run_ours(args):
@@ -290,10 +356,10 @@ def run_ours(args):
     working_set = bpn * nodes          # two population buffers of bpn / 2 bytes per node
     flush_mode = working_set < L2_BYTES
     stream = torch.cuda.Stream()
-    sims, kinds, ux0s = _make_members(L, wl, prec, stream.cuda_stream)
-    for s, kind, ux0 in zip(sims, kinds, ux0s):
+    sims, kinds, inits = _make_members(L, wl, prec, stream.cuda_stream)
+    for s, kind, init in zip(sims, kinds, inits):
         L.lbm_set_geometry(s, kind)
-        L.lbm_init_equilibrium(s, None, ux0, None)
+        L.lbm_init_equilibrium(s, *init)
     batch = L.lbm_batch_create(sims)
     flush_bytes = 256 * 1024 * 1024 if flush_mode else 0
     if args.rows:
@@ -343,7 +409,7 @@ def run_ours(args):
         except L.LbmError as ex:
             if ex.status != 5:
                 raise
-            diverged.append(f"{m['nx']}x{m['ny']} Re{m['Re']} {m['collision']}")
+            diverged.append(member_label(m))
 
     if world > 1:
         total_ms = max_over_ranks(total_ms, "cuda")
@@ -357,15 +423,19 @@ def run_ours(args):
     # initial fields in from pinned host memory; 1000 steps of the batch; force
     # series and fields out
     e2e_steps = 1000
-    sims2, kinds2, ux02 = _make_members(L, wl, prec, stream.cuda_stream)
+    sims2, kinds2, inits2 = _make_members(L, wl, prec, stream.cuda_stream)
     pinned_in = []
-    for kind, ux0 in zip(kinds2, ux02):
+    for kind, (r0, u0, v0) in zip(kinds2, inits2):
         k_p = torch.empty(kind.shape, dtype=torch.uint8, pin_memory=True).numpy()
         k_p[:] = kind
         r_p = torch.ones(kind.shape, dtype=torch.float64, pin_memory=True).numpy()
+        if r0 is not None:
+            r_p[:] = r0
         u_p = torch.empty(kind.shape, dtype=torch.float64, pin_memory=True).numpy()
-        u_p[:] = ux0
+        u_p[:] = u0
         v_p = torch.zeros(kind.shape, dtype=torch.float64, pin_memory=True).numpy()
+        if v0 is not None:
+            v_p[:] = v0
         pinned_in.append((k_p, r_p, u_p, v_p))
     torch.cuda.synchronize()
     h2d = d2h = 0
@@ -377,10 +447,10 @@ def run_ours(args):
     batch2 = L.lbm_batch_create(sims2)
     L.lbm_batch_set_tiling(batch2, rows, variant)
     L.lbm_batch_step(batch2, e2e_steps)
-    for s in sims2:
-        fx, fy = _drain(L, s, lambda: L.lbm_forces(s))
-        r_, u_, v_ = _drain(L, s, lambda: L.lbm_fields(s))
-        d2h += fx.nbytes + fy.nbytes + r_.nbytes + u_.nbytes + v_.nbytes
+    for s, m in zip(sims2, WORKLOADS[wl]):
+        _drain(L, s, lambda: L.lbm_forces(s))
+        _drain(L, s, lambda: L.lbm_fields(s))
+        d2h += 2 * 8 * e2e_steps + 3 * 8 * m["nx"] * m["ny"]
     e2e_s = time.perf_counter() - w0
     L.lbm_batch_destroy(batch2)
     for s in sims2:
@@ -407,9 +477,11 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16"}[prec], "data": "synthetic",
         "config": {"workload": wl, "lattices": len(WORKLOADS[wl]), "nodes": nodes,
-                   "members": [f"{m['nx']}x{m['ny']} Re{m['Re']} {m['collision']}"
-                               for m in WORKLOADS[wl]],
-                   "outflow": "zouhe", "storage": prec, "working_set_bytes": working_set,
+                   "members": ([member_label(m) for m in WORKLOADS[wl]]
+                               if len(WORKLOADS[wl]) <= 16 else
+                               f"{len(WORKLOADS[wl])} lattices, first: "
+                               f"{member_label(WORKLOADS[wl][0])}"),
+                   "outflow": workload_outflow(wl), "storage": prec, "working_set_bytes": working_set,
                    "l2": ("flushed before each timed step (256 MB device write), steps timed one "
                           "by one") if flush_mode else
                          "working set larger than L2: no flush, steps back to back",

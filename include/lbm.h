@@ -188,6 +188,17 @@ lbm_status lbm_capture_plane(lbm_sim* sim, int32_t x_t, int32_t every, float* de
 /* Rows captured so far (complete once the sim's stream reaches them). */
 lbm_status lbm_capture_count(lbm_sim* sim, int64_t* rows);
 
+/* Checkpoint of the simulation state (the paper has no counterpart; a restart
+ * facility for long runs): lbm_save writes the current populations (storage
+ * precision, the padded layout) and the step counter to a file (host path,
+ * created or truncated) after the stream's pending work; lbm_load reads one into
+ * a sim created with the same nx, ny and precision (else LBM_ERR_ARG) and sets
+ * its step counter, so stepping on gives the same bits as the uninterrupted run.
+ * Geometry, outflow settings and networks are not stored: set them as before.
+ * The force series restarts empty at the loaded step (drain it before saving). */
+lbm_status lbm_save(lbm_sim* sim, const char* path);
+lbm_status lbm_load(lbm_sim* sim, const char* path);
+
 /* Normalisation of the network from a data set (device rows, n >= 1): per
  * input the mean and the population standard deviation (a std below 1e-12
  * becomes 1), and out_scale = the population standard deviation of the

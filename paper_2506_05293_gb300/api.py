@@ -181,6 +181,14 @@ def lbm_capture_plane(sim, x_t, every, rows=None, cap_rows=None):
                                          c_void_p(_devptr(rows)), int(cap_rows)))
 
 
+def lbm_save(sim, path):
+    _check(_lib.load().lbm_save(sim.handle, str(path).encode()))
+
+
+def lbm_load(sim, path):
+    _check(_lib.load().lbm_load(sim.handle, str(path).encode()))
+
+
 def lbm_capture_count(sim):
     c = c_int64()
     _check(_lib.load().lbm_capture_count(sim.handle, byref(c)))

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <complex>
 #include <exception>
 #include <string>
@@ -754,6 +755,74 @@ lbm_status lbm_set_populations(lbm_sim* s, const double* f) {
                      s->scratch_fields, s->stream);
   ck(cudaGetLastError(), "import launch");
   ck(cudaStreamSynchronize(s->stream), "sync");
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+// ---- checkpoints ------------------------------------------------------------
+namespace {
+struct CheckpointHeader {
+  char magic[8];
+  int32_t nx, ny, precision, pad;
+  int64_t t, elems;
+};
+constexpr char kCheckpointMagic[8] = {'G', 'B', '3', 'L', 'B', 'M', 'v', '1'};
+}  // namespace
+
+lbm_status lbm_save(lbm_sim* s, const char* path) {
+  if (lbm_status st = check_sim(s)) return st;
+  if (!path) return fail(LBM_ERR_ARG, "path is NULL");
+  LBM_GUARD_BEGIN
+  lbm::sim_settle(s);
+  const int64_t elems = 9 * s->plane;
+  std::vector<unsigned char> host((size_t)(elems * (int64_t)s->elem));
+  ck(cudaMemcpyAsync(host.data(), s->buf[s->cur], host.size(), cudaMemcpyDeviceToHost,
+                     s->stream), "checkpoint copy");
+  if (lbm_status st = read_status(s)) return st;
+  CheckpointHeader h{};
+  memcpy(h.magic, kCheckpointMagic, 8);
+  h.nx = s->nx;
+  h.ny = s->ny;
+  h.precision = s->prec;
+  h.t = s->t_host;
+  h.elems = elems;
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return fail(LBM_ERR_ARG, std::string("cannot open ") + path + " for writing");
+  const bool ok = fwrite(&h, sizeof(h), 1, fp) == 1 &&
+                  fwrite(host.data(), 1, host.size(), fp) == host.size();
+  if (fclose(fp) != 0 || !ok) return fail(LBM_ERR_ARG, std::string("write to ") + path + " failed");
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+lbm_status lbm_load(lbm_sim* s, const char* path) {
+  if (lbm_status st = check_sim(s)) return st;
+  if (!path) return fail(LBM_ERR_ARG, "path is NULL");
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return fail(LBM_ERR_ARG, std::string("cannot open ") + path);
+  CheckpointHeader h{};
+  const bool hdr = fread(&h, sizeof(h), 1, fp) == 1;
+  if (!hdr || memcmp(h.magic, kCheckpointMagic, 8) != 0) {
+    fclose(fp);
+    return fail(LBM_ERR_ARG, "not a checkpoint of this library");
+  }
+  if (h.nx != s->nx || h.ny != s->ny || h.precision != s->prec || h.elems != 9 * s->plane ||
+      h.t < 0) {
+    fclose(fp);
+    return fail(LBM_ERR_ARG, "the checkpoint is for another lattice size or precision");
+  }
+  std::vector<unsigned char> host((size_t)(h.elems * (int64_t)s->elem));
+  const bool body = fread(host.data(), 1, host.size(), fp) == host.size();
+  fclose(fp);
+  if (!body) return fail(LBM_ERR_ARG, "the checkpoint is truncated");
+  LBM_GUARD_BEGIN
+  reset_counters(s);
+  ck(cudaMemcpyAsync(s->buf[0], host.data(), host.size(), cudaMemcpyHostToDevice, s->stream),
+     "checkpoint copy");
+  ck(cudaStreamSynchronize(s->stream), "checkpoint sync");
+  s->cur = 0;
+  s->t_host = h.t;
+  s->drained = h.t;
   return LBM_OK;
   LBM_GUARD_END
 }
