@@ -283,20 +283,23 @@ lbm_status lbm_mass(lbm_sim* sim, double* mass);
  * that steps or destroys the sim. */
 lbm_status lbm_device_state(lbm_sim* sim, void** base, int64_t* pitch, int64_t* plane);
 
-/* Tiling of the step kernel: rows per strip (1..64; a strip is 128 columns)
+/* Tiling of the step kernel: rows per strip (1..4096; a strip is 128 columns)
  * and variant: 0..2 = the register-pipelined kernel on a persistent grid with
  * at least 6, 8 or 10 resident blocks of 128 threads per SM; 3 = the staged
  * kernel (a producer warp copies rows into a 4-slot shared-memory ring with
  * cp.async.bulk, four consumer warps collide from it; one block per strip);
- * 4 = the staged kernel on a resident-sized grid, each block streaming
- * several strips through its ring.  Staged variants need rows >= 2.
+ * 4 = the staged kernel on a resident-sized grid, each block streaming a
+ * fixed share of the strips through its ring; 5 = the staged kernel on a
+ * resident-sized grid whose blocks take strips from a global counter (dynamic
+ * balance; the counter is reset by the last block, so launches of one sim or
+ * batch must not overlap).  Staged variants need rows >= 2.
  * Populations do not depend on the tiling; the FP64 force sum may differ in
  * its last bits (partial sums change order). */
 lbm_status lbm_set_tiling(lbm_sim* sim, int32_t rows, int32_t variant);
 lbm_status lbm_get_tiling(lbm_sim* sim, int32_t* rows, int32_t* variant);
 
 /* Autotuner: time `steps` (1..10000) single steps of every candidate tiling
- * (rows 2, 4, 8, 12, 16, 20, 24, 32, 40, 48, 64 x the five variants) with CUDA
+ * (rows 2, 4, 8, 12, 16, 20, 24, 32, 40, 48, 64 x the six variants) with CUDA
  * events on the sim's
  * stream and keep the fastest; *best_ms (nullable) gets its mean step time.
  * With flush_bytes > 0 a scratch buffer of that size is written before each

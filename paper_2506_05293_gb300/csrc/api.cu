@@ -432,6 +432,14 @@ lbm_status lbm_set_geometry(lbm_sim* s, const uint8_t* kind) {
   const int64_t cells = (int64_t)s->nx * s->ny;
   for (int64_t c = 0; c < cells; ++c)
     if (kind[c] > LBM_CELL_WALL) return fail(LBM_ERR_ARG, "cell kind must be 0, 1 or 2");
+  {
+    const int tiles = (s->nx + 127) / 128;
+    s->solid_tile_rows.assign((size_t)tiles * s->ny, 0);
+    for (int y = 0; y < s->ny; ++y)
+      for (int x = 0; x < s->nx; ++x)
+        if (kind[(int64_t)y * s->nx + x] == LBM_CELL_SOLID)
+          s->solid_tile_rows[(size_t)y * tiles + x / 128] = 1;
+  }
   LBM_GUARD_BEGIN
   ck(cudaMemcpyAsync(s->kind, kind, cells, cudaMemcpyHostToDevice, s->stream), "kind copy");
   lbm::launch_geometry_prep(s->kind, s->nx, s->ny, s->cfg.x_periodic, s->solid_bits,
@@ -849,7 +857,7 @@ lbm_status lbm_device_state(lbm_sim* s, void** base, int64_t* pitch, int64_t* pl
 }
 
 static lbm_status check_tiling(int32_t rows, int32_t variant) {
-  if (rows < 1 || rows > 64) return fail(LBM_ERR_ARG, "rows must be in 1..64");
+  if (rows < 1 || rows > 4096) return fail(LBM_ERR_ARG, "rows must be in 1..4096");
   if (variant < 0 || variant >= lbm::step_variants()) return fail(LBM_ERR_ARG, "bad variant");
   if (lbm::step_variant_is_bulk(variant) && rows < 2)
     return fail(LBM_ERR_ARG, "the staged variants need rows >= 2");

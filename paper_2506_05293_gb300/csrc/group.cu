@@ -21,6 +21,7 @@ namespace {
 
 constexpr int64_t kGraphChunk = 32;   // steps per captured graph (longest)
 constexpr int64_t kMinGraphChunk = 4; // shorter runs of steps launch directly
+constexpr int kPartialsPerStrip = 4;  // consumer warps of the staged kernel
 
 void fill_member(const lbm_sim* s, Member& m) {
   memset(&m, 0, sizeof(m));
@@ -101,6 +102,31 @@ bool table_stale(const Group& g) {
   return false;
 }
 
+// Force-partial slot of every strip of the table for the current strip
+// height: consecutive slots for the strips that hold a counted solid node
+// (only those can exchange momentum), -1 for the others.  Sets each
+// member's slot range.
+std::vector<int32_t> strip_force_slots(const Group& g, std::vector<Member>& ms, int strip_total,
+                                       int per_strip) {
+  std::vector<int32_t> slot((size_t)strip_total, -1);
+  int next = 0;
+  for (size_t k = 0; k < g.sims.size(); ++k) {
+    const lbm_sim* s = g.sims[k];
+    const int tiles = (s->nx + 127) / 128;
+    ms[k].part_first = next * per_strip;
+    for (int j = 0; j < ms[k].strip_count; ++j) {
+      const int y0 = (j / tiles) * g.rows, tx = j % tiles;
+      const int y1 = std::min(s->ny, y0 + g.rows);
+      bool any = false;
+      for (int y = y0; y < y1 && !any && !s->solid_tile_rows.empty(); ++y)
+        any = s->solid_tile_rows[(size_t)y * tiles + tx] != 0;
+      if (any) slot[(size_t)(ms[k].strip_first + j)] = next++;
+    }
+    ms[k].part_count = next * per_strip - ms[k].part_first;
+  }
+  return slot;
+}
+
 // (Re)build the launch table for the current tiling and member state.
 void build_table(Group& g) {
   const int n = (int)g.sims.size();
@@ -140,13 +166,30 @@ void build_table(Group& g) {
     ck(cudaMemcpyAsync(g.d_nn_block_member, nb.data(), nb.size() * sizeof(int32_t),
                        cudaMemcpyHostToDevice, g.stream), "network table copy");
   }
-  // resident capacity left to the stream-and-collide blocks
-  const int room = std::max(1, g.max_blocks_v[g.variant] - g.nn_blocks - n);
+  // resident capacity for the stream-and-collide blocks: the boundary and
+  // force-reduction blocks finish within microseconds, so they do not hold
+  // their slots for the step and are not subtracted
+  const int room = std::max(1, g.max_blocks_v[g.variant]);
+  std::vector<int32_t> force;   // strip -> force slot, when partials go per strip
   if (g.persistent) {
     const int cap = room;
     g.blocks = std::min(strip_total, cap);
     ms[0].part_first = 0;
     ms[0].part_count = g.blocks;
+  } else if (step_variant_dynamic(g.variant)) {
+    // resident-sized grid taking strips from a counter: the strip table maps
+    // every strip to its member; partials go per force strip and consumer warp
+    g.blocks = std::min(strip_total, room);
+    force = strip_force_slots(g, ms, strip_total, kPartialsPerStrip);
+    if (n > 1) {
+      std::vector<int32_t> sm((size_t)strip_total);
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < ms[(size_t)k].strip_count; ++j)
+          sm[(size_t)(ms[(size_t)k].strip_first + j)] = k;
+      ck(cudaMemcpyAsync(g.d_strip_member, sm.data(), sm.size() * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, g.stream), "strip table copy");
+    }
+    ck(cudaMemsetAsync(g.dyn_ctr, 0, 2 * sizeof(unsigned long long), g.stream), "counter reset");
   } else if (step_variant_streams(g.variant)) {
     // streaming staged kernel: a resident-sized grid shared among the members
     // in proportion to their strips; each member's blocks are contiguous
@@ -177,6 +220,8 @@ void build_table(Group& g) {
     for (int k = 0; k < n; ++k) {
       ms[(size_t)k].part_first = first;
       ms[(size_t)k].part_count = gk[(size_t)k];
+      ms[(size_t)k].blk_first = first;
+      ms[(size_t)k].blk_count = gk[(size_t)k];
       for (int j = 0; j < gk[(size_t)k]; ++j) bm.push_back(k);
       first += gk[(size_t)k];
     }
@@ -185,11 +230,13 @@ void build_table(Group& g) {
       ck(cudaMemcpyAsync(g.d_strip_member, bm.data(), bm.size() * sizeof(int32_t),
                          cudaMemcpyHostToDevice, g.stream), "block table copy");
   } else {
+    // one block per strip; partials per force strip
     g.blocks = strip_total;
     for (int k = 0; k < n; ++k) {
-      ms[(size_t)k].part_first = ms[(size_t)k].strip_first;
-      ms[(size_t)k].part_count = ms[(size_t)k].strip_count;
+      ms[(size_t)k].blk_first = ms[(size_t)k].strip_first;
+      ms[(size_t)k].blk_count = ms[(size_t)k].strip_count;
     }
+    force = strip_force_slots(g, ms, strip_total, 1);
     if (n > 1) {
       std::vector<int32_t> sm((size_t)strip_total);
       for (int k = 0; k < n; ++k)
@@ -199,7 +246,27 @@ void build_table(Group& g) {
                          cudaMemcpyHostToDevice, g.stream), "strip table copy");
     }
   }
-  if (g.blocks > g.partial_stride) throw CudaError{cudaErrorInvalidValue, "partial table too small"};
+  g.use_strip_force = !force.empty();
+  if (g.use_strip_force) {
+    if ((int)force.size() > g.force_cap) {
+      const lbm_allocator* a = g.sims[0]->have_alloc ? &g.sims[0]->alloc : nullptr;
+      if (g.d_strip_force) {
+        ck(cudaStreamSynchronize(g.stream), "table sync");
+        dev_free_raw(a, g.d_strip_force);
+        g.owned.erase(std::remove(g.owned.begin(), g.owned.end(), (void*)g.d_strip_force),
+                      g.owned.end());
+      }
+      g.d_strip_force = (int32_t*)dev_alloc_raw(a, force.size() * sizeof(int32_t));
+      g.owned.push_back(g.d_strip_force);
+      g.force_cap = (int)force.size();
+    }
+    ck(cudaMemcpyAsync(g.d_strip_force, force.data(), force.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, g.stream), "force table copy");
+  }
+  int parts = g.blocks;
+  for (int k = 0; k < n; ++k)
+    parts = std::max(parts, ms[(size_t)k].part_first + ms[(size_t)k].part_count);
+  if (parts > g.partial_stride) throw CudaError{cudaErrorInvalidValue, "partial table too small"};
   ck(cudaMemcpyAsync(g.d_members, ms.data(), ms.size() * sizeof(Member), cudaMemcpyHostToDevice,
                      g.stream), "member table copy");
   g.h_member0 = ms[0];
@@ -222,6 +289,10 @@ StepParams params(const Group& g, int q) {
   p.partial_stride = g.partial_stride;
   p.nn_blocks = g.nn_blocks;
   p.nn_block_member = g.d_nn_block_member;
+  p.dyn_ctr = g.dyn_ctr;
+  p.strip_force = g.use_strip_force ? g.d_strip_force : nullptr;
+  p.dyn_strips = 0;
+  for (const lbm_sim* s : g.sims) p.dyn_strips += step_strips(s->nx, s->ny, g.rows);
   return p;
 }
 
@@ -353,7 +424,8 @@ void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single) {
   }
   int strips1 = 0;   // strips at one row per strip: the most any tiling launches
   for (const lbm_sim* s : sims) strips1 += step_strips(s->nx, s->ny, 1);
-  g.partial_stride = std::max(most, strips1);
+  // the dynamic staged variant writes one partial per strip and consumer warp
+  g.partial_stride = std::max(most, kPartialsPerStrip * strips1);
   auto alloc = [&](size_t bytes) {
     void* p = dev_alloc_raw(a, bytes);
     g.owned.push_back(p);
@@ -363,6 +435,8 @@ void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single) {
   g.d_strip_member = sims.size() > 1 ? (int32_t*)alloc(sizeof(int32_t) * (size_t)strips1) : nullptr;
   g.partials = (double*)alloc(sizeof(double) * 4 * (size_t)g.partial_stride);
   g.t_base = (int64_t*)alloc(sizeof(int64_t));
+  g.dyn_ctr = (unsigned long long*)alloc(2 * sizeof(unsigned long long));
+  ck(cudaMemsetAsync(g.dyn_ctr, 0, 2 * sizeof(unsigned long long), g.stream), "memset");
   ck(cudaMemsetAsync(g.partials, 0, sizeof(double) * 4 * (size_t)g.partial_stride, g.stream),
      "memset");
   ck(cudaMemsetAsync(g.t_base, 0, sizeof(int64_t), g.stream), "memset");

@@ -39,6 +39,8 @@ struct Member {
   int32_t strip_count;    // strips of this member
   int32_t part_first;     // force partials of this member: [part_first, +part_count)
   int32_t part_count;
+  int32_t blk_first;      // staged kernel: blocks of this member [blk_first, +blk_count),
+  int32_t blk_count;      // strips lb, lb + blk_count, ... for local block lb
   double* ring;           // 2 doubles per step
   int64_t ring_cap;
   int* status;
@@ -74,6 +76,10 @@ struct StepParams {
   int32_t reduce_prev;           // extra blocks finalise the previous step's forces
   double* partials;              // [2 parities][partial_stride][2]
   int32_t partial_stride;
+  const int32_t* strip_force;     // per strip its force-partial slot (-1: no counted solid),
+                                 // or null: one partial per block
+  unsigned long long* dyn_ctr;   // variant 5: [next strip, finished blocks], zero between launches
+  int32_t dyn_strips;            // variant 5: strips of the whole table
   int32_t nn_blocks;             // boundary blocks (the first blocks of the grid)
   const int32_t* nn_block_member;  // member of each boundary block (multi-member)
   Member m0;                     // copy of the only member when n_members == 1: the
@@ -105,7 +111,8 @@ void launch_step_ext(int prec, int coll, const StepParams& p, int variant, int b
 int step_strips(int nx, int ny, int rows);
 int step_ext_blocks(int ny, int variant, int ext_kind);  // boundary blocks of one member
 bool step_variant_is_bulk(int variant);
-bool step_variant_streams(int variant);   // staged variant on a resident-sized grid
+bool step_variant_streams(int variant);   // staged variant with a fixed share per block
+bool step_variant_dynamic(int variant);   // staged variant taking strips from a counter
 int step_variants();
 // resident blocks per GPU (occupancy x SMs) of a variant; coll 2 = per member
 int step_max_blocks(int prec, int coll, int variant);
@@ -188,6 +195,10 @@ struct Group {
   int32_t* d_strip_member = nullptr;
   int32_t* d_nn_block_member = nullptr;   // member of each network block
   int nn_cap = 0;                // entries of d_nn_block_member
+  unsigned long long* dyn_ctr = nullptr;   // counters of the dynamic staged variant
+  int32_t* d_strip_force = nullptr;        // force-partial slot of each strip
+  int force_cap = 0;
+  bool use_strip_force = false;
   int nn_blocks = 0;             // network blocks of the current table
   double* partials = nullptr;    // [2][partial_stride][2]
   int partial_stride = 0;
@@ -216,6 +227,7 @@ struct lbm_sim {
   uint32_t* solid_bits = nullptr;
   int words_per_row = 0;
   uint8_t* links = nullptr;
+  std::vector<uint8_t> solid_tile_rows;   // per 128-column tile and row: holds a counted solid
   double* ring = nullptr;
   int64_t ring_cap = 0;
   int* status = nullptr;

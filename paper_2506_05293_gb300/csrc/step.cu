@@ -66,15 +66,16 @@ int step_ext_blocks(int ny, int variant, int ext_kind) {
 }
 
 bool step_variant_is_bulk(int variant) { return variant >= 3; }
-bool step_variant_streams(int variant) { return variant >= 4; }
+bool step_variant_streams(int variant) { return variant == 4; }
+bool step_variant_dynamic(int variant) { return variant == 5; }
 
 int step_variants() { return kVariants; }
 
 
-template <typename S, int COLL, int MINB>
+template <typename S, int COLL, int MINB, bool DYN>
 static cudaError_t occ_bulk(int* per_sm) {
   const size_t smem = step_bulk_smem(prec_of<S>(), kBulkSlots);
-  auto k = step_bulk_kernel<S, COLL, kBulkSlots, MINB, false>;
+  auto k = step_bulk_kernel<S, COLL, kBulkSlots, MINB, false, DYN>;
   const cudaError_t e =
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -87,7 +88,8 @@ static cudaError_t occ(int variant, int* per_sm) {
     case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 6, false>, 128, 0);
     case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 8, false>, 128, 0);
     case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<S, COLL, 10, false>, 128, 0);
-    default: return occ_bulk<S, COLL, 6>(per_sm);
+    case 5: return occ_bulk<S, COLL, 6, true>(per_sm);
+    default: return occ_bulk<S, COLL, 6, false>(per_sm);
   }
 }
 

@@ -16,7 +16,9 @@ void set_bulk_smem_attr() {
   if (done) return;
   const size_t ring = step_bulk_smem(prec_of<S>(), kBulkSlots);
   const size_t nn = nn_smem_bytes<R>(kBulkThreads / 32);
-  cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true>,
+  cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(ring > nn ? ring : nn));
+  cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true, true>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(ring > nn ? ring : nn));
   done = true;
 }

@@ -180,6 +180,7 @@ __device__ __forceinline__ void fluid_node(S* __restrict__ B, const Member& m,
 __device__ __forceinline__ void write_partial(const StepParams& p, int64_t t, int slot, double fx,
                                               double fy, bool touched, bool bad, int* status) {
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, DEV_NONFINITE);
+  if (slot < 0) return;   // a strip without counted solid nodes has no partial
   double* part = p.partials + (size_t)(t & 1) * 2 * p.partial_stride;
   if (!__syncthreads_or(touched)) {
     if (threadIdx.x == 0) {
@@ -585,13 +586,15 @@ __global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
     ext_dispatch<S>(p, (int)blockIdx.x, nn_smem);
     return;
   }
-  const int b = (int)blockIdx.x - p.nn_blocks;             // stream-and-collide block
-  const int nblocks = (int)gridDim.x - p.nn_blocks - p.n_members;
+  // force-reduction blocks of the previous step come next, ahead of the
+  // stream-and-collide blocks, so they finish early
   const int64_t t = step_index(p);
-  if (b >= nblocks) {
-    if (p.reduce_prev && t >= 1) reduce_force(p, b - nblocks, t - 1);
+  if ((int)blockIdx.x < p.nn_blocks + p.n_members) {
+    if (p.reduce_prev && t >= 1) reduce_force(p, (int)blockIdx.x - p.nn_blocks, t - 1);
     return;
   }
+  const int b = (int)blockIdx.x - p.nn_blocks - p.n_members;   // stream-and-collide block
+  const int nblocks = (int)gridDim.x - p.nn_blocks - p.n_members;
   double fx = 0.0, fy = 0.0;
   bool touched = false, bad = false;
   if (p.n_members == 1) {
@@ -606,7 +609,7 @@ __global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
     const Member& m = p.members[p.strip_member[b]];
     const Scalars<R> sc(m);
     reg_strip<S, COLL>(p, m, sc, t, b - m.strip_first, fx, fy, touched, bad);
-    write_partial(p, t, b, fx, fy, touched, bad, m.status);
+    write_partial(p, t, p.strip_force ? p.strip_force[b] : b, fx, fy, touched, bad, m.status);
   }
 }
 
@@ -840,10 +843,217 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
       }
     }
   }
-  write_partial(p, t, slot, fx, fy, touched, bad, m.status);
+  // the block's force partial: its strip's slot when partials go per strip
+  write_partial(p, t, p.strip_force ? p.strip_force[slot] : slot, fx, fy, touched, bad, m.status);
 }
 
-template <typename S, int COLL, int NS, int MINB, bool EXT>
+// Persistent staged kernel with dynamic strip assignment (variant 5): a
+// resident-sized grid whose producers take the next strip of the launch
+// table from a global counter, so blocks that run faster take more strips.
+// The producer records each staged row's strip and row in the slot; consumer
+// warps follow it, switching member records when the strip changes.  Forces
+// go to one partial per strip and consumer warp, so the fixed-order
+// reduction stays independent of which block took which strip.  The last
+// block to finish resets the counters for the next launch.
+template <typename S, int COLL, int NS>
+__device__ __forceinline__ void bulk_run_dyn(const StepParams& p, int n_blocks,
+                                             unsigned char* smem) {
+  using R = typename Compute<S>::R;
+  using Lay = BulkLayout<S>;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * Lay::STAGE_BYTES);
+  uint64_t* empty = full + NS;
+  __shared__ int s_abort;
+  __shared__ int s_strip[NS];     // global strip of the row staged in each slot (-1: none left)
+  __shared__ int s_row[NS];       // row of that strip
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int strips_total = p.dyn_strips;
+  unsigned long long* ctr = p.dyn_ctr;   // [0] next strip, [1] finished blocks
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_wait();
+  const int64_t t = step_index(p);
+  const int rows = p.rows;
+
+  if (warp == kConsumerWarps) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int k = 0;
+      // the next strip is claimed one strip ahead, so the atomic's round trip
+      // overlaps the copies of the current strip
+      int sg = (int)atomicAdd(ctr, 1ull);
+      for (;;) {
+        const int sg_next = sg >= strips_total ? sg : (int)atomicAdd(ctr, 1ull);
+        const bool done = sg >= strips_total;
+        const Member& m = p.members[done || p.n_members == 1 ? 0 : p.strip_member[sg]];
+        const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
+        const int ls = done ? 0 : sg - m.strip_first;
+        const int y0 = (ls / m.tiles_x) * rows;
+        const int x0 = (ls % m.tiles_x) << 7;
+        const int lead = x0 == 0 ? 0 : Lay::A;
+        const int nrows = done ? 1 : min(rows, m.ny - y0);
+        for (int r = 0; r < nrows; ++r) {
+          const int slot = k % NS;
+          if (k >= NS && !mbar_wait_bounded(&empty[slot], (uint32_t)(((k / NS) - 1) & 1))) {
+            atomicOr(m.status, DEV_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+          if (s_abort) break;
+          if (done) {
+            // no strips left: an empty stage tells the consumers to stop
+            s_strip[slot] = -1;
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[slot]))
+                         : "memory");
+            ++k;
+            break;
+          }
+          s_strip[slot] = sg;
+          s_row[slot] = r;
+          const int y = y0 + r;
+          unsigned char* st = smem + slot * Lay::STAGE_BYTES;
+          mbar_expect_tx(&full[slot], Lay::TX_BYTES);
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            int sy = y - cy(i);
+            sy = sy < 0 ? sy + m.ny : (sy >= m.ny ? sy - m.ny : sy);
+            const int sx = cx(i) == 1 ? x0 - lead : x0;
+            bulk_copy_g2s(st + i * Lay::SEG_BYTES, A + i * m.plane + sy * m.pitch + sx,
+                          (uint32_t)Lay::SEG_BYTES, &full[slot]);
+          }
+          bulk_copy_g2s(st + 9 * Lay::SEG_BYTES, m.solid_bits + y * m.words_per_row + (x0 >> 5),
+                        16u, &full[slot]);
+          ++k;
+        }
+        if (done || s_abort) break;
+        sg = sg_next;
+      }
+      // no copy may land after the block exits
+      for (int kk = k > NS ? k - NS : 0; kk < k; ++kk)
+        mbar_wait_bounded(&full[kk % NS], (uint32_t)((kk / NS) & 1));
+    }
+  } else {
+    // ---------------- consumers ----------------
+    const int lx = threadIdx.x;     // column within the 128-wide tile
+    double* part = p.partials + (size_t)(t & 1) * 2 * p.partial_stride;
+    double fx = 0.0, fy = 0.0;
+    bool touched = false, bad = false;
+    int cur = -1;
+    const Member* mp = p.members;
+    const S* A = nullptr;
+    S* B = nullptr;
+    int plane = 0, pitch = 0, nx = 0, ny = 0, y0 = 0, x = 0, lead = 0;
+    bool west = false, east = false, skip = true, ext = false;
+    Scalars<R> sc(p.members[0]);
+    // the strip's force partial of this warp, in fixed slots
+    auto flush = [&]() {
+      if (cur < 0) return;
+      const bool any = __any_sync(0xffffffffu, touched);
+      double ax = fx, ay = fy;
+      if (any) warp_sum2(ax, ay);
+      const int fs = p.strip_force[cur];
+      if (lane == 0 && fs >= 0) {
+        const int slot = fs * kConsumerWarps + warp;
+        part[2 * slot] = any ? ax : 0.0;
+        part[2 * slot + 1] = any ? ay : 0.0;
+      }
+      if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(mp->status, DEV_NONFINITE);
+      fx = fy = 0.0;
+      touched = bad = false;
+    };
+    for (int j = 0;; ++j) {
+      const int slot = j % NS;
+      const bool ready = __all_sync(
+          0xffffffffu, !s_abort && mbar_wait_bounded(&full[slot], (uint32_t)((j / NS) & 1)));
+      if (!ready) {
+        atomicOr(mp->status, DEV_TIMEOUT);
+        s_abort = 1;
+        break;
+      }
+      const int sg = s_strip[slot];
+      if (sg < 0) break;
+      if (sg != cur) {
+        flush();
+        cur = sg;
+        mp = p.members + (p.n_members == 1 ? 0 : p.strip_member[sg]);
+        A = static_cast<const S*>(mp->buf[p.q]);
+        B = static_cast<S*>(mp->buf[1 - p.q]);
+        plane = mp->plane;
+        pitch = mp->pitch;
+        nx = mp->nx;
+        ny = mp->ny;
+        const int ls = sg - mp->strip_first;
+        y0 = (ls / mp->tiles_x) * p.rows;
+        const int x0 = (ls % mp->tiles_x) << 7;
+        lead = x0 == 0 ? 0 : Lay::A;
+        x = x0 + lx;
+        west = !mp->x_periodic && x == 0;
+        east = !mp->x_periodic && x == nx - 1;
+        skip = x >= nx;
+        ext = east && mp->east_mode == EAST_EXTERNAL;
+        sc = Scalars<R>(*mp);
+      }
+      const int y = y0 + s_row[slot];
+      const unsigned char* st = smem + slot * Lay::STAGE_BYTES;
+      if (!skip) {
+        const S* seg = reinterpret_cast<const S*>(st);
+        R h[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int idx = cx(i) == 1 ? lx - 1 + lead : (cx(i) == 0 ? lx : lx + 1);
+          h[i] = to_r<R>(seg[i * Lay::SEG + (idx < 0 ? 0 : idx)]);
+        }
+        if (x == 0 || x == nx - 1) {
+          // periodic wrap of the x +- 1 neighbours at the lattice edges
+          const int ym = y == 0 ? ny - 1 : y - 1;
+          const int yp = y == ny - 1 ? 0 : y + 1;
+          if (x == 0) {
+            h[1] = to_r<R>(A[1 * plane + y * pitch + nx - 1]);
+            h[5] = to_r<R>(A[5 * plane + ym * pitch + nx - 1]);
+            h[8] = to_r<R>(A[8 * plane + yp * pitch + nx - 1]);
+          }
+          if (x == nx - 1) {
+            h[3] = to_r<R>(A[3 * plane + y * pitch]);
+            h[6] = to_r<R>(A[6 * plane + ym * pitch]);
+            h[7] = to_r<R>(A[7 * plane + yp * pitch]);
+          }
+        }
+        const uint32_t word =
+            reinterpret_cast<const uint32_t*>(st + 9 * Lay::SEG_BYTES)[lx >> 5];
+        const int o = y * pitch + x;
+        if ((word >> (lx & 31)) & 1u) {
+          solid_node<S, R>(A, B, *mp, x, y, o, h, fx, fy, touched);
+        } else if (!ext) {
+          fluid_node<S, R, COLL>(B, *mp, sc, t, west, east, y, o, h, bad);
+        }
+      }
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot]))
+                     : "memory");
+    }
+    flush();
+  }
+  // the last block out resets the counters for the next launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ctr + 1, 1ull) == (unsigned long long)(n_blocks - 1)) {
+      ctr[0] = 0ull;
+      ctr[1] = 0ull;
+      __threadfence();
+    }
+  }
+}
+
+template <typename S, int COLL, int NS, int MINB, bool EXT, bool DYN>
 __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const StepParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   pdl_launch_dependents();
@@ -852,18 +1062,23 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
     ext_dispatch<S>(p, (int)blockIdx.x, smem);
     return;
   }
-  const int b = (int)blockIdx.x - p.nn_blocks;             // stream-and-collide block
-  const int nblocks = (int)gridDim.x - p.nn_blocks - p.n_members;
-  if (b >= nblocks) {
+  // force-reduction blocks of the previous step come next, ahead of the
+  // stream-and-collide blocks, so they finish early
+  if ((int)blockIdx.x < p.nn_blocks + p.n_members) {
     pdl_wait();
     const int64_t t = step_index(p);
-    if (p.reduce_prev && t >= 1) reduce_force(p, b - nblocks, t - 1);
+    if (p.reduce_prev && t >= 1) reduce_force(p, (int)blockIdx.x - p.nn_blocks, t - 1);
     return;
   }
-  if (p.n_members == 1) {
+  const int b = (int)blockIdx.x - p.nn_blocks - p.n_members;   // stream-and-collide block
+  const int nblocks = (int)gridDim.x - p.nn_blocks - p.n_members;
+  if (DYN) {
+    bulk_run_dyn<S, COLL, NS>(p, nblocks, smem);
+  } else if (p.n_members == 1) {
     // blocks part_count apart share the strips: part_count = strips gives one
     // strip per block, fewer blocks make them stream several strips each
-    bulk_run<S, COLL, NS>(p, p.m0, b, p.m0.part_count, b, smem);
+    bulk_run<S, COLL, NS>(p, p.m0, b, p.m0.strip_count > nblocks ? nblocks : p.m0.strip_count, b,
+                          smem);
   } else {
     // stage this block's member record in shared memory once (coalesced),
     // instead of every thread chasing its fields in global memory
@@ -877,7 +1092,7 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
       for (int w = threadIdx.x; w < kWords; w += 32) dst[w] = src[w];
     }
     __syncthreads();
-    bulk_run<S, COLL, NS>(p, s_member, b - s_member.part_first, s_member.part_count, b, smem);
+    bulk_run<S, COLL, NS>(p, s_member, b - s_member.blk_first, s_member.blk_count, b, smem);
   }
 }
 
@@ -885,9 +1100,10 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
 // Variants 0-2: the register-pipelined kernel with __launch_bounds__ minimum
 // resident blocks of 128 threads per SM of 6, 8, 10.  Variant 3: the
 // warp-specialised staged kernel (4-slot ring), one block per strip.
-// Variant 4: the same on a resident-sized grid, each block streaming several
-// strips through its ring.
-constexpr int kVariants = 5;
+// Variant 4: the same on a resident-sized grid, each block streaming a fixed
+// share of the strips through its ring.  Variant 5: the resident-sized grid
+// taking strips from a global counter (dynamic balance).
+constexpr int kVariants = 6;
 constexpr int kBulkSlots = 4;
 
 template <typename S>
@@ -912,7 +1128,7 @@ inline void launch_pdl(Kernel kernel, int grid, int threads, size_t smem, cudaSt
   cudaLaunchKernelEx(&cfg, kernel, p);
 }
 
-template <typename S, int COLL, int MINB, bool EXT>
+template <typename S, int COLL, int MINB, bool EXT, bool DYN>
 void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
   // the dynamic shared memory attribute is set by the occupancy query that
   // every group runs at creation (occ_bulk), or for the network kernels at
@@ -920,7 +1136,7 @@ void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
   using R = typename Compute<S>::R;
   size_t smem = step_bulk_smem(prec_of<S>(), kBulkSlots);
   if (EXT) smem = smem > nn_smem_bytes<R>(kBulkThreads / 32) ? smem : nn_smem_bytes<R>(kBulkThreads / 32);
-  launch_pdl(step_bulk_kernel<S, COLL, kBulkSlots, MINB, EXT>, p.nn_blocks + blocks + p.n_members,
+  launch_pdl(step_bulk_kernel<S, COLL, kBulkSlots, MINB, EXT, DYN>, p.nn_blocks + blocks + p.n_members,
              kBulkThreads, smem, s, p);
 }
 
@@ -933,7 +1149,8 @@ void launch_v(const StepParams& p, int variant, int blocks, cudaStream_t s) {
     case 0: launch_pdl(step_kernel<S, COLL, 6, EXT>, g, 128, dyn, s, p); break;
     case 1: launch_pdl(step_kernel<S, COLL, 8, EXT>, g, 128, dyn, s, p); break;
     case 2: launch_pdl(step_kernel<S, COLL, 10, EXT>, g, 128, dyn, s, p); break;
-    default: launch_bulk<S, COLL, 6, EXT>(p, blocks, s); break;
+    case 5: launch_bulk<S, COLL, 6, EXT, true>(p, blocks, s); break;
+    default: launch_bulk<S, COLL, 6, EXT, false>(p, blocks, s); break;
   }
 }
 

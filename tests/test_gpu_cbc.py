@@ -134,6 +134,7 @@ def test_free_stream_fixed_point_and_batch(L):
     L.lbm_init_equilibrium(solo, rho, U + ux, uy)
     L.lbm_step(solo, 45)
     b = L.lbm_batch_create(sims)
+    L.lbm_batch_set_tiling(b, 4, 5)            # dynamic staged kernel with boundary blocks
     L.lbm_batch_step(b, 45)
     L.lbm_batch_sync(b)
     for k in (0, 2):

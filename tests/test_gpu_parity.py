@@ -293,7 +293,8 @@ def test_every_tiling_gives_the_same_populations(L, precision):
     init = random_smooth_state(nx, ny, seed=21, amp_u=0.03, amp_rho=0.01)
     kw = dict(tau=0.58, u_in=0.04, v_pert_amp=1e-3, seed=2)
     ref = None
-    for rows, variant in [(8, 1), (1, 0), (3, 2), (2, 3), (5, 3), (16, 4), (64, 4), (7, 4)]:
+    for rows, variant in [(8, 1), (1, 0), (3, 2), (2, 3), (5, 3), (16, 4), (64, 4), (7, 4), (4, 5),
+                          (9, 5), (100, 5)]:
         cfg = L.lbm_config_default(nx=nx, ny=ny, precision=precision, **kw)
         sim = L.lbm_create(cfg)
         L.lbm_set_tiling(sim, rows, variant)
