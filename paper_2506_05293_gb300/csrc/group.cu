@@ -252,16 +252,28 @@ void build_table(Group& g) {
       const lbm_allocator* a = g.sims[0]->have_alloc ? &g.sims[0]->alloc : nullptr;
       if (g.d_strip_force) {
         ck(cudaStreamSynchronize(g.stream), "table sync");
-        dev_free_raw(a, g.d_strip_force);
-        g.owned.erase(std::remove(g.owned.begin(), g.owned.end(), (void*)g.d_strip_force),
-                      g.owned.end());
+        for (void* q : {(void*)g.d_strip_force, (void*)g.d_strip_order}) {
+          dev_free_raw(a, q);
+          g.owned.erase(std::remove(g.owned.begin(), g.owned.end(), q), g.owned.end());
+        }
       }
       g.d_strip_force = (int32_t*)dev_alloc_raw(a, force.size() * sizeof(int32_t));
+      g.d_strip_order = (int32_t*)dev_alloc_raw(a, force.size() * sizeof(int32_t));
       g.owned.push_back(g.d_strip_force);
+      g.owned.push_back(g.d_strip_order);
       g.force_cap = (int)force.size();
     }
+    // launch order: the strips with counted solids (slower) first, then the rest
+    std::vector<int32_t> order;
+    order.reserve(force.size());
+    for (size_t k = 0; k < force.size(); ++k)
+      if (force[k] >= 0) order.push_back((int32_t)k);
+    for (size_t k = 0; k < force.size(); ++k)
+      if (force[k] < 0) order.push_back((int32_t)k);
     ck(cudaMemcpyAsync(g.d_strip_force, force.data(), force.size() * sizeof(int32_t),
                        cudaMemcpyHostToDevice, g.stream), "force table copy");
+    ck(cudaMemcpyAsync(g.d_strip_order, order.data(), order.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, g.stream), "order table copy");
   }
   int parts = g.blocks;
   for (int k = 0; k < n; ++k)
@@ -291,6 +303,7 @@ StepParams params(const Group& g, int q) {
   p.nn_block_member = g.d_nn_block_member;
   p.dyn_ctr = g.dyn_ctr;
   p.strip_force = g.use_strip_force ? g.d_strip_force : nullptr;
+  p.strip_order = g.use_strip_force ? g.d_strip_order : nullptr;
   p.dyn_strips = 0;
   for (const lbm_sim* s : g.sims) p.dyn_strips += step_strips(s->nx, s->ny, g.rows);
   return p;

@@ -78,6 +78,8 @@ struct StepParams {
   int32_t partial_stride;
   const int32_t* strip_force;     // per strip its force-partial slot (-1: no counted solid),
                                  // or null: one partial per block
+  const int32_t* strip_order;     // one block (or claim) per strip: the strip it takes, holding
+                                 // solids first; null: the natural order
   unsigned long long* dyn_ctr;   // variant 5: [next strip, finished blocks], zero between launches
   int32_t dyn_strips;            // variant 5: strips of the whole table
   int32_t nn_blocks;             // boundary blocks (the first blocks of the grid)
@@ -197,6 +199,7 @@ struct Group {
   int nn_cap = 0;                // entries of d_nn_block_member
   unsigned long long* dyn_ctr = nullptr;   // counters of the dynamic staged variant
   int32_t* d_strip_force = nullptr;        // force-partial slot of each strip
+  int32_t* d_strip_order = nullptr;        // launch order of the strips
   int force_cap = 0;
   bool use_strip_force = false;
   int nn_blocks = 0;             // network blocks of the current table

@@ -606,10 +606,11 @@ __global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
       reg_strip<S, COLL>(p, p.m0, sc, t, s, fx, fy, touched, bad);
     write_partial(p, t, b, fx, fy, touched, bad, p.m0.status);
   } else {
-    const Member& m = p.members[p.strip_member[b]];
+    const int sg = p.strip_order ? p.strip_order[b] : b;   // strips holding solids first
+    const Member& m = p.members[p.strip_member[sg]];
     const Scalars<R> sc(m);
-    reg_strip<S, COLL>(p, m, sc, t, b - m.strip_first, fx, fy, touched, bad);
-    write_partial(p, t, p.strip_force ? p.strip_force[b] : b, fx, fy, touched, bad, m.status);
+    reg_strip<S, COLL>(p, m, sc, t, sg - m.strip_first, fx, fy, touched, bad);
+    write_partial(p, t, p.strip_force ? p.strip_force[sg] : sg, fx, fy, touched, bad, m.status);
   }
 }
 
@@ -844,7 +845,11 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
     }
   }
   // the block's force partial: its strip's slot when partials go per strip
-  write_partial(p, t, p.strip_force ? p.strip_force[slot] : slot, fx, fy, touched, bad, m.status);
+  // (recomputed here rather than kept live through the loop)
+  (void)slot;
+  const int bb = (int)blockIdx.x - p.nn_blocks - p.n_members;
+  const int sgb = p.strip_order ? p.strip_order[bb] : bb;
+  write_partial(p, t, p.strip_force ? p.strip_force[sgb] : sgb, fx, fy, touched, bad, m.status);
 }
 
 // Persistent staged kernel with dynamic strip assignment (variant 5): a
@@ -892,6 +897,7 @@ __device__ __forceinline__ void bulk_run_dyn(const StepParams& p, int n_blocks,
       for (;;) {
         const int sg_next = sg >= strips_total ? sg : (int)atomicAdd(ctr, 1ull);
         const bool done = sg >= strips_total;
+        if (!done && p.strip_order) sg = p.strip_order[sg];   // strips holding solids first
         const Member& m = p.members[done || p.n_members == 1 ? 0 : p.strip_member[sg]];
         const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
         const int ls = done ? 0 : sg - m.strip_first;
@@ -1072,12 +1078,15 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
   }
   const int b = (int)blockIdx.x - p.nn_blocks - p.n_members;   // stream-and-collide block
   const int nblocks = (int)gridDim.x - p.nn_blocks - p.n_members;
+  // one block per strip: the strip order puts strips holding solid nodes first,
+  // so their extra work overlaps the rest instead of trailing it
+  const int sb = p.strip_order ? p.strip_order[b] : b;
   if (DYN) {
     bulk_run_dyn<S, COLL, NS>(p, nblocks, smem);
   } else if (p.n_members == 1) {
     // blocks part_count apart share the strips: part_count = strips gives one
     // strip per block, fewer blocks make them stream several strips each
-    bulk_run<S, COLL, NS>(p, p.m0, b, p.m0.strip_count > nblocks ? nblocks : p.m0.strip_count, b,
+    bulk_run<S, COLL, NS>(p, p.m0, sb, p.m0.strip_count > nblocks ? nblocks : p.m0.strip_count, 0,
                           smem);
   } else {
     // stage this block's member record in shared memory once (coalesced),
@@ -1087,12 +1096,12 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
     static_assert(sizeof(Member) % sizeof(uint64_t) == 0, "Member must be 8-byte sized");
     if (threadIdx.x < 32) {
       const uint64_t* src =
-          reinterpret_cast<const uint64_t*>(p.members + p.strip_member[b]);
+          reinterpret_cast<const uint64_t*>(p.members + p.strip_member[sb]);
       uint64_t* dst = reinterpret_cast<uint64_t*>(&s_member);
       for (int w = threadIdx.x; w < kWords; w += 32) dst[w] = src[w];
     }
     __syncthreads();
-    bulk_run<S, COLL, NS>(p, s_member, b - s_member.blk_first, s_member.blk_count, b, smem);
+    bulk_run<S, COLL, NS>(p, s_member, sb - s_member.blk_first, s_member.blk_count, 0, smem);
   }
 }
 
