@@ -366,7 +366,7 @@ def run_ours(args):
         rows, variant = args.rows, args.variant          # fixed tiling (profiling)
         L.lbm_batch_set_tiling(batch, rows, variant)
     else:
-        rows, variant, _ = L.lbm_batch_autotune(batch, steps=10, flush_bytes=flush_bytes)
+        rows, variant, _ = L.lbm_batch_autotune(batch, steps=30, flush_bytes=flush_bytes)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda") if flush_mode else None
 
     with torch.cuda.stream(stream):

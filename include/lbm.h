@@ -298,12 +298,12 @@ lbm_status lbm_device_state(lbm_sim* sim, void** base, int64_t* pitch, int64_t* 
 lbm_status lbm_set_tiling(lbm_sim* sim, int32_t rows, int32_t variant);
 lbm_status lbm_get_tiling(lbm_sim* sim, int32_t* rows, int32_t* variant);
 
-/* Autotuner: time `steps` (1..10000) single steps of every candidate tiling
- * (rows 2, 4, 8, 12, 16, 20, 24, 32, 40, 48, 64 x the six variants) with CUDA
- * events on the sim's
- * stream and keep the fastest; *best_ms (nullable) gets its mean step time.
- * With flush_bytes > 0 a scratch buffer of that size is written before each
- * timed step so the step starts from a cold L2.  The populations, step
+/* Autotuner: time `steps` (1..10000) steps of every candidate tiling (rows 2,
+ * 4, 8, 12, 16, 20, 24, 32, 40, 48, 64 x the six variants) with CUDA events on
+ * the sim's stream, back to back as a run executes them, and keep the fastest;
+ * *best_ms (nullable) gets its mean step time.  With flush_bytes > 0 a scratch
+ * buffer of that size is written before each step, which is then timed alone,
+ * so every step starts from a cold L2.  The populations, step
  * counter, force series and fallback count are restored afterwards.  Uses
  * temporary device memory (one population buffer + flush_bytes). */
 lbm_status lbm_autotune(lbm_sim* sim, int32_t steps, int64_t flush_bytes, float* best_ms);

@@ -601,19 +601,34 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
         for (lbm_sim* s : g.sims) s->last_group = &g;
         g.pending = false;
         float total = 0.f;
-        for (int k = 0; k < steps + 2; ++k) {
-          const int q = g.sims[0]->cur;
-          if (flush && k >= 2)
-            ck(cudaMemsetAsync(flush, k & 0xff, (size_t)flush_bytes, g.stream), "flush");
-          ck(cudaEventRecord(e0, g.stream), "event");
-          enqueue(g, q, g.sims[0]->t_host, -1, g.pending);
+        if (flush) {
+          // L2-resident working set: every step timed alone after a flush
+          for (int k = 0; k < steps + 2; ++k) {
+            const int q = g.sims[0]->cur;
+            if (k >= 2)
+              ck(cudaMemsetAsync(flush, k & 0xff, (size_t)flush_bytes, g.stream), "flush");
+            ck(cudaEventRecord(e0, g.stream), "event");
+            enqueue(g, q, g.sims[0]->t_host, -1, g.pending);
+            ck(cudaEventRecord(e1, g.stream), "event");
+            advance_members(g, 1);
+            g.pending = true;
+            ck(cudaEventSynchronize(e1), "event sync");
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, e0, e1), "event time");
+            if (k >= 2) total += ms;   // two untimed warm-up steps
+          }
+        } else {
+          // steps back to back, as a run executes them (consecutive launches
+          // overlap their set-up through programmatic dependent launch)
+          for (int k = 0; k < steps + 2; ++k) {
+            if (k == 2) ck(cudaEventRecord(e0, g.stream), "event");
+            enqueue(g, g.sims[0]->cur, g.sims[0]->t_host, -1, g.pending);
+            advance_members(g, 1);
+            g.pending = true;
+          }
           ck(cudaEventRecord(e1, g.stream), "event");
-          advance_members(g, 1);
-          g.pending = true;
           ck(cudaEventSynchronize(e1), "event sync");
-          float ms = 0.f;
-          ck(cudaEventElapsedTime(&ms, e0, e1), "event time");
-          if (k >= 2) total += ms;   // two untimed warm-up steps
+          ck(cudaEventElapsedTime(&total, e0, e1), "event time");
         }
         const float mean = total / (float)steps;
         if (mean < best) {
