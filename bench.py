@@ -18,6 +18,12 @@ angle of attack 4 degrees, Re 1000, U = 0.04, MRT) and ``vortex_batch_256``
 (256 convected-vortex lattices of uneven sizes, 49,153,467 nodes, with the
 characteristic outflow, sigma 0.25, kappa2 = Ma = 0.1, Re 750).
 
+The line also carries ``accuracy``, the other half of the metric: the errors
+of C_D mean, C_L RMS and St of the NN outflow and of Zou & He on the same
+truncated domain (cylinder D = 40, Re 100, wake 4D) against the 32D-long run,
+with the network trained on the GPU from that run (``--no-accuracy`` skips
+this minute-long study).
+
 Prints one JSON line.
 """
 from __future__ import annotations
@@ -337,6 +343,30 @@ def _drain(L, sim, call):
         return None
 
 
+def accuracy_study():
+    """The second half of the metric: C_D mean, C_L RMS and St errors of the
+    NN outflow and of Zou & He on the same truncated domain (cylinder D = 40,
+    Re 100, wake 4D) against the 32D-long run, the network trained on the GPU
+    from the long run (runs from rest and restarted from the developed flow),
+    plus Zou & He on 8D and 16D wakes and each run's cost per step.  A failure
+    is reported in the line instead of aborting the bench."""
+    try:
+        from paper_2506_05293_gb300 import workflow
+        t0 = time.perf_counter()
+        res = workflow.run_study(workflow.Study())
+        out = {"case": (f"cylinder D={res['D']} Re={res['Re']:g} {res['collision']}, wake 4D "
+                        f"(nx {res['nx_short']}) vs 32D (nx {res['nx_long']}), ny {res['ny']}, "
+                        f"statistics over {res['t_stat']} steps after {res['t_trans']}"),
+               "reference": res["reference"], "training": res["training"],
+               "runs": {k: {"err": v["err"], "ms_per_step": v["ms_per_step"], "nx": v["nx"],
+                            **({"fallbacks": v["fallbacks"]} if "fallbacks" in v else {})}
+                        for k, v in res["runs"].items()},
+               "wall_s": time.perf_counter() - t0}
+        return out
+    except Exception as ex:   # reported, not fatal
+        return {"error": f"{type(ex).__name__}: {ex}"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -466,6 +496,9 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return 0
     cpu = None
+    accuracy = None
+    if world == 1 and not args.no_accuracy:
+        accuracy = accuracy_study()
     if world == 1 and not args.no_cpu_baseline:
         glups_cpu, dt_cpu, _, _ = cpu_oracle_sample(wl, args.cpu_steps)
         cpu = {"value": glups_cpu, "unit": "GLUPS", "cores": 1, "kind": "oracle",
@@ -499,6 +532,7 @@ def run_ours(args):
                         f"{e2e_steps} batch steps; lbm_forces + lbm_fields to host"},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
+        "accuracy": accuracy,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -516,6 +550,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=sorted(BYTES_PER_NODE))
     ap.add_argument("--cpu-steps", type=int, default=120)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the NN vs Zou & He truncation study (about a minute)")
     ap.add_argument("--rows", type=int, default=0, help="fixed tiling instead of the autotuner")
     ap.add_argument("--variant", type=int, default=3)
     args = ap.parse_args()

@@ -691,7 +691,7 @@ constexpr int kBulkThreads = 32 * (kConsumerWarps + 1);
 
 template <typename S, int COLL, int NS>
 __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, int lb, int gk,
-                                         int slot, unsigned char* smem) {
+                                         unsigned char* smem) {
   using R = typename Compute<S>::R;
   using Lay = BulkLayout<S>;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * Lay::STAGE_BYTES);
@@ -846,7 +846,6 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
   }
   // the block's force partial: its strip's slot when partials go per strip
   // (recomputed here rather than kept live through the loop)
-  (void)slot;
   const int bb = (int)blockIdx.x - p.nn_blocks - p.n_members;
   const int sgb = p.strip_order ? p.strip_order[bb] : bb;
   write_partial(p, t, p.strip_force ? p.strip_force[sgb] : sgb, fx, fy, touched, bad, m.status);
@@ -1086,7 +1085,7 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
   } else if (p.n_members == 1) {
     // blocks part_count apart share the strips: part_count = strips gives one
     // strip per block, fewer blocks make them stream several strips each
-    bulk_run<S, COLL, NS>(p, p.m0, sb, p.m0.strip_count > nblocks ? nblocks : p.m0.strip_count, 0,
+    bulk_run<S, COLL, NS>(p, p.m0, sb, p.m0.strip_count > nblocks ? nblocks : p.m0.strip_count,
                           smem);
   } else {
     // stage this block's member record in shared memory once (coalesced),
@@ -1101,7 +1100,7 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
       for (int w = threadIdx.x; w < kWords; w += 32) dst[w] = src[w];
     }
     __syncthreads();
-    bulk_run<S, COLL, NS>(p, s_member, sb - s_member.blk_first, s_member.blk_count, 0, smem);
+    bulk_run<S, COLL, NS>(p, s_member, sb - s_member.blk_first, s_member.blk_count, smem);
   }
 }
 
