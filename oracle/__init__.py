@@ -19,6 +19,9 @@ lbm   -- lattice (Sec. 2.1, Eqs. 1-4), BGK and MRT collision, pull streaming,
          plus a whole-domain solver that applies them in the paper's order.
 mlp   -- the small MLPs of Secs. 3.1 and 4.2: forward, hand-derived backward,
          MSE loss (Eq. 16) and Adam.
+cbc_segment -- training of the CBC tuner through short simulation segments
+         (Sec. 4.2): the truncated lattice's forward pass in torch float64 and
+         its reverse-mode gradient with respect to the tuner's parameters.
 post  -- force coefficients (Eq. 12) and the Strouhal number (Sec. 2.3).
 rng   -- the SplitMix64 counter-based generator used for the inlet
          perturbation (an independent copy lives on the CUDA side).
