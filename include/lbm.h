@@ -247,6 +247,67 @@ lbm_status lbm_nn_loss_grad(const float* dev_rows, int64_t n_rows, const int32_t
                             int64_t n_batches, const lbm_train_opts* opts, const lbm_mlp* net,
                             double* losses, float* grads);
 
+/* ---- Training the CBC tuner through short simulation segments (Sec. 4.2) ----
+ * A segment starts from a reference state of the truncated lattice (nx x ny,
+ * BGK with tau, y periodic, no solid nodes, east column L = nx - 1 with the
+ * characteristic outflow of lbm_set_outflow_cbc and the tuner), runs n_t steps
+ * and is compared with the reference state n_t steps later over the last n_t
+ * columns (x = L - n_t + 1 .. L, all rows):
+ *   loss = mean (rho - rho_ref)^2 + mean over nodes and both components
+ *          (U - U_ref)^2,
+ * rho and U being the moments of the stored populations.  A batch's loss is
+ * the mean of its segments' losses.  Those columns at t0 + n_t depend only on
+ * the last W = max(2 n_t, 3) columns at t0 (so the west inlet never enters),
+ * and the library runs each segment on that strip alone.  All arithmetic is
+ * FP64; the gradient with respect to the tuner's parameters is the exact
+ * reverse-mode derivative of that computation (adjoint stream-and-collide
+ * steps, forward-mode dual numbers for the east node), summed in a fixed
+ * order (bitwise reproducible). */
+typedef struct {
+  int32_t nx, ny;           /* truncated lattice; nx >= W + 1, 3 <= ny <= 65535 */
+  int32_t n_t;              /* steps per segment, >= 1 */
+  double tau, rho_out;      /* BGK relaxation time (> 1/2); outflow far-field density */
+  double sigma, kappa2, mach, length;  /* as lbm_set_outflow_cbc (length 0 = nx) */
+  int32_t exact_mass;       /* f_0 correction: 0 Eq. 28, 1 exact mass */
+  const double* bank;       /* device, [n_states][9][ny][bank_width]: populations f (not
+                               shifted) of the last bank_width columns of the truncated
+                               lattice, e.g. written by lbm_copy_columns; caller-owned */
+  int32_t n_states, bank_width;   /* W <= bank_width <= nx */
+  const int32_t* init_state;      /* host [n_seg]: bank index of each segment's start */
+  const int32_t* final_state;     /* host [n_seg]: bank index of its reference at start + n_t */
+  int32_t n_seg;                  /* 1..65535 */
+  void* stream;             /* cudaStream_t; NULL = legacy default stream */
+} lbm_cbc_segments;
+
+/* Copy the populations f = h + w (FP64, not shifted) of columns
+ * [x0, x0 + width) of the sim's current state, every row, into device memory
+ * dev_out [9][ny][width] (caller-owned, 9 ny width doubles).  Enqueued on the
+ * sim's stream; LBM_ERR_ARG if the columns leave the lattice. */
+lbm_status lbm_copy_columns(lbm_sim* sim, int32_t x0, int32_t width, double* dev_out);
+
+/* Mean loss over all n_seg segments (host double[1]) and, if grad is not
+ * NULL, its gradient with respect to the tuner's parameters (host
+ * double[n_params], the layout of lbm_mlp.params), evaluated at params (host
+ * double[n_params]).  tuner gives the architecture (6 -> 1..2, 1..3 layers,
+ * hidden layers of at most 32 units, act 0 tanh / 1 leaky) and in_mean /
+ * in_std (NULL = 0 / 1); tuner->params is ignored.  Allocates its scratch
+ * (about n_seg (n_t + 4) 9 ny W doubles), synchronous. */
+lbm_status lbm_cbc_segment_grad(const lbm_cbc_segments* segs, const lbm_mlp* tuner,
+                                const double* params, double* loss, double* grad);
+
+/* n_steps Adam steps (Kingma & Ba 2015, lr / beta1 / beta2 / eps / adam_t0 /
+ * stream of opts; batch_rows and max_cluster are ignored) on the segment loss:
+ * step k uses the batch of segments order[k*batch .. (k+1)*batch) (host
+ * int32, indices into the segment list).  params (host double[n_params]) is
+ * the starting point and receives the result; adam_m / adam_v (host
+ * double[n_params], nullable = zeros in and not returned) are the moments, in
+ * and out; loss_log (host double[n_steps], nullable) gets each batch's loss
+ * before its step.  Synchronous. */
+lbm_status lbm_cbc_tuner_train(const lbm_cbc_segments* segs, const lbm_mlp* tuner,
+                               const int32_t* order, int32_t batch, int64_t n_steps,
+                               const lbm_train_opts* opts, double* params, double* adam_m,
+                               double* adam_v, double* loss_log);
+
 /* Enqueue n time steps (n >= 0).  Each step: pull streaming (Eq. 1), momentum
  * exchange (Eqs. 13-14) and bounce-back (Eq. 11) at solid nodes, the west
  * inlet, the east outflow, and collision of all fluid nodes; the force on

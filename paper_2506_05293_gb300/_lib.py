@@ -46,6 +46,15 @@ class LbmTrainOpts(Structure):
                 ("max_cluster", c_int32), ("stream", c_void_p)]
 
 
+class LbmCbcSegments(Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("n_t", c_int32), ("tau", c_double),
+                ("rho_out", c_double), ("sigma", c_double), ("kappa2", c_double),
+                ("mach", c_double), ("length", c_double), ("exact_mass", c_int32),
+                ("bank", c_void_p), ("n_states", c_int32), ("bank_width", c_int32),
+                ("init_state", POINTER(c_int32)), ("final_state", POINTER(c_int32)),
+                ("n_seg", c_int32), ("stream", c_void_p)]
+
+
 # name -> (restype, argtypes); every function of include/lbm.h
 SIGNATURES = {
     "lbm_config_default": (c_int, [POINTER(LbmConfig)]),
@@ -72,6 +81,12 @@ SIGNATURES = {
     "lbm_nn_loss_grad": (c_int, [c_void_p, c_int64, POINTER(c_int32), c_int64,
                                  POINTER(LbmTrainOpts), POINTER(LbmMlp), POINTER(c_double),
                                  POINTER(c_float)]),
+    "lbm_copy_columns": (c_int, [c_void_p, c_int32, c_int32, c_void_p]),
+    "lbm_cbc_segment_grad": (c_int, [POINTER(LbmCbcSegments), POINTER(LbmMlp), POINTER(c_double),
+                                     POINTER(c_double), POINTER(c_double)]),
+    "lbm_cbc_tuner_train": (c_int, [POINTER(LbmCbcSegments), POINTER(LbmMlp), POINTER(c_int32),
+                                    c_int32, c_int64, POINTER(LbmTrainOpts), POINTER(c_double),
+                                    POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
     "lbm_step": (c_int, [c_void_p, c_int64]),
     "lbm_sync": (c_int, [c_void_p]),
     "lbm_time": (c_int, [c_void_p, POINTER(c_int64)]),

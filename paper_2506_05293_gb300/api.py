@@ -263,6 +263,80 @@ def lbm_nn_loss_grad(rows, order, layers, act="tanh", in_mean=None, in_std=None,
     return (losses, g) if grads else losses
 
 
+def lbm_copy_columns(sim, x0, width, out):
+    """Populations f (FP64, not shifted) of columns [x0, x0 + width) into the
+    device tensor ``out`` (9, ny, width), enqueued on the sim's stream."""
+    _check(_lib.load().lbm_copy_columns(sim.handle, int(x0), int(width), c_void_p(_devptr(out))))
+
+
+def _segments(bank, nx, n_t, tau, sigma, kappa2, mach, init_state, final_state, length=0.0,
+              rho_out=1.0, exact_mass=False, stream=None):
+    """LbmCbcSegments over a device bank (n_states, 9, ny, bank_width) float64."""
+    n_states, _, ny, width = (int(d) for d in bank.shape)
+    init = np.ascontiguousarray(init_state, dtype=np.int32)
+    fin = np.ascontiguousarray(final_state, dtype=np.int32)
+    if init.shape != fin.shape:
+        raise ValueError("init_state and final_state differ in length")
+    g = _lib.LbmCbcSegments()
+    g.nx, g.ny, g.n_t = int(nx), ny, int(n_t)
+    g.tau, g.rho_out = float(tau), float(rho_out)
+    g.sigma, g.kappa2, g.mach, g.length = float(sigma), float(kappa2), float(mach), float(length)
+    g.exact_mass = int(bool(exact_mass))
+    g.bank = c_void_p(_devptr(bank))
+    g.n_states, g.bank_width = n_states, width
+    g.init_state = init.ctypes.data_as(POINTER(ctypes.c_int32))
+    g.final_state = fin.ctypes.data_as(POINTER(ctypes.c_int32))
+    g.n_seg = int(init.size)
+    g.stream = c_void_p(int(stream)) if stream else None
+    return g, [init, fin]
+
+
+def _tuner_struct(tuner, act, in_mean, in_std):
+    m, keep = make_mlp(tuner, act, in_mean, in_std, 1.0)
+    flat = np.concatenate([np.concatenate([np.asarray(W, np.float64).ravel(),
+                                           np.asarray(b, np.float64).ravel()]) for W, b in tuner])
+    return m, keep, np.ascontiguousarray(flat)
+
+
+def lbm_cbc_segment_grad(bank, nx, n_t, tau, sigma, kappa2, mach, init_state, final_state, tuner,
+                         act="leaky", in_mean=None, in_std=None, params=None, grad=True, **kw):
+    """Mean segment loss and (grad=True) its flat FP64 gradient with respect to
+    the tuner's parameters, evaluated at ``params`` (flat float64, default the
+    tuner's own values in float64)."""
+    g, keep_g = _segments(bank, nx, n_t, tau, sigma, kappa2, mach, init_state, final_state, **kw)
+    m, keep, flat = _tuner_struct(tuner, act, in_mean, in_std)
+    p = flat if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    loss = np.zeros(1)
+    gr = np.zeros(p.size) if grad else None
+    _check(_lib.load().lbm_cbc_segment_grad(byref(g), byref(m), _dptr(p), _dptr(loss),
+                                            _dptr(gr) if grad else None))
+    del keep, keep_g
+    return (float(loss[0]), gr) if grad else float(loss[0])
+
+
+def lbm_cbc_tuner_train(bank, nx, n_t, tau, sigma, kappa2, mach, init_state, final_state, tuner,
+                        order, batch, act="leaky", in_mean=None, in_std=None, params=None,
+                        adam_m=None, adam_v=None, lr=1e-3, adam_t0=0, stream=None, **kw):
+    """Adam steps on the segment loss, batch k = segments order[k*batch:(k+1)*batch].
+    Returns (params, adam_m, adam_v, losses), all float64."""
+    g, keep_g = _segments(bank, nx, n_t, tau, sigma, kappa2, mach, init_state, final_state,
+                          stream=stream, **kw)
+    m, keep, flat = _tuner_struct(tuner, act, in_mean, in_std)
+    p = (flat if params is None else np.asarray(params, np.float64)).copy()
+    am = np.zeros(p.size) if adam_m is None else np.asarray(adam_m, np.float64).copy()
+    av = np.zeros(p.size) if adam_v is None else np.asarray(adam_v, np.float64).copy()
+    order = _order(order)
+    n_steps = order.size // int(batch) if int(batch) > 0 else 0
+    losses = np.zeros(n_steps)
+    o = lbm_train_opts_default(lr=float(lr), adam_t0=int(adam_t0), stream=stream)
+    _check(_lib.load().lbm_cbc_tuner_train(byref(g), byref(m),
+                                           order.ctypes.data_as(POINTER(ctypes.c_int32)),
+                                           int(batch), n_steps, byref(o), _dptr(p), _dptr(am),
+                                           _dptr(av), _dptr(losses)))
+    del keep, keep_g
+    return p, am, av, losses
+
+
 def unflatten(flat, like):
     """Split a flat parameter vector into [(W, b), ...] shaped like ``like``."""
     out, off = [], 0

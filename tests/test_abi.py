@@ -104,3 +104,48 @@ def test_training_rejects_bad_networks(L):
         assert ei.value.status == 1
     with pytest.raises(L.LbmError):
         L.lbm_nn_dataset_stats(0x1000, n_rows=0)
+
+
+class _FakeBank:
+    """Stands in for a device tensor: only its address and shape are read."""
+    is_cuda = True
+
+    def __init__(self, shape):
+        self.shape = shape
+
+    def is_contiguous(self):
+        return True
+
+    def data_ptr(self):
+        return 0x1000
+
+
+@pytest.mark.parametrize("bad", [dict(n_t=0), dict(nx=8), dict(bank_w=5), dict(bank_w=21),
+                                 dict(tau=0.5), dict(ny=2), dict(init=[0, 3]), dict(init=[-1, 0]),
+                                 dict(sizes=[7, 8, 1]), dict(sizes=[6, 8, 3]),
+                                 dict(sizes=[6, 33, 1]), dict(sizes=[6, 4, 4, 4, 1]),
+                                 dict(sigma=float("nan"))])
+def test_segment_gradient_rejects_bad_arguments_before_touching_the_device(L, bad):
+    """lbm_cbc_segment_grad checks its segments and tuner on the host first;
+    the bank pointer is never dereferenced here."""
+    from synth import glorot_mlp
+    kw = dict(n_t=4, nx=20, bank_w=10, tau=0.6, ny=12, init=[0, 1], sizes=[6, 8, 2],
+              sigma=0.5)
+    kw.update(bad)
+    bank = _FakeBank((3, 9, kw["ny"], kw["bank_w"]))
+    init = kw["init"]
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_cbc_segment_grad(bank, kw["nx"], kw["n_t"], kw["tau"], kw["sigma"], 0.1, 0.1,
+                               init, [2] * len(init), glorot_mlp(kw["sizes"], 0))
+    assert ei.value.status == 1
+
+
+def test_tuner_training_rejects_bad_arguments_before_touching_the_device(L):
+    from synth import glorot_mlp
+    bank = _FakeBank((3, 9, 12, 10))
+    net = glorot_mlp([6, 8, 1], 0)
+    for order, batch, lr in (([0, 5], 1, 1e-3), ([0, 1], 0, 1e-3), ([0, 1], 1, 0.0)):
+        with pytest.raises(L.LbmError) as ei:
+            L.lbm_cbc_tuner_train(bank, 20, 4, 0.6, 0.5, 0.1, 0.1, [0, 1], [2, 2], net, order,
+                                  batch, lr=lr)
+        assert ei.value.status == 1
