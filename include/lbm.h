@@ -285,6 +285,14 @@ typedef struct {
  * sim's stream; LBM_ERR_ARG if the columns leave the lattice. */
 lbm_status lbm_copy_columns(lbm_sim* sim, int32_t x0, int32_t width, double* dev_out);
 
+/* Normalisation of the tuner's inputs from the bank: per feature (p_x, u_x,
+ * v_x, p_y, u_y, v_y at the east column of every bank state, derivatives as in
+ * lbm_set_outflow_cbc with y periodic) the mean and the population standard
+ * deviation (below 1e-12: 1), FP64 sums in a fixed order, returned as host
+ * float[6] each.  Uses bank, n_states, ny, bank_width (>= 3) and stream of segs.
+ * Synchronous. */
+lbm_status lbm_cbc_feature_stats(const lbm_cbc_segments* segs, float* in_mean, float* in_std);
+
 /* Mean loss over all n_seg segments (host double[1]) and, if grad is not
  * NULL, its gradient with respect to the tuner's parameters (host
  * double[n_params], the layout of lbm_mlp.params), evaluated at params (host

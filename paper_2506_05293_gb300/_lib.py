@@ -82,6 +82,8 @@ SIGNATURES = {
                                  POINTER(LbmTrainOpts), POINTER(LbmMlp), POINTER(c_double),
                                  POINTER(c_float)]),
     "lbm_copy_columns": (c_int, [c_void_p, c_int32, c_int32, c_void_p]),
+    "lbm_cbc_feature_stats": (c_int, [POINTER(LbmCbcSegments), POINTER(c_float),
+                                      POINTER(c_float)]),
     "lbm_cbc_segment_grad": (c_int, [POINTER(LbmCbcSegments), POINTER(LbmMlp), POINTER(c_double),
                                      POINTER(c_double), POINTER(c_double)]),
     "lbm_cbc_tuner_train": (c_int, [POINTER(LbmCbcSegments), POINTER(LbmMlp), POINTER(c_int32),

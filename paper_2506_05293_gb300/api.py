@@ -291,6 +291,18 @@ def _segments(bank, nx, n_t, tau, sigma, kappa2, mach, init_state, final_state, 
     return g, [init, fin]
 
 
+def lbm_cbc_feature_stats(bank, stream=None):
+    """(in_mean[6], in_std[6]) of the tuner's features over every bank state."""
+    g, keep = _segments(bank, int(bank.shape[3]) + 1, 1, 0.6, 0.0, 0.0, 0.0, [0], [0],
+                        stream=stream)
+    mean = np.zeros(6, np.float32)
+    std = np.zeros(6, np.float32)
+    _check(_lib.load().lbm_cbc_feature_stats(byref(g), mean.ctypes.data_as(POINTER(c_float)),
+                                             std.ctypes.data_as(POINTER(c_float))))
+    del keep
+    return mean, std
+
+
 def _tuner_struct(tuner, act, in_mean, in_std):
     m, keep = make_mlp(tuner, act, in_mean, in_std, 1.0)
     flat = np.concatenate([np.concatenate([np.asarray(W, np.float64).ravel(),

@@ -174,6 +174,22 @@ __device__ void tuner_g(const SegParams& p, const T x[6], T s[2]) {
   s[1] = p.sizes[p.n_layers] > 1 ? a[1] : mk_t<T>(0.0);
 }
 
+// moments of the five stencil nodes (L, y), (L-1, y), (L-2, y), (L, y-1), (L, y+1)
+// (in[9n .. 9n+8]) and the six derivatives (p_x, u_x, v_x, p_y, u_y, v_y):
+// one-sided second order in x, central in y, p = rho / 3
+template <typename T>
+__device__ __forceinline__ void derivs_g(const T* in, T r[5], T u[5], T v[5], T fx[6]) {
+  const double cs2 = 1.0 / 3.0;
+#pragma unroll
+  for (int n = 0; n < 5; ++n) moments_g(in + 9 * n, r[n], u[n], v[n]);
+  fx[0] = 0.5 * (3.0 * (cs2 * r[0]) - 4.0 * (cs2 * r[1]) + cs2 * r[2]);
+  fx[1] = 0.5 * (3.0 * u[0] - 4.0 * u[1] + u[2]);
+  fx[2] = 0.5 * (3.0 * v[0] - 4.0 * v[1] + v[2]);
+  fx[3] = 0.5 * (cs2 * r[4] - cs2 * r[3]);
+  fx[4] = 0.5 * (u[4] - u[3]);
+  fx[5] = 0.5 * (v[4] - v[3]);
+}
+
 // The east node (L, y) of one step: in[0..44] the post-collision populations at t
 // of (L, y), (L-1, y), (L-2, y), (L, y-1), (L, y+1); in[45..50] the pulled known
 // populations f0(L, y), f1(L-1, y), f2(L, y-1), f4(L, y+1), f5(L-1, y-1),
@@ -187,18 +203,11 @@ __device__ void east_node_g(const SegParams& p, const T in[kEastInputs], T eps_s
                             T out[9], double* feat) {
   const double cs2 = 1.0 / 3.0;
   const double cs = sqrt(cs2);
-  T r[5], u[5], v[5];
-#pragma unroll
-  for (int n = 0; n < 5; ++n) moments_g(in + 9 * n, r[n], u[n], v[n]);
-  const T px = 0.5 * (3.0 * (cs2 * r[0]) - 4.0 * (cs2 * r[1]) + cs2 * r[2]);
-  const T ux = 0.5 * (3.0 * u[0] - 4.0 * u[1] + u[2]);
-  const T vx = 0.5 * (3.0 * v[0] - 4.0 * v[1] + v[2]);
-  const T py = 0.5 * (cs2 * r[4] - cs2 * r[3]);
-  const T uy = 0.5 * (u[4] - u[3]);
-  const T vy = 0.5 * (v[4] - v[3]);
+  T r[5], u[5], v[5], fx[6];
+  derivs_g(in, r, u, v, fx);
+  const T px = fx[0], ux = fx[1], vx = fx[2], py = fx[3], vy = fx[5];
   T sigma = mk_t<T>(p.sig_max), kappa2 = mk_t<T>(p.kap);
   if (p.n_layers > 0) {
-    const T fx[6] = {px, ux, vx, py, uy, vy};
     if (feat)
       for (int k = 0; k < 6; ++k) feat[k] = value(fx[k]);
     T s[2];
@@ -605,6 +614,47 @@ __global__ void adam_kernel(double* prm, double* m, double* v, const double* g, 
   prm[k] = prm[k] - lr * mh / (sqrt(vh) + eps);
 }
 
+// Mean and population standard deviation of the six tuner features over the
+// east nodes of every bank state (one block, fixed summation order).
+__global__ void __launch_bounds__(256) feature_stats_kernel(const double* bank, int n_states,
+                                                            int ny, int bank_w, double* out) {
+  __shared__ double red[6][256];
+  __shared__ double mean[6];
+  const int64_t n = (int64_t)n_states * ny;
+  for (int pass = 0; pass < 2; ++pass) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+      const int st = (int)(k / ny), y = (int)(k % ny);
+      const double* A = bank + (int64_t)st * 9 * ny * bank_w;
+      const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+      const int js[5] = {bank_w - 1, bank_w - 2, bank_w - 3, bank_w - 1, bank_w - 1};
+      const int ys[5] = {y, y, y, ym, yp};
+      double in[45], r[5], u[5], v[5], fx[6];
+      for (int q = 0; q < 5; ++q)
+        for (int i = 0; i < 9; ++i) in[9 * q + i] = A[((int64_t)i * ny + ys[q]) * bank_w + js[q]];
+      derivs_g(in, r, u, v, fx);
+      for (int f = 0; f < 6; ++f) {
+        const double d = pass == 0 ? fx[f] : fx[f] - mean[f];
+        acc[f] += pass == 0 ? d : d * d;
+      }
+    }
+    for (int f = 0; f < 6; ++f) red[f][threadIdx.x] = acc[f];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w)
+        for (int f = 0; f < 6; ++f) red[f][threadIdx.x] += red[f][threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x < 6) {
+      const double m = red[threadIdx.x][0] / (double)n;
+      if (pass == 0) mean[threadIdx.x] = m;
+      else out[6 + threadIdx.x] = sqrt(m);
+      if (pass == 0) out[threadIdx.x] = m;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename S>
 __global__ void copy_columns_kernel(const S* src, int ny, int64_t pitch, int64_t plane, int x0,
                                     int width, double* out) {
@@ -831,6 +881,31 @@ lbm_status lbm_copy_columns(lbm_sim* s, int32_t x0, int32_t width, double* dev_o
       copy_columns_kernel<__half><<<blocks, 256, 0, s->stream>>>(
           (const __half*)s->buf[s->cur], s->ny, s->pitch, s->plane, x0, width, dev_out);
     ck(cudaGetLastError(), "column copy");
+  } catch (const CudaError& ce) {
+    set_last_error(std::string(ce.what) + ": " + cudaGetErrorString(ce.e));
+    return LBM_ERR_CUDA;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_cbc_feature_stats(const lbm_cbc_segments* g, float* in_mean, float* in_std) {
+  using namespace lbm;
+  if (!g || !in_mean || !in_std) return seg_fail(LBM_ERR_ARG, "segs, in_mean and in_std are required");
+  if (!g->bank || g->n_states < 1) return seg_fail(LBM_ERR_ARG, "bank must hold >= 1 state");
+  if (g->ny < 3 || g->bank_width < 3) return seg_fail(LBM_ERR_ARG, "ny and bank_width must be >= 3");
+  try {
+    cudaStream_t st = static_cast<cudaStream_t>(g->stream);
+    Scratch sc;
+    double* d_out = sc.get<double>(12);
+    feature_stats_kernel<<<1, 256, 0, st>>>(g->bank, g->n_states, g->ny, g->bank_width, d_out);
+    ck(cudaGetLastError(), "feature statistics");
+    double h[12];
+    ck(cudaMemcpyAsync(h, d_out, sizeof h, cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaStreamSynchronize(st), "sync");
+    for (int k = 0; k < 6; ++k) {
+      in_mean[k] = (float)h[k];
+      in_std[k] = h[6 + k] < 1e-12 || !std::isfinite(h[6 + k]) ? 1.f : (float)h[6 + k];
+    }
   } catch (const CudaError& ce) {
     set_last_error(std::string(ce.what) + ": " + cudaGetErrorString(ce.e));
     return LBM_ERR_CUDA;

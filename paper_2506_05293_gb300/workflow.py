@@ -258,15 +258,21 @@ def vortex_fields(case: VortexCase, nx):
 
 def vortex_sim(case: VortexCase, nx, outflow, stream=0, precision="fp32"):
     """One vortex run: west Zou & He inlet at u0, periodic y, BGK; outflow
-    ("zouhe" or ("cbc", sigma, kappa2))."""
+    "zouhe", ("cbc", sigma, kappa2) or ("cbc", sigma_max, kappa2_max, tuner)
+    with tuner = (layers, act, in_mean, in_std)."""
     cfg = L.lbm_config_default(nx=nx, ny=case.ny, tau=case.tau, collision="bgk",
                                precision=precision, u_in=case.u0, stream=stream)
     s = L.lbm_create(cfg)
     L.lbm_set_geometry(s, np.zeros((case.ny, nx), np.uint8))
     L.lbm_init_equilibrium(s, *vortex_fields(case, nx))
     if outflow != "zouhe":
-        _, sigma, kappa2 = outflow
-        L.lbm_set_outflow_cbc(s, sigma, kappa2, case.mach, 0.0)
+        sigma, kappa2 = outflow[1], outflow[2]
+        if len(outflow) > 3:
+            layers, act, mean, std = outflow[3]
+            L.lbm_set_outflow_cbc(s, sigma, kappa2, case.mach, 0.0, tuner=layers, act=act,
+                                  in_mean=mean, in_std=std)
+        else:
+            L.lbm_set_outflow_cbc(s, sigma, kappa2, case.mach, 0.0)
     return s
 
 
@@ -283,7 +289,12 @@ def vortex_study(cases, outflows, eval_steps, stream=0, precision="fp32"):
                             for c in cases]}
     names = {}
     for o in outflows:
-        name = o if isinstance(o, str) else f"cbc_s{o[1]:g}_k{o[2]:g}"
+        if isinstance(o, str):
+            name = o
+        elif len(o) > 3:
+            name = f"cbc_tuned_s{o[1]:g}_k{o[2]:g}"
+        else:
+            name = f"cbc_s{o[1]:g}_k{o[2]:g}"
         names[name] = o
         groups[name] = [vortex_sim(c, c.nx, o, stream, precision) for c in cases]
     batches = {k: L.lbm_batch_create(v) for k, v in groups.items()}
@@ -305,3 +316,144 @@ def vortex_study(cases, outflows, eval_steps, stream=0, precision="fp32"):
         for s in groups[k]:
             L.lbm_destroy(s)
     return {k: np.array(v) for k, v in errors.items()}
+
+
+# --------------------------------------------------------------------------- #
+# Sec. 4.2: the tuner of the characteristic outflow, trained through segments
+# --------------------------------------------------------------------------- #
+@dataclass
+class TunerStudy:
+    """Training of the CBC tuner on the convected vortex (Sec. 4.2).
+
+    The reference run (ref_factor x longer, Zou & He far away) stores the east
+    bank_width columns of the truncated lattice every bank_every steps; n_init
+    segment starts are taken every init_every steps from step first; each start
+    runs segments of every length in n_ts.  The paper takes 110 starts every 5
+    steps at Mach 0.3; at Mach 0.1 the vortex needs three times as many steps
+    to cover the same distance, so the starts are 15 steps apart by default."""
+    case: VortexCase = field(default_factory=lambda: VortexCase(200, 200, 0.1))
+    n_ts: tuple = (5, 10, 25)
+    n_init: int = 110
+    first: int = 1
+    init_every: int = 15
+    bank_every: int = 5
+    hidden: tuple = (20, 20)
+    act: str = "leaky"
+    sigma_max: float = 1.0
+    kappa2_max: float = 0.2
+    epochs: int = 100
+    batch: int = 10
+    lr: float = 1e-3
+    seed: int = 1
+    fixed: tuple = ((0.0, 0.0), (0.0, 0.1), (0.25, 0.1), (1.0, 0.0))
+    eval_every: int = 100
+    eval_until: int = 3000
+    stream: int = 0
+
+
+def _bank_of_reference(st: TunerStudy, stream):
+    """FP64 reference run; bank[k] = its east columns of the truncated lattice
+    at step first + k * bank_every."""
+    import torch
+    c = st.case
+    width = 2 * max(st.n_ts)
+    last = st.first + (st.n_init - 1) * st.init_every + max(st.n_ts)
+    n_states = (last - st.first) // st.bank_every + 1
+    bank = torch.zeros((n_states, 9, c.ny, width), dtype=torch.float64, device="cuda")
+    ref = vortex_sim(c, c.ref_factor * c.nx, "zouhe", stream, "fp64")
+    L.lbm_step(ref, st.first)
+    for k in range(n_states):
+        if k:
+            L.lbm_step(ref, st.bank_every)
+        L.lbm_copy_columns(ref, c.nx - width, width, bank[k])
+    L.lbm_sync(ref)
+    L.lbm_destroy(ref)
+    return bank
+
+
+def _segment_lists(st: TunerStudy, n_t):
+    ratio_i, ratio_t = st.init_every // st.bank_every, n_t // st.bank_every
+    init = np.arange(st.n_init, dtype=np.int32) * ratio_i
+    return init, init + ratio_t
+
+
+def _saturated_tuner(sizes, sigma, kappa2, st: TunerStudy):
+    """A tuner with zero weights whose output biases give constant sigma and
+    kappa2 (through the sigmoids; 0 becomes sigmoid(-40) ~ 4e-18)."""
+    def logit(q, qmax):
+        if qmax <= 0:
+            return 0.0
+        r = min(max(q / qmax, 0.0), 1.0)
+        return -40.0 if r <= 0 else (40.0 if r >= 1 else float(np.log(r / (1 - r))))
+    layers = [(np.zeros((o, i), np.float32), np.zeros(o, np.float32))
+              for i, o in zip(sizes[:-1], sizes[1:])]
+    layers[-1][1][0] = logit(sigma, st.sigma_max)
+    layers[-1][1][1] = logit(kappa2, st.kappa2_max)
+    return layers
+
+
+def tuner_study(st: TunerStudy):
+    """Train the tuner through segments and score it.  Returns the segment
+    losses (per n_t) of the initial tuner, the trained one and tuners frozen at
+    each fixed (sigma, kappa2), the training log, and the L2 density error over
+    the truncated lattice against the reference for Zou & He, each fixed set
+    and the trained tuner (``vortex_study`` at eval steps)."""
+    import torch
+    c = st.case
+    if not st.stream:
+        keep_stream = torch.cuda.Stream()
+        stream = keep_stream.cuda_stream
+    else:
+        stream = st.stream
+    t0 = time.perf_counter()
+    bank = _bank_of_reference(st, stream)
+    t_ref = time.perf_counter() - t0
+    mean, std = L.lbm_cbc_feature_stats(bank, stream=stream)
+    sizes = [6, *st.hidden, 2]
+    layers = glorot_layers(sizes, st.seed)
+    flat0 = np.concatenate([np.concatenate([W.astype(np.float64).ravel(), b.astype(np.float64)])
+                            for W, b in layers])
+    common = dict(act=st.act, in_mean=mean, in_std=std)
+
+    def losses_at(params, lay=layers):
+        out = {}
+        for n_t in st.n_ts:
+            init, fin = _segment_lists(st, n_t)
+            out[n_t] = L.lbm_cbc_segment_grad(bank, c.nx, n_t, c.tau, st.sigma_max,
+                                              st.kappa2_max, c.mach, init, fin, lay,
+                                              params=params, grad=False, stream=stream, **common)
+        return out
+
+    before = losses_at(flat0)
+    rng = np.random.default_rng(st.seed + 5)
+    p, am, av, t_adam = flat0.copy(), None, None, 0
+    log = []
+    t1 = time.perf_counter()
+    for ep in range(st.epochs):
+        for n_t in [st.n_ts[k] for k in rng.permutation(len(st.n_ts))]:
+            init, fin = _segment_lists(st, n_t)
+            n_b = st.n_init // st.batch
+            order = rng.permutation(st.n_init)[:n_b * st.batch].astype(np.int32)
+            p, am, av, ls = L.lbm_cbc_tuner_train(bank, c.nx, n_t, c.tau, st.sigma_max,
+                                                  st.kappa2_max, c.mach, init, fin, layers, order,
+                                                  st.batch, params=p, adam_m=am, adam_v=av,
+                                                  adam_t0=t_adam, lr=st.lr, stream=stream, **common)
+            t_adam += n_b
+            log.append((ep, n_t, float(np.mean(ls))))
+    t_train = time.perf_counter() - t1
+    after = losses_at(p)
+    fixed_losses = {}
+    for sg, kp in st.fixed:
+        lay = _saturated_tuner(sizes, sg, kp, st)
+        flat = np.concatenate([np.concatenate([W.astype(np.float64).ravel(), b.astype(np.float64)])
+                               for W, b in lay])
+        fixed_losses[(sg, kp)] = losses_at(flat, lay)
+    trained = [(W.astype(np.float32), b.astype(np.float32)) for W, b in L.unflatten(p, layers)]
+    outflows = ["zouhe"] + [("cbc", sg, kp) for sg, kp in st.fixed] + \
+               [("cbc", st.sigma_max, st.kappa2_max, (trained, st.act, mean, std))]
+    steps = list(range(st.eval_every, st.eval_until + 1, st.eval_every))
+    errors = vortex_study([c], outflows, steps, stream=stream)
+    return {"before": before, "after": after, "fixed": fixed_losses, "log": log,
+            "errors": errors, "eval_steps": steps, "params": p, "in_mean": mean,
+            "in_std": std, "t_reference_s": t_ref, "t_train_s": t_train,
+            "adam_steps": t_adam}

@@ -165,3 +165,40 @@ def test_full_size_vortex_segments_sampled(L):
                                         in_std=std)
     assert loss == pytest.approx(loss_o, rel=1e-10)
     assert np.max(np.abs(grad - grad_o)) <= 1e-8 * np.max(np.abs(grad_o))
+
+
+def test_feature_statistics_match_oracle(L):
+    nx, ny = 15, 11
+    states = _states(nx, ny, 4, 80)
+    bank = _bank(states, 6)
+    mean, std = L.lbm_cbc_feature_stats(bank)
+    from oracle import cbc
+    feats = []
+    for f in states:
+        rho, u, v = lbm.moments(f)
+        p = rho / 3.0
+        Lc = nx - 1
+        solid = np.zeros(ny, bool)
+        feats.append(np.stack([cbc.d_dx_backward(p, Lc), cbc.d_dx_backward(u, Lc),
+                               cbc.d_dx_backward(v, Lc), cbc.d_dy(p, Lc, solid),
+                               cbc.d_dy(u, Lc, solid), cbc.d_dy(v, Lc, solid)], 1))
+    feats = np.concatenate(feats)
+    assert np.allclose(mean, feats.mean(0), rtol=1e-6, atol=1e-12)
+    assert np.allclose(std, feats.std(0), rtol=1e-6, atol=0)
+
+
+def test_small_tuner_study_lowers_the_segment_loss(L):
+    """The Sec. 4.2 protocol end to end on a small vortex: reference run, bank,
+    feature statistics, Adam through segments of three lengths, scoring."""
+    from paper_2506_05293_gb300 import workflow as W
+    st = W.TunerStudy(case=W.VortexCase(64, 48, 0.1), n_ts=(2, 4, 6), n_init=12, init_every=6,
+                      bank_every=2, hidden=(8,), epochs=15, batch=4, lr=3e-3,
+                      fixed=((0.25, 0.1),), eval_every=50, eval_until=200)
+    res = W.tuner_study(st)
+    assert res["adam_steps"] == 15 * 3 * 3
+    tot_before = sum(res["before"].values())
+    tot_after = sum(res["after"].values())
+    assert tot_after < tot_before
+    errs = res["errors"]
+    assert set(errs) == {"zouhe", "cbc_s0.25_k0.1", "cbc_tuned_s1_k0.2"}
+    assert all(np.all(np.isfinite(e)) for e in errs.values())
