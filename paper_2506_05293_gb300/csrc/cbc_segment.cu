@@ -16,12 +16,14 @@
 // Reverse pass, step t+1 -> t, given lambda_{t+1} = dL/df(t+1):
 //  * interior node: f(t+1) = BGK(p), p_i = f_i(x - c_i, t); mu = J_BGK(p)^T lambda
 //    in closed form (the equilibrium's derivatives in rho, u, v);
-//  * east node: its 51 inputs (the populations of the five stencil nodes whose
-//    moments give the derivatives, and the six known pulled populations) plus
-//    sigma and kappa2; each of the 53 directional derivatives of
-//    lambda . node(inputs) comes from one forward-mode (dual number)
-//    evaluation of the same templated node function the forward pass runs,
-//    one thread per direction;
+//  * east node: its inputs are the moments (rho, u, v) of the five stencil
+//    nodes whose differences give the derivatives, the six known pulled
+//    populations, and sigma and kappa2, which the tuner computes from the
+//    derivatives.  One warp per east node: forward-mode (dual number)
+//    evaluations of the same templated functions the forward pass runs give
+//    the tuner's Jacobian (one lane per feature) and the 23 directional
+//    derivatives of lambda . node (one lane per input); the moments' adjoints
+//    add the path through the tuner and become population adjoints;
 //  * lambda_t gathers, per population, the consumers' mu and the east nodes'
 //    input adjoints (a fixed order: bitwise reproducible).
 // The sensitivities to sigma and kappa2 of every east node and step, with the
@@ -44,7 +46,6 @@ namespace lbm {
 namespace {
 
 constexpr int kEastInputs = 51;           // 5 stencil nodes x 9 + 6 known pulls
-constexpr int kEastDirs = kEastInputs + 2;  // + sigma, kappa2
 constexpr int kSegMaxW = 32;              // widest hidden layer of the tuner
 constexpr int kRecWidth = 8;              // features (6), dL/dsigma, dL/dkappa2
 constexpr int kGradThreads = 128;
@@ -111,7 +112,7 @@ struct SegParams {
   double* lam_in;         // [n_seg][9][ny][W]   lambda_{t+1}
   double* lam_out;        // [n_seg][9][ny][W]   lambda_t
   double* mu;             // [n_seg][9][ny][W]
-  double* east;           // [n_seg][ny][kEastDirs]
+  double* east;           // [n_seg][ny][kEastInputs]
   double* rec;            // [n_seg][n_t][ny][kRecWidth]
   double* loss_part;      // per block of the loss kernel
 };
@@ -175,49 +176,55 @@ __device__ void tuner_g(const SegParams& p, const T x[6], T s[2]) {
 }
 
 // moments of the five stencil nodes (L, y), (L-1, y), (L-2, y), (L, y-1), (L, y+1)
-// (in[9n .. 9n+8]) and the six derivatives (p_x, u_x, v_x, p_y, u_y, v_y):
-// one-sided second order in x, central in y, p = rho / 3
+// from their populations in[9n .. 9n+8]: mac[3n + {0, 1, 2}] = rho, u, v of node n
 template <typename T>
-__device__ __forceinline__ void derivs_g(const T* in, T r[5], T u[5], T v[5], T fx[6]) {
-  const double cs2 = 1.0 / 3.0;
+__device__ __forceinline__ void stencil_macros(const T* in, T mac[15]) {
 #pragma unroll
-  for (int n = 0; n < 5; ++n) moments_g(in + 9 * n, r[n], u[n], v[n]);
-  fx[0] = 0.5 * (3.0 * (cs2 * r[0]) - 4.0 * (cs2 * r[1]) + cs2 * r[2]);
-  fx[1] = 0.5 * (3.0 * u[0] - 4.0 * u[1] + u[2]);
-  fx[2] = 0.5 * (3.0 * v[0] - 4.0 * v[1] + v[2]);
-  fx[3] = 0.5 * (cs2 * r[4] - cs2 * r[3]);
-  fx[4] = 0.5 * (u[4] - u[3]);
-  fx[5] = 0.5 * (v[4] - v[3]);
+  for (int n = 0; n < 5; ++n) moments_g(in + 9 * n, mac[3 * n], mac[3 * n + 1], mac[3 * n + 2]);
 }
 
-// The east node (L, y) of one step: in[0..44] the post-collision populations at t
-// of (L, y), (L-1, y), (L-2, y), (L, y-1), (L, y+1); in[45..50] the pulled known
-// populations f0(L, y), f1(L-1, y), f2(L, y-1), f4(L, y+1), f5(L-1, y-1),
-// f8(L-1, y+1).  Derivatives (one-sided in x, central periodic in y), the tuner,
-// Eqs. 20-27, one Euler step, Zou & He with the prescribed state, the f_0
-// correction of Eq. 28 (or the exact-mass one), then BGK.  eps_s / eps_k are
-// added to sigma / kappa2 (zero in the forward pass; the seeds of the reverse
-// pass).  feat (nullable) receives the tuner's six inputs.
+// the six derivatives (p_x, u_x, v_x, p_y, u_y, v_y) of the east node from the
+// stencil moments: one-sided second order in x, central in y, p = rho / 3
 template <typename T>
-__device__ void east_node_g(const SegParams& p, const T in[kEastInputs], T eps_s, T eps_k,
-                            T out[9], double* feat) {
+__device__ __forceinline__ void features_g(const T mac[15], T fx[6]) {
   const double cs2 = 1.0 / 3.0;
-  const double cs = sqrt(cs2);
-  T r[5], u[5], v[5], fx[6];
-  derivs_g(in, r, u, v, fx);
-  const T px = fx[0], ux = fx[1], vx = fx[2], py = fx[3], vy = fx[5];
-  T sigma = mk_t<T>(p.sig_max), kappa2 = mk_t<T>(p.kap);
+  fx[0] = 0.5 * (3.0 * (cs2 * mac[0]) - 4.0 * (cs2 * mac[3]) + cs2 * mac[6]);
+  fx[1] = 0.5 * (3.0 * mac[1] - 4.0 * mac[4] + mac[7]);
+  fx[2] = 0.5 * (3.0 * mac[2] - 4.0 * mac[5] + mac[8]);
+  fx[3] = 0.5 * (cs2 * mac[12] - cs2 * mac[9]);
+  fx[4] = 0.5 * (mac[13] - mac[10]);
+  fx[5] = 0.5 * (mac[14] - mac[11]);
+}
+
+// sigma and kappa2 of a node from its features: constants, or the tuner's
+// sigma_max sigmoid(s_0) (and kappa2_max sigmoid(s_1) with two outputs)
+template <typename T>
+__device__ __forceinline__ void cbc_params_g(const SegParams& p, const T fx[6], T& sigma,
+                                             T& kappa2) {
+  sigma = mk_t<T>(p.sig_max);
+  kappa2 = mk_t<T>(p.kap);
   if (p.n_layers > 0) {
-    if (feat)
-      for (int k = 0; k < 6; ++k) feat[k] = value(fx[k]);
     T s[2];
     tuner_g(p, fx, s);
     sigma = p.sig_max * sigmoid_g(s[0]);
     if (p.sizes[p.n_layers] > 1) kappa2 = p.kap * sigmoid_g(s[1]);
   }
-  sigma = sigma + eps_s;
-  kappa2 = kappa2 + eps_k;
-  const T rho = r[0], u0 = u[0], v0 = v[0];
+}
+
+// The east node (L, y) of one step from the stencil moments at t, the pulled
+// known populations kn = f0(L, y), f1(L-1, y), f2(L, y-1), f4(L, y+1),
+// f5(L-1, y-1), f8(L-1, y+1) and the node's sigma, kappa2: Eqs. 20-27, one
+// Euler step, Zou & He with the prescribed state, the f_0 correction of Eq. 28
+// (or the exact-mass one), then BGK.
+template <typename T>
+__device__ void east_core_g(const SegParams& p, const T mac[15], const T kn[6], T sigma,
+                            T kappa2, T out[9]) {
+  const double cs2 = 1.0 / 3.0;
+  const double cs = sqrt(cs2);
+  T fx[6];
+  features_g(mac, fx);
+  const T px = fx[0], ux = fx[1], vx = fx[2], py = fx[3], vy = fx[5];
+  const T rho = mac[0], u0 = mac[1], v0 = mac[2];
   const T pL = cs2 * rho;
   const T L5 = (u0 + cs) * (px + rho * cs * ux);                 // Eq. 22
   const T L3 = u0 * vx;                                          // Eq. 21
@@ -230,12 +237,12 @@ __device__ void east_node_g(const SegParams& p, const T in[kEastInputs], T eps_s
   const T un = u0 + (-(L5 - L1) / (2.0 * rho * cs) + (T5 - T1) / (2.0 * rho * cs));  // Eq. 18
   const T vn = v0 + (-L3 + T3);                                  // Eq. 19
   T g[9];
-  g[0] = in[45];
-  g[1] = in[46];
-  g[2] = in[47];
-  g[4] = in[48];
-  g[5] = in[49];
-  g[8] = in[50];
+  g[0] = kn[0];
+  g[1] = kn[1];
+  g[2] = kn[2];
+  g[4] = kn[3];
+  g[5] = kn[4];
+  g[8] = kn[5];
   T fe[9];
   feq_g(rn, un, vn, fe);
   const T half_t = 0.5 * ((g[4] - fe[4]) - (g[2] - fe[2]));
@@ -248,22 +255,26 @@ __device__ void east_node_g(const SegParams& p, const T in[kEastInputs], T eps_s
   bgk_g(g, p.omega, out);
 }
 
-// the 51 inputs of east node y from a strip state
-__device__ __forceinline__ void east_inputs(const SegParams& p, const double* A, int y,
-                                            double in[kEastInputs]) {
+// offset in a strip state of east input k of node y: k < 45 population k % 9 of
+// stencil node k / 9, then the six known pulls
+__device__ __forceinline__ int64_t east_input_offset(const SegParams& p, int y, int k) {
   const int W = p.W, ny = p.ny;
   const int64_t pl = node_plane(p);
   const int ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
-  const int js[5] = {W - 1, W - 2, W - 3, W - 1, W - 1};
-  const int ys[5] = {y, y, y, ym, yp};
-  for (int n = 0; n < 5; ++n)
-    for (int i = 0; i < 9; ++i) in[9 * n + i] = A[i * pl + (int64_t)ys[n] * W + js[n]];
-  in[45] = A[0 * pl + (int64_t)y * W + W - 1];
-  in[46] = A[1 * pl + (int64_t)y * W + W - 2];
-  in[47] = A[2 * pl + (int64_t)ym * W + W - 1];
-  in[48] = A[4 * pl + (int64_t)yp * W + W - 1];
-  in[49] = A[5 * pl + (int64_t)ym * W + W - 2];
-  in[50] = A[8 * pl + (int64_t)yp * W + W - 2];
+  if (k < 45) {
+    const int n = k / 9, i = k % 9;
+    const int j = n == 1 ? W - 2 : (n == 2 ? W - 3 : W - 1);
+    const int yy = n == 3 ? ym : (n == 4 ? yp : y);
+    return i * pl + (int64_t)yy * W + j;
+  }
+  switch (k) {
+    case 45: return 0 * pl + (int64_t)y * W + W - 1;
+    case 46: return 1 * pl + (int64_t)y * W + W - 2;
+    case 47: return 2 * pl + (int64_t)ym * W + W - 1;
+    case 48: return 4 * pl + (int64_t)yp * W + W - 1;
+    case 49: return 5 * pl + (int64_t)ym * W + W - 2;
+    default: return 8 * pl + (int64_t)yp * W + W - 2;
+  }
 }
 
 // index among the east node's inputs of the known pulled population i (-1: unknown)
@@ -291,33 +302,48 @@ __global__ void seg_init_kernel(const SegParams p) {
   hist_at(p, s, 0)[k] = src[iy * p.bank_w + (p.bank_w - p.W) + j];
 }
 
+// interior nodes (columns 0 .. W-2): pull and BGK
 __global__ void seg_forward_kernel(const SegParams p, int t) {
   const int s = blockIdx.y;
   const int64_t pl = node_plane(p);
+  const int wi = p.W - 1;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= pl) return;
-  const int y = idx / p.W, j = idx % p.W;
+  if (idx >= p.ny * wi) return;
+  const int y = idx / wi, j = idx % wi;
   const double* A = hist_at(p, s, t);
   const double* A0 = hist_at(p, s, 0);
   double* B = hist_at(p, s, t + 1);
-  double out[9];
-  if (j == p.W - 1) {
-    double in[kEastInputs];
-    east_inputs(p, A, y, in);
-    east_node_g<double>(p, in, 0.0, 0.0, out, nullptr);
-  } else {
-    double g[9];
+  double g[9], out[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int jsrc = j - cx(i);
-      const int ysrc = wrap(y - cy(i), p.ny);
-      g[i] = jsrc >= 0 ? A[i * pl + (int64_t)ysrc * p.W + jsrc]
-                       : A0[i * pl + (int64_t)ysrc * p.W];     // frozen west edge
-    }
-    bgk_g<double>(g, p.omega, out);
+  for (int i = 0; i < 9; ++i) {
+    const int jsrc = j - cx(i);
+    const int ysrc = wrap(y - cy(i), p.ny);
+    g[i] = jsrc >= 0 ? A[i * pl + (int64_t)ysrc * p.W + jsrc]
+                     : A0[i * pl + (int64_t)ysrc * p.W];     // frozen west edge
   }
+  bgk_g<double>(g, p.omega, out);
+  const int64_t o = (int64_t)y * p.W + j;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) B[i * pl + idx] = out[i];
+  for (int i = 0; i < 9; ++i) B[i * pl + o] = out[i];
+}
+
+// east nodes (column W-1): the characteristic outflow with the tuner
+__global__ void seg_forward_east_kernel(const SegParams p, int t) {
+  const int s = blockIdx.y;
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= p.ny) return;
+  const int64_t pl = node_plane(p);
+  const double* A = hist_at(p, s, t);
+  double* B = hist_at(p, s, t + 1);
+  double in[kEastInputs], mac[15], fx[6], sigma, kappa2, out[9];
+  for (int k = 0; k < kEastInputs; ++k) in[k] = A[east_input_offset(p, y, k)];
+  stencil_macros(in, mac);
+  features_g(mac, fx);
+  cbc_params_g(p, fx, sigma, kappa2);
+  east_core_g<double>(p, mac, in + 45, sigma, kappa2, out);
+  const int64_t o = (int64_t)y * p.W + p.W - 1;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) B[i * pl + o] = out[i];
 }
 
 // loss of the batch (mean over segments) and lambda at t = n_t
@@ -404,42 +430,100 @@ __global__ void seg_adj_interior_kernel(const SegParams p, int t) {
     mu[i * pl + idx] = (1.0 - om) * l[i] + om * (sr + su * (cx(i) - u) + sv * (cy(i) - v));
 }
 
-// 53 directional derivatives of lambda_{t+1}(L, y) . east_node per east node
-__global__ void __launch_bounds__(64) seg_adj_east_kernel(const SegParams p, int t) {
+// Input adjoints of lambda_{t+1}(L, y) . east_node, one warp per east node:
+// lanes 0..5 differentiate the tuner along each feature (its Jacobian, once);
+// lanes 0..22 differentiate the core along the 15 stencil moments, the 6 known
+// pulls, sigma and kappa2 (forward mode); the moments' adjoints take the
+// feature path (the features are linear in the moments) and become population
+// adjoints through d(rho, u, v)/df.  Records (features, dL/dsigma, dL/dkappa2)
+// feed the parameter gradient.
+constexpr int kAdjWarps = 4;
+constexpr int kAdjShared = 51 + 15 + 9 + 6 + 6 + 6 + 2 + 23 + 15;
+
+__global__ void __launch_bounds__(32 * kAdjWarps) seg_adj_east_kernel(const SegParams p, int t) {
+  __shared__ double sh[kAdjWarps][kAdjShared];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.y;
-  const int y = blockIdx.x;
-  const int d = threadIdx.x;
-  if (d >= kEastDirs) return;
+  const int y = blockIdx.x * kAdjWarps + warp;
+  if (y >= p.ny) return;                     // whole warps only
+  double* in = sh[warp];
+  double* mac = in + 51;
+  double* lam = mac + 15;
+  double* fx = lam + 9;
+  double* gs = fx + 6;
+  double* gk = gs + 6;
+  double* sk = gk + 6;
+  double* a = sk + 2;
+  double* mb = a + 23;
   const int64_t pl = node_plane(p);
   const double* A = hist_at(p, s, t);
-  const double* lam = p.lam_in + (int64_t)s * 9 * pl;
-  const int64_t o = (int64_t)y * p.W + p.W - 1;
-  double l[9];
-  bool any = false;
-  for (int i = 0; i < 9; ++i) {
-    l[i] = lam[i * pl + o];
-    any |= l[i] != 0.0;
+  for (int k = lane; k < kEastInputs; k += 32) in[k] = A[east_input_offset(p, y, k)];
+  if (lane < 9) lam[lane] = p.lam_in[(int64_t)s * 9 * pl + lane * pl + (int64_t)y * p.W + p.W - 1];
+  __syncwarp();
+  if (lane < 5) {
+    double r, u, v;
+    moments_g(in + 9 * lane, r, u, v);
+    mac[3 * lane] = r;
+    mac[3 * lane + 1] = u;
+    mac[3 * lane + 2] = v;
   }
-  double* e = p.east + ((int64_t)s * p.ny + y) * kEastDirs;
-  double* rec = p.rec + (((int64_t)s * p.n_t + t) * p.ny + y) * kRecWidth;
-  double xin[kEastInputs];
-  east_inputs(p, A, y, xin);
-  Dual in[kEastInputs];
-  for (int k = 0; k < kEastInputs; ++k) in[k] = {xin[k], k == d ? 1.0 : 0.0};
-  const Dual es = {0.0, d == kEastInputs ? 1.0 : 0.0};
-  const Dual ek = {0.0, d == kEastInputs + 1 ? 1.0 : 0.0};
-  Dual out[9];
-  double feat[6];
-  east_node_g<Dual>(p, in, es, ek, out, d == kEastInputs ? feat : nullptr);
-  double acc = 0.0;
-  for (int i = 0; i < 9; ++i) acc += l[i] * out[i].d;
-  if (!any) acc = 0.0;
-  e[d] = acc;
-  if (d == kEastInputs) {
-    for (int k = 0; k < 6; ++k) rec[k] = p.n_layers > 0 ? feat[k] : 0.0;
-    rec[6] = acc;
-  } else if (d == kEastInputs + 1) {
-    rec[7] = acc;
+  __syncwarp();
+  if (lane == 0) features_g(mac, fx);
+  __syncwarp();
+  if (lane < 6) {
+    Dual xf[6];
+    for (int k = 0; k < 6; ++k) xf[k] = {fx[k], k == lane ? 1.0 : 0.0};
+    Dual sg, kp;
+    cbc_params_g(p, xf, sg, kp);
+    gs[lane] = sg.d;
+    gk[lane] = kp.d;
+    if (lane == 0) {
+      sk[0] = sg.v;
+      sk[1] = kp.v;
+    }
+  }
+  __syncwarp();
+  if (lane < 23) {
+    Dual m[15], kn[6];
+    for (int q = 0; q < 15; ++q) m[q] = {mac[q], q == lane ? 1.0 : 0.0};
+    for (int q = 0; q < 6; ++q) kn[q] = {in[45 + q], 15 + q == lane ? 1.0 : 0.0};
+    const Dual sg = {sk[0], lane == 21 ? 1.0 : 0.0};
+    const Dual kp = {sk[1], lane == 22 ? 1.0 : 0.0};
+    Dual out[9];
+    east_core_g<Dual>(p, m, kn, sg, kp, out);
+    double acc = 0.0;
+    for (int i = 0; i < 9; ++i) acc += lam[i] * out[i].d;
+    a[lane] = acc;
+  }
+  __syncwarp();
+  if (lane < 15) {
+    // feature path: fbar_f = dL/dsigma dsigma/dfx_f + dL/dkappa2 dkappa2/dfx_f,
+    // times d fx_f / d mac_lane (the linear feature map, by one dual pass)
+    Dual md[15], fd[6];
+    for (int q = 0; q < 15; ++q) md[q] = {mac[q], q == lane ? 1.0 : 0.0};
+    features_g(md, fd);
+    double acc = a[lane];
+    for (int f = 0; f < 6; ++f) acc += (a[21] * gs[f] + a[22] * gk[f]) * fd[f].d;
+    mb[lane] = acc;
+  }
+  __syncwarp();
+  double* e = p.east + ((int64_t)s * p.ny + y) * kEastInputs;
+  for (int k = lane; k < kEastInputs; k += 32) {
+    double v;
+    if (k < 45) {
+      const int n = k / 9, i = k % 9;
+      const double rho = mac[3 * n], uu = mac[3 * n + 1], vv = mac[3 * n + 2];
+      v = mb[3 * n] + (mb[3 * n + 1] * (cx(i) - uu) + mb[3 * n + 2] * (cy(i) - vv)) / rho;
+    } else {
+      v = a[15 + (k - 45)];
+    }
+    e[k] = v;
+  }
+  if (lane == 0) {
+    double* rec = p.rec + (((int64_t)s * p.n_t + t) * p.ny + y) * kRecWidth;
+    for (int k = 0; k < 6; ++k) rec[k] = fx[k];
+    rec[6] = a[21];
+    rec[7] = a[22];
   }
 }
 
@@ -451,7 +535,7 @@ __global__ void seg_gather_kernel(const SegParams p) {
   if (idx >= pl) return;
   const int y = idx / p.W, j = idx % p.W, W = p.W, ny = p.ny;
   const double* mu = p.mu + (int64_t)s * 9 * pl;
-  const double* E = p.east + (int64_t)s * ny * kEastDirs;
+  const double* E = p.east + (int64_t)s * ny * kEastInputs;
   double* lam = p.lam_out + (int64_t)s * 9 * pl;
   const int yu = wrap(y + 1, ny), yd = wrap(y - 1, ny);
   for (int i = 0; i < 9; ++i) {
@@ -460,15 +544,15 @@ __global__ void seg_gather_kernel(const SegParams p) {
     if (jc >= 0 && jc <= W - 2) acc += mu[i * pl + (int64_t)yc * W + jc];
     else if (jc == W - 1) {
       const int k = known_input(i);
-      if (k >= 0) acc += E[(int64_t)yc * kEastDirs + k];
+      if (k >= 0) acc += E[(int64_t)yc * kEastInputs + k];
     }
     if (j == W - 1)
-      acc += E[(int64_t)y * kEastDirs + i] + E[(int64_t)yu * kEastDirs + 27 + i] +
-             E[(int64_t)yd * kEastDirs + 36 + i];
+      acc += E[(int64_t)y * kEastInputs + i] + E[(int64_t)yu * kEastInputs + 27 + i] +
+             E[(int64_t)yd * kEastInputs + 36 + i];
     else if (j == W - 2)
-      acc += E[(int64_t)y * kEastDirs + 9 + i];
+      acc += E[(int64_t)y * kEastInputs + 9 + i];
     else if (j == W - 3)
-      acc += E[(int64_t)y * kEastDirs + 18 + i];
+      acc += E[(int64_t)y * kEastInputs + 18 + i];
     lam[i * pl + idx] = acc;
   }
 }
@@ -629,10 +713,11 @@ __global__ void __launch_bounds__(256) feature_stats_kernel(const double* bank, 
       const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
       const int js[5] = {bank_w - 1, bank_w - 2, bank_w - 3, bank_w - 1, bank_w - 1};
       const int ys[5] = {y, y, y, ym, yp};
-      double in[45], r[5], u[5], v[5], fx[6];
+      double in[45], mac[15], fx[6];
       for (int q = 0; q < 5; ++q)
         for (int i = 0; i < 9; ++i) in[9 * q + i] = A[((int64_t)i * ny + ys[q]) * bank_w + js[q]];
-      derivs_g(in, r, u, v, fx);
+      stencil_macros(in, mac);
+      features_g(mac, fx);
       for (int f = 0; f < 6; ++f) {
         const double d = pass == 0 ? fx[f] : fx[f] - mean[f];
         acc[f] += pass == 0 ? d : d * d;
@@ -767,7 +852,7 @@ class SegmentRunner {
     p_.lam_in = sc_.get<double>((size_t)max_batch * 9 * pl);
     p_.lam_out = sc_.get<double>((size_t)max_batch * 9 * pl);
     p_.mu = sc_.get<double>((size_t)max_batch * 9 * pl);
-    p_.east = sc_.get<double>((size_t)max_batch * p_.ny * kEastDirs);
+    p_.east = sc_.get<double>((size_t)max_batch * p_.ny * kEastInputs);
     p_.rec = sc_.get<double>((size_t)max_batch * p_.n_t * p_.ny * kRecWidth);
     loss_blocks_ = (int)((pl + 127) / 128);
     p_.loss_part = sc_.get<double>((size_t)max_batch * loss_blocks_);
@@ -806,12 +891,18 @@ class SegmentRunner {
     const dim3 gn((unsigned)((pl + 127) / 128), (unsigned)n);
     const dim3 gi((unsigned)((9 * pl + 127) / 128), (unsigned)n);
     seg_init_kernel<<<gi, 128, 0, st_>>>(p);
-    for (int t = 0; t < p.n_t; ++t) seg_forward_kernel<<<gn, 128, 0, st_>>>(p, t);
+    const dim3 gf((unsigned)((p.ny * (p.W - 1) + 127) / 128), (unsigned)n);
+    const dim3 ge((unsigned)((p.ny + 63) / 64), (unsigned)n);
+    for (int t = 0; t < p.n_t; ++t) {
+      seg_forward_kernel<<<gf, 128, 0, st_>>>(p, t);
+      seg_forward_east_kernel<<<ge, 64, 0, st_>>>(p, t);
+    }
     seg_loss_kernel<<<gn, 128, 0, st_>>>(p);
     sum_loss_kernel<<<1, 32, 0, st_>>>(p.loss_part, (int64_t)n * loss_blocks_, d_loss);
     for (int t = p.n_t - 1; t >= 0; --t) {
       seg_adj_interior_kernel<<<gn, 128, 0, st_>>>(p, t);
-      seg_adj_east_kernel<<<dim3((unsigned)p.ny, (unsigned)n), 64, 0, st_>>>(p, t);
+      seg_adj_east_kernel<<<dim3((unsigned)((p.ny + kAdjWarps - 1) / kAdjWarps), (unsigned)n),
+                            32 * kAdjWarps, 0, st_>>>(p, t);
       if (t > 0) {
         seg_gather_kernel<<<gn, 128, 0, st_>>>(p);
         std::swap(p.lam_in, p.lam_out);

@@ -308,7 +308,13 @@ def vortex_study(cases, outflows, eval_steps, stream=0, precision="fp32"):
         for k in names:
             row = []
             for c, s, r in zip(cases, groups[k], ref):
-                rho = L.lbm_fields(s)[0]
+                try:
+                    rho = L.lbm_fields(s)[0]
+                except L.LbmError as ex:          # a diverged run scores NaN from then on
+                    if ex.status != 5:
+                        raise
+                    row.append(float("nan"))
+                    continue
                 row.append(float(np.sqrt(np.mean((rho - r[:, :c.nx]) ** 2))))
             errors[k].append(row)
     for k, b in batches.items():

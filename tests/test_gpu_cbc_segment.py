@@ -191,7 +191,8 @@ def test_small_tuner_study_lowers_the_segment_loss(L):
     """The Sec. 4.2 protocol end to end on a small vortex: reference run, bank,
     feature statistics, Adam through segments of three lengths, scoring."""
     from paper_2506_05293_gb300 import workflow as W
-    st = W.TunerStudy(case=W.VortexCase(64, 48, 0.1), n_ts=(2, 4, 6), n_init=12, init_every=6,
+    st = W.TunerStudy(case=W.VortexCase(64, 48, 0.1, re=150.0), n_ts=(2, 4, 6), n_init=12,
+                      init_every=6,
                       bank_every=2, hidden=(8,), epochs=15, batch=4, lr=3e-3,
                       fixed=((0.25, 0.1),), eval_every=50, eval_until=200)
     res = W.tuner_study(st)
