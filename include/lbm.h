@@ -258,17 +258,20 @@ lbm_status lbm_nn_loss_grad(const float* dev_rows, int64_t n_rows, const int32_t
  * rho and U being the moments of the stored populations.  A batch's loss is
  * the mean of its segments' losses.  Those columns at t0 + n_t depend only on
  * the last W = max(2 n_t, 3) columns at t0 (so the west inlet never enters),
- * and the library runs each segment on that strip alone.  All arithmetic is
- * FP64; the gradient with respect to the tuner's parameters is the exact
- * reverse-mode derivative of that computation (adjoint stream-and-collide
- * steps, forward-mode dual numbers for the east node), summed in a fixed
- * order (bitwise reproducible). */
+ * and the library runs each segment on that strip alone.  The gradient with
+ * respect to the tuner's parameters is the exact reverse-mode derivative of
+ * that computation in the chosen precision (adjoint stream-and-collide steps,
+ * forward-mode dual numbers for the east node), summed in a fixed order
+ * (bitwise reproducible). */
 typedef struct {
   int32_t nx, ny;           /* truncated lattice; nx >= W + 1, 3 <= ny <= 65535 */
   int32_t n_t;              /* steps per segment, >= 1 */
   double tau, rho_out;      /* BGK relaxation time (> 1/2); outflow far-field density */
   double sigma, kappa2, mach, length;  /* as lbm_set_outflow_cbc (length 0 = nx) */
   int32_t exact_mass;       /* f_0 correction: 0 Eq. 28, 1 exact mass */
+  int32_t precision;        /* LBM_FP64 (default), or LBM_FP32: states, adjoints and the
+                               tuner in FP32 on shifted populations h = f - w (loss,
+                               parameter sums and Adam stay FP64) */
   const double* bank;       /* device, [n_states][9][ny][bank_width]: populations f (not
                                shifted) of the last bank_width columns of the truncated
                                lattice, e.g. written by lbm_copy_columns; caller-owned */

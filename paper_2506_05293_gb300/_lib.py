@@ -50,7 +50,7 @@ class LbmCbcSegments(Structure):
     _fields_ = [("nx", c_int32), ("ny", c_int32), ("n_t", c_int32), ("tau", c_double),
                 ("rho_out", c_double), ("sigma", c_double), ("kappa2", c_double),
                 ("mach", c_double), ("length", c_double), ("exact_mass", c_int32),
-                ("bank", c_void_p), ("n_states", c_int32), ("bank_width", c_int32),
+                ("precision", c_int32), ("bank", c_void_p), ("n_states", c_int32), ("bank_width", c_int32),
                 ("init_state", POINTER(c_int32)), ("final_state", POINTER(c_int32)),
                 ("n_seg", c_int32), ("stream", c_void_p)]
 

@@ -270,7 +270,7 @@ def lbm_copy_columns(sim, x0, width, out):
 
 
 def _segments(bank, nx, n_t, tau, sigma, kappa2, mach, init_state, final_state, length=0.0,
-              rho_out=1.0, exact_mass=False, stream=None):
+              rho_out=1.0, exact_mass=False, precision="fp64", stream=None):
     """LbmCbcSegments over a device bank (n_states, 9, ny, bank_width) float64."""
     n_states, _, ny, width = (int(d) for d in bank.shape)
     init = np.ascontiguousarray(init_state, dtype=np.int32)
@@ -282,6 +282,7 @@ def _segments(bank, nx, n_t, tau, sigma, kappa2, mach, init_state, final_state, 
     g.tau, g.rho_out = float(tau), float(rho_out)
     g.sigma, g.kappa2, g.mach, g.length = float(sigma), float(kappa2), float(mach), float(length)
     g.exact_mass = int(bool(exact_mass))
+    g.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     g.bank = c_void_p(_devptr(bank))
     g.n_states, g.bank_width = n_states, width
     g.init_state = init.ctypes.data_as(POINTER(ctypes.c_int32))

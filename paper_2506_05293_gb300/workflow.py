@@ -354,6 +354,7 @@ class TunerStudy:
     fixed: tuple = ((0.0, 0.0), (0.0, 0.1), (0.25, 0.1), (1.0, 0.0))
     eval_every: int = 100
     eval_until: int = 3000
+    precision: str = "fp32"          # segment arithmetic (losses, sums and Adam stay FP64)
     stream: int = 0
 
 
@@ -419,7 +420,7 @@ def tuner_study(st: TunerStudy):
     layers = glorot_layers(sizes, st.seed)
     flat0 = np.concatenate([np.concatenate([W.astype(np.float64).ravel(), b.astype(np.float64)])
                             for W, b in layers])
-    common = dict(act=st.act, in_mean=mean, in_std=std)
+    common = dict(act=st.act, in_mean=mean, in_std=std, precision=st.precision)
 
     def losses_at(params, lay=layers):
         out = {}
