@@ -22,7 +22,10 @@ The line also carries ``accuracy``, the other half of the metric: the errors
 of C_D mean, C_L RMS and St of the NN outflow and of Zou & He on the same
 truncated domain (cylinder D = 40, Re 100, wake 4D) against the 32D-long run,
 with the network trained on the GPU from that run (``--no-accuracy`` skips
-this minute-long study).
+this minute-long study), and ``cbc_tuner``: the tuner of the characteristic
+outflow trained through n_t-step segments of the 200 x 200 convected vortex
+(Sec. 4.2) and its L2 density error against fixed (sigma, kappa2) settings and
+Zou & He (``--no-tuner`` skips these few seconds).
 
 Prints one JSON line.
 """
@@ -367,6 +370,40 @@ def accuracy_study():
         return {"error": f"{type(ex).__name__}: {ex}"}
 
 
+def tuner_study():
+    """The CBC tuner trained through segments (Sec. 4.2) on the convected
+    vortex: segment losses before and after training and of tuners frozen at
+    fixed (sigma, kappa2), the summed L2 density error over 3000 steps for every
+    outflow, and the training's cost.  A failure is reported, not raised."""
+    try:
+        import math
+        from paper_2506_05293_gb300 import workflow
+        st = workflow.TunerStudy()
+        t0 = time.perf_counter()
+        res = workflow.tuner_study(st)
+
+        def tot(d):
+            return float(sum(d.values()))
+        errs = {k: float(sum(v[:, 0])) for k, v in res["errors"].items()}
+        return {"case": (f"vortex {st.case.nx}x{st.case.ny} strength {st.case.strength} "
+                         f"Ma {st.case.mach} Re {st.case.re:g}; {st.n_init} starts every "
+                         f"{st.init_every} steps x n_t {list(st.n_ts)}; tuner 6-"
+                         f"{'-'.join(map(str, st.hidden))}-2 {st.act}, sigma_max {st.sigma_max}, "
+                         f"kappa2_max {st.kappa2_max}; {st.precision}"),
+                "segment_loss": {"initial": tot(res["before"]), "trained": tot(res["after"]),
+                                 **{f"fixed_s{a:g}_k{b:g}": tot(v)
+                                    for (a, b), v in res["fixed"].items()}},
+                "l2_density_error_sum": {k: (None if math.isnan(v) else v)
+                                         for k, v in errs.items()},
+                "eval_steps": f"{res['eval_steps'][0]}..{res['eval_steps'][-1]} every "
+                              f"{st.eval_every}",
+                "adam_steps": res["adam_steps"], "train_s": res["t_train_s"],
+                "ms_per_adam_step": 1e3 * res["t_train_s"] / max(1, res["adam_steps"]),
+                "wall_s": time.perf_counter() - t0}
+    except Exception as ex:   # reported, not fatal
+        return {"error": f"{type(ex).__name__}: {ex}"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -497,8 +534,11 @@ def run_ours(args):
         return 0
     cpu = None
     accuracy = None
+    tuner = None
     if world == 1 and not args.no_accuracy:
         accuracy = accuracy_study()
+    if world == 1 and not args.no_tuner:
+        tuner = tuner_study()
     if world == 1 and not args.no_cpu_baseline:
         glups_cpu, dt_cpu, _, _ = cpu_oracle_sample(wl, args.cpu_steps)
         cpu = {"value": glups_cpu, "unit": "GLUPS", "cores": 1, "kind": "oracle",
@@ -533,6 +573,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "accuracy": accuracy,
+        "cbc_tuner": tuner,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -552,6 +593,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the NN vs Zou & He truncation study (about a minute)")
+    ap.add_argument("--no-tuner", action="store_true",
+                    help="skip the CBC tuner training study (a few seconds)")
     ap.add_argument("--rows", type=int, default=0, help="fixed tiling instead of the autotuner")
     ap.add_argument("--variant", type=int, default=3)
     args = ap.parse_args()

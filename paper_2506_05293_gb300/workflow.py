@@ -464,3 +464,26 @@ def tuner_study(st: TunerStudy):
             "errors": errors, "eval_steps": steps, "params": p, "in_mean": mean,
             "in_std": std, "t_reference_s": t_ref, "t_train_s": t_train,
             "adam_steps": t_adam}
+
+
+def _main(argv=None):
+    """``python -m paper_2506_05293_gb300.workflow tuner [--epochs N] [--precision P]``:
+    run the tuner study and print its summary as one JSON line."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(prog="python -m paper_2506_05293_gb300.workflow")
+    ap.add_argument("study", choices=["tuner"])
+    ap.add_argument("--epochs", type=int, default=TunerStudy.epochs)
+    ap.add_argument("--precision", default=TunerStudy.precision, choices=["fp32", "fp64"])
+    args = ap.parse_args(argv)
+    st = TunerStudy(epochs=args.epochs, precision=args.precision)
+    res = tuner_study(st)
+    out = {"segment_loss_initial": res["before"], "segment_loss_trained": res["after"],
+           "segment_loss_fixed": {f"s{a:g}_k{b:g}": v for (a, b), v in res["fixed"].items()},
+           "l2_density_error_sum": {k: float(np.sum(v[:, 0])) for k, v in res["errors"].items()},
+           "adam_steps": res["adam_steps"], "train_s": res["t_train_s"]}
+    print(json.dumps(out, default=float))
+
+
+if __name__ == "__main__":
+    _main()
