@@ -185,6 +185,16 @@ lbm_status lbm_set_outflow_cbc(lbm_sim* sim, double sigma, double kappa2, double
  * In a batch each member captures on its own. */
 lbm_status lbm_capture_plane(lbm_sim* sim, int32_t x_t, int32_t every, float* dev_rows,
                              int64_t cap_rows);
+
+/* Training rows from one snapshot (Sec. 3.1: the network is trained on a
+ * snapshot of a converged flow, each layer of the training region one
+ * batch): for every column x in [x_begin, x_end) (4 <= x_begin < x_end <=
+ * nx-1) and every row y, the row that lbm_capture_plane at x_t = x would
+ * record during the next step (post-stream populations pulled from the current
+ * post-collision state, solid nodes reversing what arrives), written to
+ * dev_rows[(x - x_begin) * ny + y] (device float[(x_end - x_begin) * ny][84],
+ * caller-owned).  Enqueued on the sim's stream; the state is not changed. */
+lbm_status lbm_capture_snapshot(lbm_sim* sim, int32_t x_begin, int32_t x_end, float* dev_rows);
 /* Rows captured so far (complete once the sim's stream reaches them). */
 lbm_status lbm_capture_count(lbm_sim* sim, int64_t* rows);
 

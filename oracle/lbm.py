@@ -308,6 +308,18 @@ class Solver:
         self.capture = (int(x_t), int(every))
         self.captured = []
 
+    def snapshot_rows(self, x_begin, x_end):
+        """Training rows of Sec. 3.1 from the current state alone (one
+        converged snapshot, each column a batch): for every column x in
+        [x_begin, x_end) the ny rows that ``capture_plane(x, ...)`` records
+        during the next step -- the pull of the stored post-collision state
+        with bounce-back at solid nodes (columns 4..nx-2 never touch the open
+        boundaries) -- stacked column by column, float64 (n, 84)."""
+        g = bounce_back(stream_pull(self.f), self.kind)
+        out = [np.hstack([nn_features(g, x), g[list(NN_POPS), :, x].T])
+               for x in range(x_begin, x_end)]
+        return np.vstack(out)
+
     def dataset(self):
         """All captured rows, float64 (n, 84), in capture order."""
         if not self.captured:

@@ -70,6 +70,7 @@ SIGNATURES = {
                                     POINTER(LbmMlp), c_int32]),
     "lbm_capture_plane": (c_int, [c_void_p, c_int32, c_int32, c_void_p, c_int64]),
     "lbm_capture_count": (c_int, [c_void_p, POINTER(c_int64)]),
+    "lbm_capture_snapshot": (c_int, [c_void_p, c_int32, c_int32, c_void_p]),
     "lbm_save": (c_int, [c_void_p, c_char_p]),
     "lbm_load": (c_int, [c_void_p, c_char_p]),
     "lbm_nn_dataset_stats": (c_int, [c_void_p, c_int64, c_void_p, POINTER(c_float),

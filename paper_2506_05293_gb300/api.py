@@ -181,6 +181,16 @@ def lbm_capture_plane(sim, x_t, every, rows=None, cap_rows=None):
                                          c_void_p(_devptr(rows)), int(cap_rows)))
 
 
+def lbm_capture_snapshot(sim, x_begin, x_end, rows):
+    """Rows of the columns [x_begin, x_end) of the current state into the device
+    tensor ``rows`` ((x_end - x_begin) * ny, 84), one batch of ny rows per column."""
+    need = (int(x_end) - int(x_begin)) * sim.ny
+    if rows.shape[0] < need or rows.shape[1] != 84:
+        raise ValueError(f"rows must hold {need} x 84 floats")
+    _check(_lib.load().lbm_capture_snapshot(sim.handle, int(x_begin), int(x_end),
+                                            c_void_p(_devptr(rows))))
+
+
 def lbm_save(sim, path):
     _check(_lib.load().lbm_save(sim.handle, str(path).encode()))
 

@@ -604,6 +604,30 @@ lbm_status lbm_capture_plane(lbm_sim* s, int32_t x_t, int32_t every, float* dev_
   return LBM_OK;
 }
 
+lbm_status lbm_capture_snapshot(lbm_sim* s, int32_t x_begin, int32_t x_end, float* dev_rows) {
+  if (lbm_status st = check_sim(s)) return st;
+  if (!dev_rows) return fail(LBM_ERR_ARG, "dev_rows is NULL");
+  if (!s->solid_bits) return fail(LBM_ERR_STATE, "set the geometry first");
+  if (x_begin < 4 || x_end <= x_begin || x_end > s->nx - 1)
+    return fail(LBM_ERR_ARG, "columns must satisfy 4 <= x_begin < x_end <= nx-1");
+  if ((int64_t)(x_end - x_begin) > 65535) return fail(LBM_ERR_ARG, "at most 65535 columns");
+  LBM_GUARD_BEGIN
+  lbm::CaptureParams c{};
+  c.src = s->buf[s->cur];
+  c.solid_bits = s->solid_bits;
+  c.words_per_row = s->words_per_row;
+  c.nx = s->nx;
+  c.ny = s->ny;
+  c.pitch = s->pitch;
+  c.plane = s->plane;
+  c.x_t = x_begin;
+  c.out = dev_rows;
+  lbm::launch_snapshot(s->prec, c, x_end - x_begin, s->stream);
+  ck(cudaGetLastError(), "snapshot launch");
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
 lbm_status lbm_capture_count(lbm_sim* s, int64_t* rows) {
   if (lbm_status st = check_sim(s)) return st;
   if (!rows) return fail(LBM_ERR_ARG, "rows is NULL");

@@ -143,6 +143,7 @@ struct CaptureParams {
   float* out;                      // ny rows of kRowFloats
 };
 void launch_capture(int prec, const CaptureParams& p, cudaStream_t s);
+void launch_snapshot(int prec, const CaptureParams& p, int n_cols, cudaStream_t s);
 
 void dataset_stats(const float* rows, int64_t n, double* scratch, cudaStream_t s);
 int dataset_stats_scratch_doubles();

@@ -39,11 +39,8 @@ __device__ __forceinline__ double pop_value(const __half* a, int64_t k) {
 // columns x_t-1..x_t-3, rows y-1..y+1 (81 inputs of Eq. 15, index
 // k*27 + j*9 + i), then f_3, f_6, f_7 at (x_t, y).
 template <typename S>
-__global__ void capture_kernel(const CaptureParams p) {
-  const int y = blockIdx.x * blockDim.x + threadIdx.x;
-  if (y >= p.ny) return;
+__device__ __forceinline__ void capture_row(const CaptureParams& p, int x_t, int y, float* out) {
   const S* __restrict__ A = static_cast<const S*>(p.src);
-  float* out = p.out + (int64_t)y * kRowFloats;
   auto post = [&](int i, int x, int yy) -> float {
     yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
     const uint32_t word = p.solid_bits[(int64_t)yy * p.words_per_row + (x >> 5)];
@@ -55,10 +52,28 @@ __global__ void capture_kernel(const CaptureParams p) {
   };
   for (int k = 0; k < 3; ++k)
     for (int j = 0; j < 3; ++j)
-      for (int i = 0; i < 9; ++i) out[k * 27 + j * 9 + i] = post(i, p.x_t - 1 - k, y - 1 + j);
-  out[81] = post(3, p.x_t, y);
-  out[82] = post(6, p.x_t, y);
-  out[83] = post(7, p.x_t, y);
+      for (int i = 0; i < 9; ++i) out[k * 27 + j * 9 + i] = post(i, x_t - 1 - k, y - 1 + j);
+  out[81] = post(3, x_t, y);
+  out[82] = post(6, x_t, y);
+  out[83] = post(7, x_t, y);
+}
+
+template <typename S>
+__global__ void capture_kernel(const CaptureParams p) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= p.ny) return;
+  capture_row<S>(p, p.x_t, y, p.out + (int64_t)y * kRowFloats);
+}
+
+// Snapshot (Sec. 3.1: the training set is one converged snapshot, each
+// column a batch): column x_t + blockIdx.y, rows in order, one batch of ny
+// rows per column.
+template <typename S>
+__global__ void snapshot_kernel(const CaptureParams p) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= p.ny) return;
+  const int c = blockIdx.y;
+  capture_row<S>(p, p.x_t + c, y, p.out + ((int64_t)c * p.ny + y) * kRowFloats);
 }
 
 void launch_capture(int prec, const CaptureParams& p, cudaStream_t s) {
@@ -66,6 +81,13 @@ void launch_capture(int prec, const CaptureParams& p, cudaStream_t s) {
   if (prec == LBM_FP64) capture_kernel<double><<<grid, 128, 0, s>>>(p);
   else if (prec == LBM_FP32) capture_kernel<float><<<grid, 128, 0, s>>>(p);
   else capture_kernel<__half><<<grid, 128, 0, s>>>(p);
+}
+
+void launch_snapshot(int prec, const CaptureParams& p, int n_cols, cudaStream_t s) {
+  const dim3 grid((unsigned)((p.ny + 127) / 128), (unsigned)n_cols);
+  if (prec == LBM_FP64) snapshot_kernel<double><<<grid, 128, 0, s>>>(p);
+  else if (prec == LBM_FP32) snapshot_kernel<float><<<grid, 128, 0, s>>>(p);
+  else snapshot_kernel<__half><<<grid, 128, 0, s>>>(p);
 }
 
 // ---- data-set statistics ------------------------------------------------------

@@ -217,6 +217,186 @@ def run_study(st: Study, starts=("rest", "restart")):
 
 
 # --------------------------------------------------------------------------- #
+# Sec. 3.1's own protocol: one converged snapshot at the training Reynolds
+# number, every layer of the wake a batch; then the trained outflow over a
+# range of Reynolds numbers in acoustic and diffusive scaling
+# --------------------------------------------------------------------------- #
+@dataclass
+class SnapshotStudy:
+    """Training from one snapshot and the Reynolds sweep of Sec. 3.2.
+
+    Acoustic scaling keeps the inlet velocity (Mach number) and changes the
+    relaxation time; diffusive scaling keeps the relaxation time of the
+    training run and changes the velocity.  Every Reynolds number runs a long
+    reference and two truncated lattices (Zou & He, network) from rest, all
+    of them in two batches."""
+    D: int = 40
+    u: float = 0.05
+    height_d: float = 16.0
+    centre_d: float = 8.0
+    long_wake_d: float = 32.0
+    short_wake_d: float = 4.0
+    re_train: float = 200.0
+    collision: str = "mrt"
+    t_snapshot: int = 150_000
+    train_from_d: float = 2.0          # first training column: 2 D behind the centre
+    hidden: tuple = (64, 64)
+    epochs: int = 30
+    lr: float = 1e-3
+    val_frac: float = 0.1
+    acoustic_re: tuple = (20.0, 50.0, 100.0, 150.0, 200.0)
+    diffusive_re: tuple = (100.0, 150.0)
+    t_trans: int = 150_000
+    t_stat: int = 65_536
+    seed: int = 1
+    v_pert_amp: float = 1e-3
+    fallback_drho: float = 0.05
+    precision: str = "fp32"
+
+    @property
+    def ny(self):
+        return int(round(self.height_d * self.D))
+
+    def nx_for(self, wake_d):
+        return int(round((self.centre_d + wake_d) * self.D))
+
+    def tau_for(self, re, u):
+        return 3.0 * u * self.D / re + 0.5
+
+
+def _cyl_sim(st, nx, tau, u, stream):
+    kind = cylinder_kind(nx, st.ny, st.centre_d * st.D, st.ny / 2.0, st.D)
+    cfg = L.lbm_config_default(nx=nx, ny=st.ny, tau=tau, collision=st.collision,
+                               precision=st.precision, u_in=u, v_pert_amp=st.v_pert_amp,
+                               seed=st.seed, stream=stream)
+    s = L.lbm_create(cfg)
+    L.lbm_set_geometry(s, kind)
+    L.lbm_init_equilibrium(s, None, np.where(kind == 0, u, 0.0), None)
+    return s
+
+
+def _coeffs(D, u, fx, fy):
+    q = 0.5 * u * u * D
+    cd, cl = fx / q, fy / q
+    return {"cd": float(cd.mean()), "cl_rms": float(np.sqrt(np.mean((cl - cl.mean()) ** 2))),
+            "st": float(L.lbm_strouhal(cl, D, u))}
+
+
+def snapshot_train(st: SnapshotStudy, stream):
+    """Reference at re_train to t_snapshot, one snapshot of the wake columns,
+    normalisation from the training columns, Adam over shuffled columns."""
+    import torch
+    t0 = time.perf_counter()
+    nx = st.nx_for(st.long_wake_d)
+    s = _cyl_sim(st, nx, st.tau_for(st.re_train, st.u), st.u, stream)
+    L.lbm_step(s, st.t_snapshot)
+    x0 = int(round((st.centre_d + st.train_from_d) * st.D))
+    x1 = nx - 1
+    n_cols = x1 - x0
+    rows = torch.zeros((n_cols * st.ny, 84), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    L.lbm_capture_snapshot(s, x0, x1, rows)
+    L.lbm_sync(s)
+    L.lbm_destroy(s)
+    t_ref = time.perf_counter() - t0
+    rng = np.random.default_rng(st.seed + 29)
+    perm = torch.as_tensor(rng.permutation(n_cols), device="cuda")
+    rows = rows.view(n_cols, st.ny, 84)[perm].reshape(-1, 84).contiguous()
+    n_val = max(1, int(round(st.val_frac * n_cols)))
+    n_train = n_cols - n_val
+    mean, std, scale = L.lbm_nn_dataset_stats(rows, n_rows=n_train * st.ny)
+    order = np.concatenate([rng.permutation(n_train) for _ in range(st.epochs)]).astype(np.int32)
+    init = glorot_layers([81, *st.hidden, 3], st.seed)
+    t1 = time.perf_counter()
+    layers, _, _, losses = L.lbm_nn_train(rows, order, init, "tanh", mean, std, scale,
+                                          batch_rows=st.ny, lr=st.lr, stream=stream)
+    t_train = time.perf_counter() - t1
+    val_b = np.arange(n_train, n_cols)
+    val = L.lbm_nn_loss_grad(rows, val_b, layers, "tanh", mean, std, scale, grads=False,
+                             batch_rows=st.ny, stream=stream)
+    zero = [(np.zeros_like(W), np.zeros_like(b)) for W, b in layers]
+    val0 = L.lbm_nn_loss_grad(rows, val_b, zero, "tanh", mean, std, scale, grads=False,
+                              batch_rows=st.ny, stream=stream)
+    info = {"columns": [x0, x1], "batches_train": int(n_train), "batches_val": int(n_val),
+            "adam_steps": int(order.size), "train_loss_last_epoch":
+            float(losses[-n_train:].mean()), "val_loss": float(val.mean()),
+            "val_loss_zero_gradient": float(val0.mean()), "reference_s": t_ref,
+            "train_s": t_train}
+    return (layers, mean, std, scale), info
+
+
+def reynolds_sweep(st: SnapshotStudy, net, stream):
+    """For every (scaling, Re): a long reference and the truncated lattice with
+    Zou & He and with the network, from rest; coefficients over t_stat steps
+    after t_trans.  Errors are relative to the reference (C_L RMS and St only
+    where the reference sheds)."""
+    layers, mean, std, scale = net
+    tau_train = st.tau_for(st.re_train, st.u)
+    cases = [("acoustic", re, st.tau_for(re, st.u), st.u) for re in st.acoustic_re]
+    cases += [("diffusive", re, tau_train, re * (tau_train - 0.5) / (3.0 * st.D))
+              for re in st.diffusive_re]
+    longs, shorts = [], []
+    for _, re, tau, u in cases:
+        longs.append(_cyl_sim(st, st.nx_for(st.long_wake_d), tau, u, stream))
+        zh = _cyl_sim(st, st.nx_for(st.short_wake_d), tau, u, stream)
+        nn = _cyl_sim(st, st.nx_for(st.short_wake_d), tau, u, stream)
+        L.lbm_set_outflow_nn(nn, layers, "tanh", mean, std, scale, st.fallback_drho)
+        shorts += [zh, nn]
+    t0 = time.perf_counter()
+    batches = [L.lbm_batch_create(longs), L.lbm_batch_create(shorts)]
+    for b in batches:
+        L.lbm_batch_step(b, st.t_trans)
+    for b in batches:
+        L.lbm_batch_sync(b)
+    for s in longs + shorts:
+        L.lbm_forces(s)                     # drop the transient
+    for b in batches:
+        L.lbm_batch_step(b, st.t_stat)
+    for b in batches:
+        L.lbm_batch_sync(b)
+    wall = time.perf_counter() - t0
+    out = []
+    for k, (scaling, re, tau, u) in enumerate(cases):
+        ref = _coeffs(st.D, u, *L.lbm_forces(longs[k]))
+        row = {"scaling": scaling, "re": re, "tau": tau, "u": u, "reference": ref}
+        sheds = ref["cl_rms"] > 1e-3
+        for name, s in (("zouhe", shorts[2 * k]), ("nn", shorts[2 * k + 1])):
+            try:
+                c = _coeffs(st.D, u, *L.lbm_forces(s))
+            except L.LbmError as ex:
+                if ex.status != 5:
+                    raise
+                row[name] = {"diverged": True}
+                continue
+            err = {"cd": abs(c["cd"] - ref["cd"]) / abs(ref["cd"])}
+            if sheds:
+                err["cl_rms"] = abs(c["cl_rms"] - ref["cl_rms"]) / ref["cl_rms"]
+                err["st"] = abs(c["st"] - ref["st"]) / ref["st"]
+            row[name] = {**c, "err": err}
+        row["nn"]["fallbacks"] = L.lbm_nn_fallbacks(shorts[2 * k + 1]) \
+            if "diverged" not in row["nn"] else None
+        out.append(row)
+    for b in batches:
+        L.lbm_batch_destroy(b)
+    for s in longs + shorts:
+        L.lbm_destroy(s)
+    return out, wall
+
+
+def snapshot_study(st: SnapshotStudy):
+    """Train from one snapshot, then the Reynolds sweep; a JSON-ready dict."""
+    import torch
+    keep = torch.cuda.Stream()
+    stream = keep.cuda_stream
+    net, info = snapshot_train(st, stream)
+    sweep, wall = reynolds_sweep(st, net, stream)
+    return {"D": st.D, "collision": st.collision, "re_train": st.re_train,
+            "nx_long": st.nx_for(st.long_wake_d), "nx_short": st.nx_for(st.short_wake_d),
+            "ny": st.ny, "t_trans": st.t_trans, "t_stat": st.t_stat, "training": info,
+            "sweep": sweep, "sweep_wall_s": wall}
+
+
+# --------------------------------------------------------------------------- #
 # Convected vortex (Sec. 4.1): outflow treatments against a longer domain
 # --------------------------------------------------------------------------- #
 CS = (1.0 / 3.0) ** 0.5
@@ -472,10 +652,13 @@ def _main(argv=None):
     import argparse
     import json
     ap = argparse.ArgumentParser(prog="python -m paper_2506_05293_gb300.workflow")
-    ap.add_argument("study", choices=["tuner"])
+    ap.add_argument("study", choices=["tuner", "snapshot"])
     ap.add_argument("--epochs", type=int, default=TunerStudy.epochs)
     ap.add_argument("--precision", default=TunerStudy.precision, choices=["fp32", "fp64"])
     args = ap.parse_args(argv)
+    if args.study == "snapshot":
+        print(json.dumps(snapshot_study(SnapshotStudy()), default=float))
+        return
     st = TunerStudy(epochs=args.epochs, precision=args.precision)
     res = tuner_study(st)
     out = {"segment_loss_initial": res["before"], "segment_loss_trained": res["after"],

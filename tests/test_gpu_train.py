@@ -59,6 +59,53 @@ def test_capture_matches_oracle(L, precision, tol):
     L.lbm_destroy(sim)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1.2e-7), ("fp32", 5e-6)])
+def test_snapshot_matches_oracle_and_the_plane_capture(L, precision, tol, tmp_path):
+    """Single-snapshot rows (every column of a window around and behind the
+    cylinder) against the oracle, and bit for bit against the rows the plane
+    capture records at the same columns during the next step."""
+    import torch
+    nx, ny, steps = 72, 40, 23
+    kind, init = _cyl_run(nx, ny)
+    cfg = L.lbm_config_default(nx=nx, ny=ny, tau=0.6, precision=precision, u_in=0.05,
+                               v_pert_amp=1e-3, seed=5)
+    sim = L.lbm_create(cfg)
+    L.lbm_set_geometry(sim, kind)
+    L.lbm_init_equilibrium(sim, *init)
+    L.lbm_step(sim, steps)
+    x0, x1 = 6, nx - 1
+    snap = torch.full(((x1 - x0) * ny + ny, 84), -1.0, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    L.lbm_capture_snapshot(sim, x0, x1, snap)
+    L.lbm_sync(sim)
+    got = snap[:(x1 - x0) * ny].cpu().numpy().astype(np.float64)
+    assert (snap[(x1 - x0) * ny:].cpu().numpy() == -1.0).all()
+    o = lbm.Solver(lbm.Config(nx=nx, ny=ny, tau=0.6, u_in=0.05, v_pert_amp=1e-3, seed=5), kind)
+    o.init_equilibrium(*init)
+    o.step(steps)
+    want = o.snapshot_rows(x0, x1)
+    assert np.abs(got - want).max() <= tol * np.abs(want).max()
+    ck = str(tmp_path / "state.bin")
+    L.lbm_save(sim, ck)                             # the exact stored state
+    for x in (x0, 16, 30, x1 - 1):                  # the plane capture of the next step
+        s2 = L.lbm_create(cfg)
+        L.lbm_set_geometry(s2, kind)
+        L.lbm_load(s2, ck)
+        buf = torch.zeros((ny, 84), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        L.lbm_capture_plane(s2, x, 1, buf)
+        L.lbm_step(s2, 1)
+        L.lbm_sync(s2)
+        c = x - x0
+        assert np.array_equal(buf.cpu().numpy(), snap[c * ny:(c + 1) * ny].cpu().numpy())
+        L.lbm_destroy(s2)
+    with pytest.raises(L.LbmError):
+        L.lbm_capture_snapshot(sim, 3, 10, snap)
+    with pytest.raises(L.LbmError):
+        L.lbm_capture_snapshot(sim, 10, nx, snap)
+    L.lbm_destroy(sim)
+
+
 def test_capture_stops_at_capacity_and_in_batches(L):
     import torch
     nx, ny = 40, 16

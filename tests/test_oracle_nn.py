@@ -204,3 +204,39 @@ def test_capture_every_and_uniform_state():
                     for w, (cx, cy) in zip([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, _C)])
     assert np.allclose(rows[:, :81], np.tile(feq, 9)[None, :], atol=1e-15, rtol=0)
     assert np.allclose(rows[:, 81:], feq[[3, 6, 7]][None, :], atol=1e-15, rtol=0)
+
+
+def test_snapshot_rows_follow_the_streaming_definition_and_equal_the_plane_capture():
+    """One snapshot's rows (Sec. 3.1's single-snapshot data set): entry by entry
+    the pull definition on a state with distinct values and a solid node in the
+    window, and, column by column, exactly what capture_plane records during the
+    next step of an open (inlet + outflow) lattice."""
+    ny, nx = 7, 12
+    kind = np.zeros((ny, nx), np.uint8)
+    kind[3, 5] = 1
+    o = lbm.Solver(lbm.Config(nx=nx, ny=ny, tau=0.8, u_in=0.04), kind)
+    f = np.empty((9, ny, nx))
+    for i in range(9):
+        for y in range(ny):
+            for x in range(nx):
+                f[i, y, x] = 0.1 + 1e-3 * i + 1e-5 * y + 1e-7 * x
+    o.f = f.copy()
+    rows = o.snapshot_rows(4, nx - 1)
+    assert rows.shape == ((nx - 5) * ny, 84)
+    for c, x in enumerate(range(4, nx - 1)):
+        for y in range(ny):
+            r = rows[c * ny + y]
+            for k in range(3):
+                for j in range(3):
+                    for i in range(9):
+                        assert r[k * 27 + j * 9 + i] == _post_stream_value(
+                            f, kind, i, x - 1 - k, (y + j - 1) % ny)
+            for n, i in enumerate((3, 6, 7)):
+                assert r[81 + n] == _post_stream_value(f, kind, i, x, y)
+    for x in (4, 7, nx - 2):
+        p = lbm.Solver(lbm.Config(nx=nx, ny=ny, tau=0.8, u_in=0.04), kind)
+        p.f = f.copy()
+        p.capture_plane(x, 1)
+        p.step(1)
+        c = x - 4
+        assert np.array_equal(p.dataset(), rows[c * ny:(c + 1) * ny])
