@@ -89,14 +89,31 @@ typedef struct {
   int64_t force_capacity;   /* device ring of per-step forces; 0: 1 << 20 steps */
   int64_t ramp_steps;       /* > 0: the inlet velocity of step t is u_in min(1, (t+1)/ramp_steps)
                                (a smooth start; the paper does not state how its runs start) */
+  int32_t layout;           /* lbm_layout: LBM_LAYOUT_AB (default) or LBM_LAYOUT_AA */
 } lbm_config;
+
+/* Population storage.  AB: two buffers, each step pulls from one into the
+ * other.  AA (Bailey et al., ICPP 2009): one buffer updated in place, half the
+ * population memory for the same 72 B (FP32) of traffic per node and step.
+ * Steps from an even step count read every node's nine incoming populations
+ * from its neighbours' opposite slots and push the nine outgoing ones into
+ * them; steps from an odd count read and write the node's own slots.  Solid
+ * nodes need no writes (the swapped slots already hold the reversed
+ * populations) and the momentum exchange is summed at the fluid side of each
+ * counted link.  Results equal the AB step's (forces up to the summation
+ * order).  An AA lattice runs alone (no batches), with the Zou & He outflow,
+ * on the register kernel (tiling variants 0-2), and supports neither capture
+ * calls nor lbm_copy_columns; one ghost column on each side keeps the
+ * populations that leave the lattice, so exports stay exact. */
+typedef enum { LBM_LAYOUT_AB = 0, LBM_LAYOUT_AA = 1 } lbm_layout;
 
 /* Fill *cfg with defaults (tau 0.6, BGK, FP32, open x, rho_out 1). */
 lbm_status lbm_config_default(lbm_config* cfg);
 
 /* Create a simulation: allocates two population buffers of
- * 9 * ny * pitch elements (pitch = nx rounded up to 64), initialised to the
- * rest state (rho = 1, u = 0), all cells fluid, Zou & He outflow. */
+ * 9 * ny * pitch elements (pitch = nx rounded up to 64), or with
+ * LBM_LAYOUT_AA one buffer with pitch = nx + 2 rounded up to 64, initialised
+ * to the rest state (rho = 1, u = 0), all cells fluid, Zou & He outflow. */
 lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out);
 lbm_status lbm_destroy(lbm_sim* sim);
 
@@ -361,8 +378,11 @@ lbm_status lbm_mass(lbm_sim* sim, double* mass);
 
 /* Device pointer of the current population buffer and its geometry, for
  * zero-copy access: element (i, y, x) is at base[i * plane + y * pitch + x],
- * storing f_i - w_i in the configured precision.  Valid until the next call
- * that steps or destroys the sim. */
+ * storing f_i - w_i in the configured precision.  With LBM_LAYOUT_AA after
+ * an even number of steps f_i(x, y) is at slot opp(i) of (x, y); after an odd
+ * number it is at slot i of (x + c_ix, y + c_iy) (y periodic, x = -1 and
+ * x = nx are the ghost columns).  Valid until the next call that steps or
+ * destroys the sim. */
 lbm_status lbm_device_state(lbm_sim* sim, void** base, int64_t* pitch, int64_t* plane);
 
 /* Tiling of the step kernel: rows per strip (1..4096; a strip is 128 columns)

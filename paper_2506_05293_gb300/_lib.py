@@ -31,7 +31,7 @@ class LbmConfig(Structure):
                 ("mrt_rates", c_double * 9), ("precision", c_int32), ("x_periodic", c_int32),
                 ("u_in", c_double), ("v_pert_amp", c_double), ("seed", c_uint64),
                 ("rho_out", c_double), ("stream", c_void_p), ("alloc", POINTER(LbmAllocator)),
-                ("force_capacity", c_int64), ("ramp_steps", c_int64)]
+                ("force_capacity", c_int64), ("ramp_steps", c_int64), ("layout", c_int32)]
 
 
 class LbmMlp(Structure):

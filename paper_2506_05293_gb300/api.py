@@ -65,6 +65,8 @@ def lbm_config_default(**kw):
             v = COLLISIONS[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "layout" and isinstance(v, str):
+            v = {"ab": 0, "aa": 1}[v]
         if k == "mrt_rates":
             arr = (c_double * 9)(*[float(r) for r in v])
             cfg.mrt_rates = arr

@@ -333,7 +333,9 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   if ((int64_t)cfg->nx * cfg->ny > (int64_t)1 << 31)
     return fail(LBM_ERR_ARG, "lattice larger than 2^31 nodes");
   if (cfg->ny > 65535) return fail(LBM_ERR_ARG, "ny must be <= 65535");
-  if ((int64_t)9 * cfg->ny * (((int64_t)cfg->nx + 63) / 64 * 64) >= ((int64_t)1 << 31))
+  if (cfg->layout != LBM_LAYOUT_AB && cfg->layout != LBM_LAYOUT_AA)
+    return fail(LBM_ERR_ARG, "unknown layout");
+  if ((int64_t)9 * cfg->ny * (((int64_t)cfg->nx + 2 + 63) / 64 * 64) >= ((int64_t)1 << 31))
     return fail(LBM_ERR_ARG, "9 * ny * pitch must stay below 2^31 elements");
   if (!(cfg->tau > 0.5) || !std::isfinite(cfg->tau)) return fail(LBM_ERR_ARG, "tau must be > 1/2");
   if (cfg->collision != LBM_BGK && cfg->collision != LBM_MRT)
@@ -358,7 +360,9 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   s->ny = cfg->ny;
   s->prec = cfg->precision;
   s->elem = s->prec == LBM_FP64 ? 8 : (s->prec == LBM_FP32 ? 4 : 2);
-  s->pitch = ((int64_t)s->nx + 63) / 64 * 64;
+  s->layout = cfg->layout;
+  // the in-place layout keeps a ghost column on each side (x = -1 and x = nx)
+  s->pitch = ((int64_t)s->nx + (s->layout == LBM_LAYOUT_AA ? 2 : 0) + 63) / 64 * 64;
   s->plane = s->pitch * s->ny;
   s->rho_out = cfg->rho_out;
   if (cfg->alloc) {
@@ -375,13 +379,20 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   // + slack: the staged kernel copies whole 16-byte aligned row segments that
   // may run up to 128 + 8 elements past the last row of the last population
   const size_t bytes = ((size_t)9 * s->plane + 256) * s->elem;
-  s->buf[0] = dev_alloc(s, bytes);
-  s->buf[1] = dev_alloc(s, bytes);
+  if (s->layout == LBM_LAYOUT_AA) {
+    s->buf_alloc = dev_alloc(s, bytes);
+    s->buf[0] = static_cast<unsigned char*>(s->buf_alloc) + s->elem;   // x = -1 at the start
+    s->buf[1] = s->buf[0];
+  } else {
+    s->buf[0] = dev_alloc(s, bytes);
+    s->buf[1] = dev_alloc(s, bytes);
+  }
   const int64_t cells = (int64_t)s->nx * s->ny;
   s->kind = (uint8_t*)dev_alloc(s, cells);
   s->words_per_row = (s->nx + 127) / 128 * 4;   // whole 16-byte groups per row
   s->solid_bits = (uint32_t*)dev_alloc(s, (size_t)s->words_per_row * s->ny * 4);
   s->links = (uint8_t*)dev_alloc(s, cells);
+  s->near_bits = (uint32_t*)dev_alloc(s, (size_t)s->words_per_row * s->ny * 4);
   s->ring_cap = cfg->force_capacity > 0 ? cfg->force_capacity : kDefaultRing;
   s->ring = (double*)dev_alloc(s, (size_t)2 * s->ring_cap * sizeof(double));
   s->status = (int*)dev_alloc(s, sizeof(int));
@@ -392,13 +403,17 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   ck(cudaMemsetAsync(s->status, 0, sizeof(int), s->stream), "memset");
   ck(cudaMemsetAsync(s->nn_fallbacks, 0, sizeof(unsigned long long), s->stream), "memset");
   ck(cudaMemsetAsync(s->ring, 0, (size_t)2 * s->ring_cap * sizeof(double), s->stream), "memset");
-  // padding columns are never read by the step, but keep them defined
-  ck(cudaMemsetAsync(s->buf[0], 0, bytes, s->stream), "memset");
-  ck(cudaMemsetAsync(s->buf[1], 0, bytes, s->stream), "memset");
+  // padding (and ghost) columns are never read by the step, but keep them defined
+  if (s->layout == LBM_LAYOUT_AA) {
+    ck(cudaMemsetAsync(s->buf_alloc, 0, bytes, s->stream), "memset");
+  } else {
+    ck(cudaMemsetAsync(s->buf[0], 0, bytes, s->stream), "memset");
+    ck(cudaMemsetAsync(s->buf[1], 0, bytes, s->stream), "memset");
+  }
   lbm::launch_geometry_prep(s->kind, s->nx, s->ny, s->cfg.x_periodic, s->solid_bits,
-                            s->words_per_row, s->links, s->stream);
+                            s->words_per_row, s->links, s->near_bits, s->stream);
   lbm::launch_init_equilibrium(s->prec, s->buf[0], s->nx, s->ny, s->pitch, s->plane, nullptr,
-                               nullptr, nullptr, s->stream);
+                               nullptr, nullptr, s->stream, lbm::pop_map(s, 0));
   ck(cudaGetLastError(), "init launch");
   lbm::group_init(s->own, std::vector<lbm_sim*>{s}, true);
   ck(cudaStreamSynchronize(s->stream), "create sync");
@@ -443,7 +458,7 @@ lbm_status lbm_set_geometry(lbm_sim* s, const uint8_t* kind) {
   LBM_GUARD_BEGIN
   ck(cudaMemcpyAsync(s->kind, kind, cells, cudaMemcpyHostToDevice, s->stream), "kind copy");
   lbm::launch_geometry_prep(s->kind, s->nx, s->ny, s->cfg.x_periodic, s->solid_bits,
-                            s->words_per_row, s->links, s->stream);
+                            s->words_per_row, s->links, s->near_bits, s->stream);
   ck(cudaGetLastError(), "geometry launch");
   ck(cudaStreamSynchronize(s->stream), "geometry sync");
   s->version++;
@@ -482,7 +497,7 @@ lbm_status lbm_init_equilibrium(lbm_sim* s, const double* rho, const double* ux,
   }
   s->cur = 0;
   lbm::launch_init_equilibrium(s->prec, s->buf[0], s->nx, s->ny, s->pitch, s->plane, dr, du, dv,
-                               s->stream);
+                               s->stream, lbm::pop_map(s, 0));
   ck(cudaGetLastError(), "init launch");
   reset_counters(s);
   ck(cudaStreamSynchronize(s->stream), "init sync");
@@ -503,6 +518,8 @@ lbm_status lbm_set_outflow_zouhe(lbm_sim* s, double rho_out) {
 
 lbm_status lbm_set_outflow_nn(lbm_sim* s, const lbm_mlp* net, double fallback_drho) {
   if (lbm_status st = check_sim(s)) return st;
+  if (s->layout == LBM_LAYOUT_AA)
+    return fail(LBM_ERR_UNSUPPORTED, "the in-place (AA) layout supports the Zou & He outflow only");
   if (!net || !net->params) return fail(LBM_ERR_ARG, "net and net->params must be non-NULL");
   if (s->cfg.x_periodic) return fail(LBM_ERR_STATE, "x is periodic: there is no outflow");
   if (s->nx < 5) return fail(LBM_ERR_ARG, "the NN outflow needs nx >= 5");
@@ -531,6 +548,8 @@ lbm_status lbm_set_outflow_nn(lbm_sim* s, const lbm_mlp* net, double fallback_dr
 lbm_status lbm_set_outflow_cbc(lbm_sim* s, double sigma, double kappa2, double mach, double length,
                                const lbm_mlp* tuner, int32_t exact_mass) {
   if (lbm_status st = check_sim(s)) return st;
+  if (s->layout == LBM_LAYOUT_AA)
+    return fail(LBM_ERR_UNSUPPORTED, "the in-place (AA) layout supports the Zou & He outflow only");
   if (s->cfg.x_periodic) return fail(LBM_ERR_STATE, "x is periodic: there is no outflow");
   if (s->nx < 4) return fail(LBM_ERR_ARG, "the characteristic outflow needs nx >= 4");
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(LBM_ERR_ARG, "sigma must be >= 0");
@@ -586,6 +605,8 @@ lbm_status lbm_nn_fallbacks(lbm_sim* s, int64_t* count) {
 lbm_status lbm_capture_plane(lbm_sim* s, int32_t x_t, int32_t every, float* dev_rows,
                              int64_t cap_rows) {
   if (lbm_status st = check_sim(s)) return st;
+  if (s->layout == LBM_LAYOUT_AA)
+    return fail(LBM_ERR_UNSUPPORTED, "capture needs the two-buffer (AB) layout");
   if (!dev_rows) {
     s->cap_every = 0;
     s->cap_out = nullptr;
@@ -606,6 +627,8 @@ lbm_status lbm_capture_plane(lbm_sim* s, int32_t x_t, int32_t every, float* dev_
 
 lbm_status lbm_capture_snapshot(lbm_sim* s, int32_t x_begin, int32_t x_end, float* dev_rows) {
   if (lbm_status st = check_sim(s)) return st;
+  if (s->layout == LBM_LAYOUT_AA)
+    return fail(LBM_ERR_UNSUPPORTED, "capture needs the two-buffer (AB) layout");
   if (!dev_rows) return fail(LBM_ERR_ARG, "dev_rows is NULL");
   if (!s->solid_bits) return fail(LBM_ERR_STATE, "set the geometry first");
   if (x_begin < 4 || x_end <= x_begin || x_end > s->nx - 1)
@@ -753,7 +776,7 @@ lbm_status lbm_fields(lbm_sim* s, double* rho, double* ux, double* uy) {
   LBM_GUARD_BEGIN
   double* d = s->scratch_fields;
   lbm::launch_export(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane, nullptr, d,
-                     d + cells, d + 2 * cells, s->stream);
+                     d + cells, d + 2 * cells, s->stream, lbm::pop_map(s, s->t_host));
   ck(cudaGetLastError(), "export launch");
   if (rho) ck(cudaMemcpyAsync(rho, d, cells * 8, cudaMemcpyDeviceToHost, s->stream), "copy");
   if (ux) ck(cudaMemcpyAsync(ux, d + cells, cells * 8, cudaMemcpyDeviceToHost, s->stream), "copy");
@@ -768,7 +791,8 @@ lbm_status lbm_get_populations(lbm_sim* s, double* f) {
   const int64_t cells = (int64_t)s->nx * s->ny;
   LBM_GUARD_BEGIN
   lbm::launch_export(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane,
-                     s->scratch_fields, nullptr, nullptr, nullptr, s->stream);
+                     s->scratch_fields, nullptr, nullptr, nullptr, s->stream,
+                     lbm::pop_map(s, s->t_host));
   ck(cudaGetLastError(), "export launch");
   ck(cudaMemcpyAsync(f, s->scratch_fields, 9 * cells * 8, cudaMemcpyDeviceToHost, s->stream),
      "copy");
@@ -784,7 +808,7 @@ lbm_status lbm_set_populations(lbm_sim* s, const double* f) {
   ck(cudaMemcpyAsync(s->scratch_fields, f, 9 * cells * 8, cudaMemcpyHostToDevice, s->stream),
      "copy");
   lbm::launch_import(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane,
-                     s->scratch_fields, s->stream);
+                     s->scratch_fields, s->stream, lbm::pop_map(s, s->t_host));
   ck(cudaGetLastError(), "import launch");
   ck(cudaStreamSynchronize(s->stream), "sync");
   return LBM_OK;
@@ -806,16 +830,18 @@ lbm_status lbm_save(lbm_sim* s, const char* path) {
   if (!path) return fail(LBM_ERR_ARG, "path is NULL");
   LBM_GUARD_BEGIN
   lbm::sim_settle(s);
-  const int64_t elems = 9 * s->plane;
+  const bool aa = s->layout == LBM_LAYOUT_AA;
+  const int64_t elems = 9 * s->plane + (aa ? 1 : 0);
   std::vector<unsigned char> host((size_t)(elems * (int64_t)s->elem));
-  ck(cudaMemcpyAsync(host.data(), s->buf[s->cur], host.size(), cudaMemcpyDeviceToHost,
-                     s->stream), "checkpoint copy");
+  ck(cudaMemcpyAsync(host.data(), aa ? s->buf_alloc : s->buf[s->cur], host.size(),
+                     cudaMemcpyDeviceToHost, s->stream), "checkpoint copy");
   if (lbm_status st = read_status(s)) return st;
   CheckpointHeader h{};
   memcpy(h.magic, kCheckpointMagic, 8);
   h.nx = s->nx;
   h.ny = s->ny;
   h.precision = s->prec;
+  h.pad = s->layout;
   h.t = s->t_host;
   h.elems = elems;
   FILE* fp = fopen(path, "wb");
@@ -838,10 +864,11 @@ lbm_status lbm_load(lbm_sim* s, const char* path) {
     fclose(fp);
     return fail(LBM_ERR_ARG, "not a checkpoint of this library");
   }
-  if (h.nx != s->nx || h.ny != s->ny || h.precision != s->prec || h.elems != 9 * s->plane ||
-      h.t < 0) {
+  const bool aa = s->layout == LBM_LAYOUT_AA;
+  if (h.nx != s->nx || h.ny != s->ny || h.precision != s->prec || h.pad != s->layout ||
+      h.elems != 9 * s->plane + (aa ? 1 : 0) || h.t < 0) {
     fclose(fp);
-    return fail(LBM_ERR_ARG, "the checkpoint is for another lattice size or precision");
+    return fail(LBM_ERR_ARG, "the checkpoint is for another lattice size, precision or layout");
   }
   std::vector<unsigned char> host((size_t)(h.elems * (int64_t)s->elem));
   const bool body = fread(host.data(), 1, host.size(), fp) == host.size();
@@ -849,8 +876,8 @@ lbm_status lbm_load(lbm_sim* s, const char* path) {
   if (!body) return fail(LBM_ERR_ARG, "the checkpoint is truncated");
   LBM_GUARD_BEGIN
   reset_counters(s);
-  ck(cudaMemcpyAsync(s->buf[0], host.data(), host.size(), cudaMemcpyHostToDevice, s->stream),
-     "checkpoint copy");
+  ck(cudaMemcpyAsync(aa ? s->buf_alloc : s->buf[0], host.data(), host.size(),
+                     cudaMemcpyHostToDevice, s->stream), "checkpoint copy");
   ck(cudaStreamSynchronize(s->stream), "checkpoint sync");
   s->cur = 0;
   s->t_host = h.t;
@@ -864,7 +891,7 @@ lbm_status lbm_mass(lbm_sim* s, double* mass) {
   if (!mass) return fail(LBM_ERR_ARG, "mass is NULL");
   LBM_GUARD_BEGIN
   lbm::launch_mass(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane, s->scratch_sums,
-                   s->ny, s->scratch_sums + s->ny, s->stream);
+                   s->ny, s->scratch_sums + s->ny, s->stream, lbm::pop_map(s, s->t_host));
   ck(cudaGetLastError(), "mass launch");
   ck(cudaMemcpyAsync(mass, s->scratch_sums + s->ny, 8, cudaMemcpyDeviceToHost, s->stream), "copy");
   return read_status(s);
@@ -891,6 +918,8 @@ static lbm_status check_tiling(int32_t rows, int32_t variant) {
 lbm_status lbm_set_tiling(lbm_sim* s, int32_t rows, int32_t variant) {
   if (lbm_status st = check_sim(s)) return st;
   if (lbm_status st = check_tiling(rows, variant)) return st;
+  if (s->layout == LBM_LAYOUT_AA && lbm::step_variant_is_bulk(variant))
+    return fail(LBM_ERR_UNSUPPORTED, "the in-place (AA) layout runs on variants 0-2");
   LBM_GUARD_BEGIN
   lbm::group_set_tiling(s->own, rows, variant);
   return LBM_OK;
@@ -909,6 +938,8 @@ lbm_status lbm_autotune(lbm_sim* s, int32_t steps, int64_t flush_bytes, float* b
   if (lbm_status st = check_sim(s)) return st;
   if (steps < 1 || steps > 10000) return fail(LBM_ERR_ARG, "steps must be in 1..10000");
   if (flush_bytes < 0) return fail(LBM_ERR_ARG, "flush_bytes must be >= 0");
+  if (s->layout == LBM_LAYOUT_AA)
+    return fail(LBM_ERR_UNSUPPORTED, "the in-place (AA) layout has one kernel: set rows instead");
   LBM_GUARD_BEGIN
   const float ms = lbm::group_autotune(s->own, steps, flush_bytes);
   if (best_ms) *best_ms = ms;
@@ -922,6 +953,8 @@ lbm_status lbm_batch_create(lbm_sim* const* sims, int32_t n, lbm_batch** out) {
   *out = nullptr;
   for (int32_t k = 0; k < n; ++k) {
     if (lbm_status st = check_sim(sims[k])) return st;
+    if (sims[k]->layout == LBM_LAYOUT_AA)
+      return fail(LBM_ERR_UNSUPPORTED, "an in-place (AA) lattice runs alone, not in a batch");
     if (sims[k]->prec != sims[0]->prec)
       return fail(LBM_ERR_ARG, "batch members must share one precision");
     if (sims[k]->stream != sims[0]->stream)

@@ -1077,6 +1077,8 @@ lbm_status lbm_copy_columns(lbm_sim* s, int32_t x0, int32_t width, double* dev_o
   using namespace lbm;
   if (!s || !s->buf[0]) return seg_fail(LBM_ERR_STATE, "sim is not initialised");
   if (!dev_out) return seg_fail(LBM_ERR_ARG, "dev_out is NULL");
+  if (s->layout == LBM_LAYOUT_AA)
+    return seg_fail(LBM_ERR_UNSUPPORTED, "column copies need the two-buffer (AB) layout");
   if (width < 1 || x0 < 0 || (int64_t)x0 + width > s->nx)
     return seg_fail(LBM_ERR_ARG, "columns out of range");
   try {

@@ -34,6 +34,7 @@ void fill_member(const lbm_sim* s, Member& m) {
   m.solid_bits = s->solid_bits;
   m.words_per_row = s->words_per_row;
   m.links = s->links;
+  m.near_bits = s->near_bits;
   m.omega = 1.0 / s->cfg.tau;
   const double* r = s->cfg.mrt_rates;
   bool any = false;
@@ -169,7 +170,7 @@ void build_table(Group& g) {
   // resident capacity for the stream-and-collide blocks: the boundary and
   // force-reduction blocks finish within microseconds, so they do not hold
   // their slots for the step and are not subtracted
-  const int room = std::max(1, g.max_blocks_v[g.variant]);
+  const int room = std::max(1, g.aa ? g.aa_max_blocks : g.max_blocks_v[g.variant]);
   std::vector<int32_t> force;   // strip -> force slot, when partials go per strip
   if (g.persistent) {
     const int cap = room;
@@ -322,7 +323,8 @@ void enqueue(Group& g, int q, int64_t t, int graph_k, bool reduce_prev) {
     p.t_offset = graph_k;
   }
   p.reduce_prev = reduce_prev ? 1 : 0;
-  launch_step(g.prec, g.coll_mode, p, g.variant, g.blocks, g.stream);
+  if (g.aa) launch_aa(g.prec, g.coll_mode, p, g.blocks, g.stream);
+  else launch_step(g.prec, g.coll_mode, p, g.variant, g.blocks, g.stream);
   ck(cudaGetLastError(), "step launch");
 }
 
@@ -428,6 +430,12 @@ void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single) {
   for (const lbm_sim* s : sims)
     if (s->cfg.collision != s0->cfg.collision) mode = 2;
   g.coll_mode = mode;
+  g.aa = single && s0->layout == LBM_LAYOUT_AA;
+  if (g.aa) {
+    g.variant = 0;   // the in-place kernel strides over the strips like the register kernel
+    g.aa_max_blocks = aa_max_blocks(g.prec, mode);
+    if (g.aa_max_blocks <= 0) throw CudaError{cudaGetLastError(), "occupancy query"};
+  }
   const lbm_allocator* a = s0->have_alloc ? &s0->alloc : nullptr;
   int most = 0;
   for (int v = 0; v < step_variants(); ++v) {

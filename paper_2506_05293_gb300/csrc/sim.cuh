@@ -26,7 +26,9 @@ struct Member {
   int32_t nx, ny, pitch, plane;   // elements; 9 * plane < 2^31
   const uint32_t* solid_bits;
   int32_t words_per_row;
-  const uint8_t* links;   // per node: bit i-1 set for a counted link in direction i
+  const uint8_t* links;   // per node: bit i-1 set for a counted link in direction i (a solid
+                          // node: to the fluid node s - c_i; a fluid node: to the solid x + c_i)
+  const uint32_t* near_bits;   // fluid nodes with a counted link (layout of solid_bits)
   double omega, mrt_se, mrt_seps, mrt_sq, mrt_snu, u_in, v_amp, rho_out;
   float omega_f, mrt_f[4], u_in_f, rho_out_f;   // FP32 copies for the FP32/FP16 kernels
   uint64_t seed;
@@ -119,16 +121,45 @@ int step_variants();
 // resident blocks per GPU (occupancy x SMs) of a variant; coll 2 = per member
 int step_max_blocks(int prec, int coll, int variant);
 void launch_geometry_prep(const uint8_t* kind, int nx, int ny, int x_periodic, uint32_t* bits,
-                          int words_per_row, uint8_t* links, cudaStream_t s);
+                          int words_per_row, uint8_t* links, uint32_t* near_bits, cudaStream_t s);
+
+// Where f_i(x, y) of the current state lives.  mode 0: two-buffer layout,
+// slot i of (x, y); 1: in-place layout after an even number of steps, slot
+// opp(i) of (x, y); 2: in-place layout after an odd number, slot i of
+// (x + c_ix, y + c_iy), y periodic, x periodic or into the ghost columns.
+struct PopMap {
+  int32_t mode = 0;
+  int32_t x_periodic = 0;
+};
+__host__ __device__ __forceinline__ int64_t pop_offset(const PopMap& pm, int i, int x, int y,
+                                                      int nx, int ny, int64_t pitch,
+                                                      int64_t plane) {
+  if (pm.mode == 1) return (int64_t)opp(i) * plane + (int64_t)y * pitch + x;
+  if (pm.mode == 2) {
+    int xs = x + cx(i), ys = y + cy(i);
+    ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+    if (pm.x_periodic) xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+    return (int64_t)i * plane + (int64_t)ys * pitch + xs;
+  }
+  return (int64_t)i * plane + (int64_t)y * pitch + x;
+}
+
 void launch_init_equilibrium(int prec, void* dst, int nx, int ny, int64_t pitch, int64_t plane,
                              const double* rho, const double* ux, const double* uy,
-                             cudaStream_t s);
+                             cudaStream_t s, PopMap pm = PopMap{});
 void launch_export(int prec, const void* src, int nx, int ny, int64_t pitch, int64_t plane,
-                   double* f_out, double* rho, double* ux, double* uy, cudaStream_t s);
+                   double* f_out, double* rho, double* ux, double* uy, cudaStream_t s,
+                   PopMap pm = PopMap{});
 void launch_import(int prec, void* dst, int nx, int ny, int64_t pitch, int64_t plane,
-                   const double* f_in, cudaStream_t s);
+                   const double* f_in, cudaStream_t s, PopMap pm = PopMap{});
 void launch_mass(int prec, const void* src, int nx, int ny, int64_t pitch, int64_t plane,
-                 double* partials, int n_partials, double* out, cudaStream_t s);
+                 double* partials, int n_partials, double* out, cudaStream_t s,
+                 PopMap pm = PopMap{});
+
+// ---- in-place (AA) step (aa.cu) ----
+// launches blocks + n_members (= 1) blocks like launch_step's register kernel
+void launch_aa(int prec, int coll, const StepParams& p, int blocks, cudaStream_t s);
+int aa_max_blocks(int prec, int coll);
 
 // ---- training rows and training (train.cu) ----
 constexpr int kRowFloats = 84;   // 81 inputs of Eq. 15 + f_3, f_6, f_7 at the plane
@@ -209,6 +240,8 @@ struct Group {
   int64_t* t_base = nullptr;
   int blocks = 0;                // lattice blocks of the current table
   bool persistent = false;
+  bool aa = false;               // the in-place layout (a single member)
+  int aa_max_blocks = 0;         // resident blocks of the in-place kernel
   std::vector<uint64_t> built_versions;   // member versions the table was built from
   bool pending = false;          // forces of the last launched step not yet in the rings
   int max_blocks_v[8] = {0};
@@ -231,6 +264,9 @@ struct lbm_sim {
   uint32_t* solid_bits = nullptr;
   int words_per_row = 0;
   uint8_t* links = nullptr;
+  uint32_t* near_bits = nullptr;
+  int layout = LBM_LAYOUT_AB;
+  void* buf_alloc = nullptr;         // AA: the allocation (buf[0] = it + one element)
   std::vector<uint8_t> solid_tile_rows;   // per 128-column tile and row: holds a counted solid
   double* ring = nullptr;
   int64_t ring_cap = 0;
@@ -286,5 +322,14 @@ struct CudaError {
 };
 inline void ck(cudaError_t e, const char* what) {
   if (e != cudaSuccess) throw CudaError{e, what};
+}
+// where the state after t steps keeps its populations (see PopMap)
+inline PopMap pop_map(const lbm_sim* s, int64_t t) {
+  PopMap pm;
+  if (s->layout == LBM_LAYOUT_AA) {
+    pm.mode = t % 2 == 0 ? 1 : 2;
+    pm.x_periodic = s->cfg.x_periodic;
+  }
+  return pm;
 }
 }  // namespace lbm

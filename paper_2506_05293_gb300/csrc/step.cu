@@ -125,44 +125,53 @@ void launch_step(int prec, int coll, const StepParams& p, int variant, int block
 // counted solid node, the mask of links to fluid neighbours s - c_i.
 __global__ void geometry_prep_kernel(const uint8_t* __restrict__ kind, int nx, int ny,
                                      int x_periodic, uint32_t* bits, int wpr,
-                                     uint8_t* links) {
+                                     uint8_t* links, uint32_t* near_bits) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (w >= wpr || y >= ny) return;
-  uint32_t word = 0;
+  uint32_t word = 0, near = 0;
   for (int b = 0; b < 32; ++b) {
     const int x = w * 32 + b;
     if (x >= nx) break;
     const uint8_t k = kind[(int64_t)y * nx + x];
     if (k != LBM_CELL_FLUID) word |= 1u << b;
+    // a counted solid node: links to the fluid nodes s - c_i; a fluid node:
+    // links to the counted solid nodes x + c_i (the same links seen from the
+    // fluid side, where the in-place step sums them)
+    const uint8_t want = k == LBM_CELL_SOLID ? LBM_CELL_FLUID : LBM_CELL_SOLID;
+    const int sgn = k == LBM_CELL_SOLID ? -1 : 1;
     uint8_t lk = 0;
-    if (k == LBM_CELL_SOLID) {
+    if (k == LBM_CELL_SOLID || k == LBM_CELL_FLUID) {
       for (int i = 1; i < 9; ++i) {
-        int sx = x - cx(i);
-        int sy = y - cy(i);
+        int sx = x + sgn * cx(i);
+        int sy = y + sgn * cy(i);
         sy = (sy + ny) % ny;
         if (sx < 0 || sx >= nx) {
           if (!x_periodic) continue;
           sx = (sx + nx) % nx;
         }
-        if (kind[(int64_t)sy * nx + sx] == LBM_CELL_FLUID) lk |= (uint8_t)(1u << (i - 1));
+        if (kind[(int64_t)sy * nx + sx] == want) lk |= (uint8_t)(1u << (i - 1));
       }
     }
     links[(int64_t)y * nx + x] = lk;
+    if (k == LBM_CELL_FLUID && lk) near |= 1u << b;
   }
   bits[(int64_t)y * wpr + w] = word;
+  if (near_bits) near_bits[(int64_t)y * wpr + w] = near;
 }
 
 void launch_geometry_prep(const uint8_t* kind, int nx, int ny, int x_periodic, uint32_t* bits,
-                          int words_per_row, uint8_t* links, cudaStream_t s) {
+                          int words_per_row, uint8_t* links, uint32_t* near_bits, cudaStream_t s) {
   dim3 grid((words_per_row + 127) / 128, ny);
-  geometry_prep_kernel<<<grid, 128, 0, s>>>(kind, nx, ny, x_periodic, bits, words_per_row, links);
+  geometry_prep_kernel<<<grid, 128, 0, s>>>(kind, nx, ny, x_periodic, bits, words_per_row, links,
+                                            near_bits);
 }
 
 // ---- initialisation, import and export --------------------------------------
 template <typename S>
 __global__ void init_eq_kernel(S* dst, int nx, int ny, int64_t pitch, int64_t plane,
-                               const double* rho, const double* ux, const double* uy) {
+                               const double* rho, const double* ux, const double* uy,
+                               PopMap pm) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= nx) return;
@@ -172,25 +181,25 @@ __global__ void init_eq_kernel(S* dst, int nx, int ny, int64_t pitch, int64_t pl
   const double v = uy ? uy[c] : 0.0;
   double heq[9];
   heq_all<double>(r - 1.0, u, v, heq);
-  for (int i = 0; i < 9; ++i) dst[i * plane + (int64_t)y * pitch + x] = from_r<S>(heq[i]);
+  for (int i = 0; i < 9; ++i) dst[pop_offset(pm, i, x, y, nx, ny, pitch, plane)] = from_r<S>(heq[i]);
 }
 
 void launch_init_equilibrium(int prec, void* dst, int nx, int ny, int64_t pitch, int64_t plane,
                              const double* rho, const double* ux, const double* uy,
-                             cudaStream_t s) {
+                             cudaStream_t s, PopMap pm) {
   dim3 grid((nx + 127) / 128, ny);
   if (prec == LBM_FP64)
-    init_eq_kernel<double><<<grid, 128, 0, s>>>((double*)dst, nx, ny, pitch, plane, rho, ux, uy);
+    init_eq_kernel<double><<<grid, 128, 0, s>>>((double*)dst, nx, ny, pitch, plane, rho, ux, uy, pm);
   else if (prec == LBM_FP32)
-    init_eq_kernel<float><<<grid, 128, 0, s>>>((float*)dst, nx, ny, pitch, plane, rho, ux, uy);
+    init_eq_kernel<float><<<grid, 128, 0, s>>>((float*)dst, nx, ny, pitch, plane, rho, ux, uy, pm);
   else
-    init_eq_kernel<__half><<<grid, 128, 0, s>>>((__half*)dst, nx, ny, pitch, plane, rho, ux, uy);
+    init_eq_kernel<__half><<<grid, 128, 0, s>>>((__half*)dst, nx, ny, pitch, plane, rho, ux, uy, pm);
 }
 
 // f_i = h_i + w_i into a dense double[9][ny][nx]; moments into rho/ux/uy.
 template <typename S>
 __global__ void export_kernel(const S* src, int nx, int ny, int64_t pitch, int64_t plane,
-                              double* f_out, double* rho, double* ux, double* uy) {
+                              double* f_out, double* rho, double* ux, double* uy, PopMap pm) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= nx) return;
@@ -198,7 +207,8 @@ __global__ void export_kernel(const S* src, int nx, int ny, int64_t pitch, int64
   const int64_t n = (int64_t)nx * ny;
   double f[9];
   for (int i = 0; i < 9; ++i) {
-    f[i] = (double)to_r<double>(src[i * plane + (int64_t)y * pitch + x]) + wgt<double>(i);
+    f[i] = (double)to_r<double>(src[pop_offset(pm, i, x, y, nx, ny, pitch, plane)]) +
+           wgt<double>(i);
     if (f_out) f_out[i * n + c] = f[i];
   }
   double r = 0.0, jx = 0.0, jy = 0.0;
@@ -213,51 +223,53 @@ __global__ void export_kernel(const S* src, int nx, int ny, int64_t pitch, int64
 }
 
 void launch_export(int prec, const void* src, int nx, int ny, int64_t pitch, int64_t plane,
-                   double* f_out, double* rho, double* ux, double* uy, cudaStream_t s) {
+                   double* f_out, double* rho, double* ux, double* uy, cudaStream_t s,
+                   PopMap pm) {
   dim3 grid((nx + 127) / 128, ny);
   if (prec == LBM_FP64)
     export_kernel<double><<<grid, 128, 0, s>>>((const double*)src, nx, ny, pitch, plane, f_out,
-                                               rho, ux, uy);
+                                               rho, ux, uy, pm);
   else if (prec == LBM_FP32)
     export_kernel<float><<<grid, 128, 0, s>>>((const float*)src, nx, ny, pitch, plane, f_out, rho,
-                                              ux, uy);
+                                              ux, uy, pm);
   else
     export_kernel<__half><<<grid, 128, 0, s>>>((const __half*)src, nx, ny, pitch, plane, f_out,
-                                               rho, ux, uy);
+                                               rho, ux, uy, pm);
 }
 
 template <typename S>
 __global__ void import_kernel(S* dst, int nx, int ny, int64_t pitch, int64_t plane,
-                              const double* f_in) {
+                              const double* f_in, PopMap pm) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= nx) return;
   const int64_t c = (int64_t)y * nx + x;
   const int64_t n = (int64_t)nx * ny;
   for (int i = 0; i < 9; ++i)
-    dst[i * plane + (int64_t)y * pitch + x] = from_r<S>(f_in[i * n + c] - wgt<double>(i));
+    dst[pop_offset(pm, i, x, y, nx, ny, pitch, plane)] = from_r<S>(f_in[i * n + c] - wgt<double>(i));
 }
 
 void launch_import(int prec, void* dst, int nx, int ny, int64_t pitch, int64_t plane,
-                   const double* f_in, cudaStream_t s) {
+                   const double* f_in, cudaStream_t s, PopMap pm) {
   dim3 grid((nx + 127) / 128, ny);
   if (prec == LBM_FP64)
-    import_kernel<double><<<grid, 128, 0, s>>>((double*)dst, nx, ny, pitch, plane, f_in);
+    import_kernel<double><<<grid, 128, 0, s>>>((double*)dst, nx, ny, pitch, plane, f_in, pm);
   else if (prec == LBM_FP32)
-    import_kernel<float><<<grid, 128, 0, s>>>((float*)dst, nx, ny, pitch, plane, f_in);
+    import_kernel<float><<<grid, 128, 0, s>>>((float*)dst, nx, ny, pitch, plane, f_in, pm);
   else
-    import_kernel<__half><<<grid, 128, 0, s>>>((__half*)dst, nx, ny, pitch, plane, f_in);
+    import_kernel<__half><<<grid, 128, 0, s>>>((__half*)dst, nx, ny, pitch, plane, f_in, pm);
 }
 
 // ---- total mass: per-row partial sums, then one block sums the rows --------
 template <typename S>
 __global__ void mass_rows_kernel(const S* src, int nx, int ny, int64_t pitch, int64_t plane,
-                                 double* partials) {
+                                 double* partials, PopMap pm) {
   const int y = blockIdx.x;
   double acc = 0.0;
   for (int x = threadIdx.x; x < nx; x += blockDim.x) {
     double cell = 1.0;   // sum of the weights
-    for (int i = 0; i < 9; ++i) cell += (double)to_r<double>(src[i * plane + (int64_t)y * pitch + x]);
+    for (int i = 0; i < 9; ++i)
+      cell += (double)to_r<double>(src[pop_offset(pm, i, x, y, nx, ny, pitch, plane)]);
     acc += cell;
   }
   __shared__ double sh[32];
@@ -288,14 +300,17 @@ __global__ void sum_partials_kernel(const double* partials, int n, double* out) 
 }
 
 void launch_mass(int prec, const void* src, int nx, int ny, int64_t pitch, int64_t plane,
-                 double* partials, int n_partials, double* out, cudaStream_t s) {
+                 double* partials, int n_partials, double* out, cudaStream_t s, PopMap pm) {
   (void)n_partials;
   if (prec == LBM_FP64)
-    mass_rows_kernel<double><<<ny, 256, 0, s>>>((const double*)src, nx, ny, pitch, plane, partials);
+    mass_rows_kernel<double><<<ny, 256, 0, s>>>((const double*)src, nx, ny, pitch, plane, partials,
+                                                pm);
   else if (prec == LBM_FP32)
-    mass_rows_kernel<float><<<ny, 256, 0, s>>>((const float*)src, nx, ny, pitch, plane, partials);
+    mass_rows_kernel<float><<<ny, 256, 0, s>>>((const float*)src, nx, ny, pitch, plane, partials,
+                                               pm);
   else
-    mass_rows_kernel<__half><<<ny, 256, 0, s>>>((const __half*)src, nx, ny, pitch, plane, partials);
+    mass_rows_kernel<__half><<<ny, 256, 0, s>>>((const __half*)src, nx, ny, pitch, plane, partials,
+                                                pm);
   sum_partials_kernel<<<1, 1024, 0, s>>>(partials, ny, out);
 }
 
