@@ -128,24 +128,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(layout="ab"):
     h = hashlib.sha256()
-    for f in ("step_kernels.cuh", "step.cu", "lattice.cuh", "sim.cuh"):
+    files = ("step_kernels.cuh", "step.cu", "lattice.cuh", "sim.cuh")
+    if layout == "aa":
+        files += ("aa.cu",)
+    for f in files:
         with open(os.path.join(ROOT, "paper_2506_05293_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def step_kernel_traffic(prec, wl):
+def step_kernel_traffic(prec, wl, layout="ab"):
     """dram bytes per launch of the step kernel from the committed ncu summary,
     if the kernel sources are unchanged since it was taken (else None)."""
-    path = os.path.join(ROOT, "profiles", f"step_kernel_{wl}_{prec}.md")
+    tag = "" if layout == "ab" else f"_{layout}"
+    path = os.path.join(ROOT, "profiles", f"step_kernel{tag}_{wl}_{prec}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.e+]+)", txt)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    if not m or not t or m.group(1) != kernel_source_hash(layout):
         return None
     return float(t.group(1))
 
@@ -319,12 +323,43 @@ def workload_outflow(wl):
     return "+".join(sorted({m["outflow"] for m in WORKLOADS[wl]}))
 
 
-def _make_members(L, wl, prec, stream):
+class _Stepper:
+    """The lattices of a workload advanced together: a batch, or with the
+    in-place (AA) layout the single lattice itself."""
+
+    def __init__(self, L, sims, layout):
+        self.L, self.sims, self.aa = L, sims, layout == "aa"
+        self.batch = None if self.aa else L.lbm_batch_create(sims)
+
+    def step(self, n):
+        if self.aa:
+            self.L.lbm_step(self.sims[0], n)
+        else:
+            self.L.lbm_batch_step(self.batch, n)
+
+    def set_tiling(self, rows, variant):
+        if self.aa:
+            self.L.lbm_set_tiling(self.sims[0], rows, variant)
+        else:
+            self.L.lbm_batch_set_tiling(self.batch, rows, variant)
+
+    def autotune(self, steps, flush_bytes):
+        if self.aa:
+            return self.L.lbm_autotune(self.sims[0], steps=steps, flush_bytes=flush_bytes)
+        return self.L.lbm_batch_autotune(self.batch, steps=steps, flush_bytes=flush_bytes)
+
+    def destroy(self):
+        if self.batch is not None:
+            self.L.lbm_batch_destroy(self.batch)
+
+
+def _make_members(L, wl, prec, stream, layout="ab"):
     sims, kinds, inits = [], [], []
     for m in WORKLOADS[wl]:
         kind, tau, init = member_geometry(m)
         cfg = L.lbm_config_default(nx=m["nx"], ny=m["ny"], tau=tau, precision=prec,
-                                   collision=m["collision"], u_in=m["U"], stream=stream)
+                                   collision=m["collision"], u_in=m["U"], stream=stream,
+                                   layout=layout)
         s = L.lbm_create(cfg)
         if m["outflow"] == "cbc":
             L.lbm_set_outflow_cbc(s, 0.25, m["mach"], m["mach"], 0.0)
@@ -420,25 +455,26 @@ def run_ours(args):
     prec, wl = args.precision, args.workload
     nodes = workload_nodes(wl)
     bpn = BYTES_PER_NODE[prec]
-    working_set = bpn * nodes          # two population buffers of bpn / 2 bytes per node
+    # two population buffers of bpn / 2 bytes per node; one with the in-place layout
+    working_set = bpn * nodes // (2 if args.layout == "aa" else 1)
     flush_mode = working_set < L2_BYTES
     stream = torch.cuda.Stream()
-    sims, kinds, inits = _make_members(L, wl, prec, stream.cuda_stream)
+    sims, kinds, inits = _make_members(L, wl, prec, stream.cuda_stream, args.layout)
     for s, kind, init in zip(sims, kinds, inits):
         L.lbm_set_geometry(s, kind)
         L.lbm_init_equilibrium(s, *init)
-    batch = L.lbm_batch_create(sims)
+    batch = _Stepper(L, sims, args.layout)
     flush_bytes = 256 * 1024 * 1024 if flush_mode else 0
     if args.rows:
         rows, variant = args.rows, args.variant          # fixed tiling (profiling)
-        L.lbm_batch_set_tiling(batch, rows, variant)
+        batch.set_tiling(rows, variant)
     else:
-        rows, variant, _ = L.lbm_batch_autotune(batch, steps=30, flush_bytes=flush_bytes)
+        rows, variant, _ = batch.autotune(30, flush_bytes)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda") if flush_mode else None
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            L.lbm_batch_step(batch, 1)
+            batch.step(1)
             if flush is not None:
                 flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -452,7 +488,7 @@ def run_ours(args):
                       for _ in range(args.steps)]
                 for k in range(args.steps):
                     ev[k][0].record(stream)
-                    L.lbm_batch_step(batch, 1)
+                    batch.step(1)
                     ev[k][1].record(stream)
                     flush.fill_(float(k))
                 torch.cuda.synchronize()
@@ -461,7 +497,7 @@ def run_ours(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                L.lbm_batch_step(batch, args.steps)
+                batch.step(args.steps)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 total_ms = e0.elapsed_time(e1)
@@ -482,7 +518,7 @@ def run_ours(args):
         total_ms = max_over_ranks(total_ms, "cuda")
     value = job_glups(world, nodes, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
-    L.lbm_batch_destroy(batch)
+    batch.destroy()
     for s in sims:
         L.lbm_destroy(s)
 
@@ -490,7 +526,7 @@ def run_ours(args):
     # initial fields in from pinned host memory; 1000 steps of the batch; force
     # series and fields out
     e2e_steps = 1000
-    sims2, kinds2, inits2 = _make_members(L, wl, prec, stream.cuda_stream)
+    sims2, kinds2, inits2 = _make_members(L, wl, prec, stream.cuda_stream, args.layout)
     pinned_in = []
     for kind, (r0, u0, v0) in zip(kinds2, inits2):
         k_p = torch.empty(kind.shape, dtype=torch.uint8, pin_memory=True).numpy()
@@ -511,22 +547,22 @@ def run_ours(args):
         L.lbm_set_geometry(s, k_p)
         L.lbm_init_equilibrium(s, r_p, u_p, v_p)
         h2d += k_p.nbytes + r_p.nbytes + u_p.nbytes + v_p.nbytes
-    batch2 = L.lbm_batch_create(sims2)
-    L.lbm_batch_set_tiling(batch2, rows, variant)
-    L.lbm_batch_step(batch2, e2e_steps)
+    batch2 = _Stepper(L, sims2, args.layout)
+    batch2.set_tiling(rows, variant)
+    batch2.step(e2e_steps)
     for s, m in zip(sims2, WORKLOADS[wl]):
         _drain(L, s, lambda: L.lbm_forces(s))
         _drain(L, s, lambda: L.lbm_fields(s))
         d2h += 2 * 8 * e2e_steps + 3 * 8 * m["nx"] * m["ny"]
     e2e_s = time.perf_counter() - w0
-    L.lbm_batch_destroy(batch2)
+    batch2.destroy()
     for s in sims2:
         L.lbm_destroy(s)
     e2e_value = world * nodes * e2e_steps / e2e_s / 1e9
 
     peak, peak_kind = measured_peaks()
     achieved = bpn * nodes / (ms_per_step * 1e-3) / 1e9
-    traffic = step_kernel_traffic(prec, wl)
+    traffic = step_kernel_traffic(prec, wl, args.layout)
 
     if rank != 0:
         if world > 1:
@@ -554,7 +590,8 @@ def run_ours(args):
                                if len(WORKLOADS[wl]) <= 16 else
                                f"{len(WORKLOADS[wl])} lattices, first: "
                                f"{member_label(WORKLOADS[wl][0])}"),
-                   "outflow": workload_outflow(wl), "storage": prec, "working_set_bytes": working_set,
+                   "outflow": workload_outflow(wl), "storage": prec, "layout": args.layout,
+                   "working_set_bytes": working_set,
                    "l2": ("flushed before each timed step (256 MB device write), steps timed one "
                           "by one") if flush_mode else
                          "working set larger than L2: no flush, steps back to back",
@@ -593,6 +630,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the NN vs Zou & He truncation study (about a minute)")
+    ap.add_argument("--layout", default="ab", choices=["ab", "aa"],
+                    help="population storage: two buffers, or one updated in place (single-"
+                         "lattice workloads)")
     ap.add_argument("--no-tuner", action="store_true",
                     help="skip the CBC tuner training study (a few seconds)")
     ap.add_argument("--rows", type=int, default=0, help="fixed tiling instead of the autotuner")
@@ -600,6 +640,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.layout == "aa" and len(WORKLOADS[args.workload]) != 1:
+        ap.error("--layout aa runs single-lattice workloads (an in-place lattice is not batched)")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -102,8 +102,8 @@ typedef struct {
  * populations) and the momentum exchange is summed at the fluid side of each
  * counted link.  Results equal the AB step's (forces up to the summation
  * order).  An AA lattice runs alone (no batches), with the Zou & He outflow,
- * on the register kernel (tiling variants 0-2), and supports neither capture
- * calls nor lbm_copy_columns; one ghost column on each side keeps the
+ * on its own kernel (tiling variants 0-2 set its occupancy; the autotuner
+ * tries those), and supports neither capture calls nor lbm_copy_columns; one ghost column on each side keeps the
  * populations that leave the lattice, so exports stay exact. */
 typedef enum { LBM_LAYOUT_AB = 0, LBM_LAYOUT_AA = 1 } lbm_layout;
 

@@ -938,8 +938,6 @@ lbm_status lbm_autotune(lbm_sim* s, int32_t steps, int64_t flush_bytes, float* b
   if (lbm_status st = check_sim(s)) return st;
   if (steps < 1 || steps > 10000) return fail(LBM_ERR_ARG, "steps must be in 1..10000");
   if (flush_bytes < 0) return fail(LBM_ERR_ARG, "flush_bytes must be >= 0");
-  if (s->layout == LBM_LAYOUT_AA)
-    return fail(LBM_ERR_UNSUPPORTED, "the in-place (AA) layout has one kernel: set rows instead");
   LBM_GUARD_BEGIN
   const float ms = lbm::group_autotune(s->own, steps, flush_bytes);
   if (best_ms) *best_ms = ms;

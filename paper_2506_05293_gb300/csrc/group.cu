@@ -170,7 +170,8 @@ void build_table(Group& g) {
   // resident capacity for the stream-and-collide blocks: the boundary and
   // force-reduction blocks finish within microseconds, so they do not hold
   // their slots for the step and are not subtracted
-  const int room = std::max(1, g.aa ? g.aa_max_blocks : g.max_blocks_v[g.variant]);
+  const int room = std::max(1, g.aa ? g.aa_max_blocks[std::min(g.variant, 2)]
+                                    : g.max_blocks_v[g.variant]);
   std::vector<int32_t> force;   // strip -> force slot, when partials go per strip
   if (g.persistent) {
     const int cap = room;
@@ -323,7 +324,7 @@ void enqueue(Group& g, int q, int64_t t, int graph_k, bool reduce_prev) {
     p.t_offset = graph_k;
   }
   p.reduce_prev = reduce_prev ? 1 : 0;
-  if (g.aa) launch_aa(g.prec, g.coll_mode, p, g.blocks, g.stream);
+  if (g.aa) launch_aa(g.prec, g.coll_mode, p, g.variant, g.blocks, g.stream);
   else launch_step(g.prec, g.coll_mode, p, g.variant, g.blocks, g.stream);
   ck(cudaGetLastError(), "step launch");
 }
@@ -433,8 +434,10 @@ void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single) {
   g.aa = single && s0->layout == LBM_LAYOUT_AA;
   if (g.aa) {
     g.variant = 0;   // the in-place kernel strides over the strips like the register kernel
-    g.aa_max_blocks = aa_max_blocks(g.prec, mode);
-    if (g.aa_max_blocks <= 0) throw CudaError{cudaGetLastError(), "occupancy query"};
+    for (int v = 0; v < 3; ++v) {
+      g.aa_max_blocks[v] = aa_max_blocks(g.prec, mode, v);
+      if (g.aa_max_blocks[v] <= 0) throw CudaError{cudaGetLastError(), "occupancy query"};
+    }
   }
   const lbm_allocator* a = s0->have_alloc ? &s0->alloc : nullptr;
   int most = 0;
@@ -568,7 +571,7 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
       lbm_sim* s = g.sims[k];
       const size_t bytes = ((size_t)9 * s->plane + 256) * s->elem;
       ck(cudaMalloc(&snaps[k], bytes), "autotune snapshot");
-      ck(cudaMemcpyAsync(snaps[k], s->buf[s->cur], bytes, cudaMemcpyDeviceToDevice, g.stream),
+      ck(cudaMemcpyAsync(snaps[k], state_alloc(s), bytes, cudaMemcpyDeviceToDevice, g.stream),
          "snapshot");
       saved[k].cur = s->cur;
       saved[k].t = s->t_host;
@@ -587,7 +590,7 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
         lbm_sim* s = g.sims[k];
         const size_t bytes = ((size_t)9 * s->plane + 256) * s->elem;
         s->cur = saved[k].cur;
-        ck(cudaMemcpyAsync(s->buf[s->cur], snaps[k], bytes, cudaMemcpyDeviceToDevice, g.stream),
+        ck(cudaMemcpyAsync(state_alloc(s), snaps[k], bytes, cudaMemcpyDeviceToDevice, g.stream),
            "restore");
         ck(cudaMemcpyAsync(s->nn_fallbacks, &saved[k].fb, 8, cudaMemcpyHostToDevice, g.stream),
            "restore");
@@ -603,6 +606,7 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
     float best = 1e30f;
     int best_rows = g.rows, best_var = g.variant;
     for (int v = 0; v < step_variants(); ++v) {
+      if (g.aa && step_variant_is_bulk(v)) continue;   // the in-place kernel: variants 0-2
       for (int r : rows_c) {
         group_set_tiling(g, r, v);
         build_table(g);

@@ -158,8 +158,9 @@ void launch_mass(int prec, const void* src, int nx, int ny, int64_t pitch, int64
 
 // ---- in-place (AA) step (aa.cu) ----
 // launches blocks + n_members (= 1) blocks like launch_step's register kernel
-void launch_aa(int prec, int coll, const StepParams& p, int blocks, cudaStream_t s);
-int aa_max_blocks(int prec, int coll);
+// variants 0-2 choose 6, 8 or 10 resident blocks per SM
+void launch_aa(int prec, int coll, const StepParams& p, int variant, int blocks, cudaStream_t s);
+int aa_max_blocks(int prec, int coll, int variant);
 
 // ---- training rows and training (train.cu) ----
 constexpr int kRowFloats = 84;   // 81 inputs of Eq. 15 + f_3, f_6, f_7 at the plane
@@ -241,7 +242,7 @@ struct Group {
   int blocks = 0;                // lattice blocks of the current table
   bool persistent = false;
   bool aa = false;               // the in-place layout (a single member)
-  int aa_max_blocks = 0;         // resident blocks of the in-place kernel
+  int aa_max_blocks[3] = {0, 0, 0};   // resident blocks of the in-place kernel per variant
   std::vector<uint64_t> built_versions;   // member versions the table was built from
   bool pending = false;          // forces of the last launched step not yet in the rings
   int max_blocks_v[8] = {0};
@@ -322,6 +323,11 @@ struct CudaError {
 };
 inline void ck(cudaError_t e, const char* what) {
   if (e != cudaSuccess) throw CudaError{e, what};
+}
+// the allocation holding the current state (9 plane + 256 elements): the in-place
+// layout's buffer starts one element (the first ghost) before buf[0]
+inline void* state_alloc(lbm_sim* s) {
+  return s->layout == LBM_LAYOUT_AA ? s->buf_alloc : s->buf[s->cur];
 }
 // where the state after t steps keeps its populations (see PopMap)
 inline PopMap pop_map(const lbm_sim* s, int64_t t) {
