@@ -40,6 +40,7 @@ class Study:
     v_pert_amp: float = 1e-3
     fallback_drho: float = 0.05
     precision: str = "fp32"
+    autotune: bool = True            # tune every lattice's tiling before it runs
     stream: int = 0
     timings: dict = field(default_factory=dict)
 
@@ -81,6 +82,14 @@ def make_sim(st: Study, nx):
     return s
 
 
+def _tuned(st, s):
+    """The sim with the fastest tiling for its size and boundaries (the
+    autotuner restores the state it times)."""
+    if st.autotune:
+        L.lbm_autotune(s, steps=30)
+    return s
+
+
 def coefficients(st: Study, fx, fy):
     """C_D mean, C_L RMS (about its mean) and St of a force window (Eq. 12 with
     rho = 1, U = inlet velocity, reference length D)."""
@@ -105,7 +114,7 @@ def long_run(st: Study, rows):
     reference coefficients, the number of rows and the developed populations
     at t_trans (for restarts)."""
     t0 = time.perf_counter()
-    s = make_sim(st, st.nx_long)
+    s = _tuned(st, make_sim(st, st.nx_long))
     L.lbm_step(s, st.capture_from)
     L.lbm_capture_plane(s, st.nx_short - 1, st.every, rows)
     L.lbm_step(s, st.t_trans - st.capture_from)
@@ -162,7 +171,6 @@ def truncated_runs(st: Study, ref, net, f_dev, starts=("rest", "restart")):
     out = {}
 
     def one(name, nx, kind, start):
-        t0 = time.perf_counter()
         s = make_sim(st, nx)
         if kind == "nn":
             L.lbm_set_outflow_nn(s, layers, "tanh", mean, std, scale, st.fallback_drho)
@@ -171,6 +179,8 @@ def truncated_runs(st: Study, ref, net, f_dev, starts=("rest", "restart")):
             skip = st.t_restart_skip
         else:
             skip = st.t_trans
+        _tuned(st, s)
+        t0 = time.perf_counter()
         r = _window(st, s, skip, st.t_stat)
         r["err"] = {k: abs(r[k] - ref[k]) / abs(ref[k]) for k in ref}
         if kind == "nn":
@@ -289,6 +299,7 @@ def snapshot_train(st: SnapshotStudy, stream):
     t0 = time.perf_counter()
     nx = st.nx_for(st.long_wake_d)
     s = _cyl_sim(st, nx, st.tau_for(st.re_train, st.u), st.u, stream)
+    L.lbm_autotune(s, steps=30)
     L.lbm_step(s, st.t_snapshot)
     x0 = int(round((st.centre_d + st.train_from_d) * st.D))
     x1 = nx - 1
@@ -342,8 +353,10 @@ def reynolds_sweep(st: SnapshotStudy, net, stream):
         nn = _cyl_sim(st, st.nx_for(st.short_wake_d), tau, u, stream)
         L.lbm_set_outflow_nn(nn, layers, "tanh", mean, std, scale, st.fallback_drho)
         shorts += [zh, nn]
-    t0 = time.perf_counter()
     batches = [L.lbm_batch_create(longs), L.lbm_batch_create(shorts)]
+    for b in batches:
+        L.lbm_batch_autotune(b, steps=30)
+    t0 = time.perf_counter()
     for b in batches:
         L.lbm_batch_step(b, st.t_trans)
     for b in batches:
