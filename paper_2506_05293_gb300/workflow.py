@@ -165,8 +165,9 @@ def truncated_runs(st: Study, ref, net, f_dev, starts=("rest", "restart")):
     """Zou & He and NN outflow on the truncated domain, from rest (the same
     start as the reference) and restarted from the reference's developed
     state cropped to the truncated domain; then Zou & He from rest on the
-    longer domains of zh_wakes_d.  Errors are relative to ref; ms_per_step
-    is the wall time of the run divided by its steps."""
+    longer domains of zh_wakes_d.  Every lattice is autotuned first.  Errors
+    are relative to ref; ms_per_step is the wall time of the stepping
+    (creation and tuning excluded) divided by its steps."""
     layers, mean, std, scale = net
     out = {}
 
