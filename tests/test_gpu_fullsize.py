@@ -1,0 +1,112 @@
+"""Parity at the benchmark's full sizes and in its launch configuration: the
+12-lattice truncation sweep (6,963,200 nodes, FP32, one batch, strips of 16
+rows on the staged kernel with one block per strip) and the 8192 x 4096
+cylinder.  The GPU state after some steps is exported; one more GPU step is
+compared with one oracle step from that same state -- every node of the sweep,
+and for the large lattice windows around the inlet, the cylinder and the
+outflow (an interior node's step depends only on its neighbours, so a window's
+inner columns are exact)."""
+import numpy as np
+import pytest
+
+from oracle import lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import bench
+    import paper_2506_05293_gb300 as pkg
+    return pkg, bench, torch
+
+
+def _oracle_step(m, kind, tau, f, t):
+    ny, nx = kind.shape
+    o = lbm.Solver(lbm.Config(nx=nx, ny=ny, tau=tau, collision=m["collision"], u_in=m["U"]), kind)
+    o.f = f.copy()
+    o.t = t
+    o.step(1)
+    return o.f, o.force_series()[-1]
+
+
+def test_sweep_batch_one_step_matches_oracle(env):
+    L, bench, torch = env
+    wl = "cylinder_sweep_D40"
+    stream = torch.cuda.Stream()
+    sims, kinds, inits = bench._make_members(L, wl, "fp32", stream.cuda_stream)
+    for s, kind, init in zip(sims, kinds, inits):
+        L.lbm_set_geometry(s, kind)
+        L.lbm_init_equilibrium(s, *init)
+    batch = L.lbm_batch_create(sims)
+    L.lbm_batch_set_tiling(batch, 16, 3)
+    t0 = 20
+    L.lbm_batch_step(batch, t0)
+    L.lbm_batch_sync(batch)
+    before = [L.lbm_get_populations(s) for s in sims]
+    for s in sims:
+        L.lbm_forces(s)                               # drop the first t0 forces
+    L.lbm_batch_step(batch, 1)
+    L.lbm_batch_sync(batch)
+    assert sum(m["nx"] * m["ny"] for m in bench.WORKLOADS[wl]) == 6963200
+    for m, s, kind, f0 in zip(bench.WORKLOADS[wl], sims, kinds, before):
+        _, tau, _ = bench.member_geometry(m)
+        want, F = _oracle_step(m, kind, tau, f0, t0)
+        got = L.lbm_get_populations(s)
+        fl = kind == 0
+        assert np.abs(got - want)[:, fl].max() < 2e-6, bench.member_label(m)
+        fx, fy = L.lbm_forces(s)
+        assert len(fx) == 1
+        assert np.abs(np.array([fx[0], fy[0]]) - F).max() <= 1e-4 * np.abs(F).max() + 1e-9
+    L.lbm_batch_destroy(batch)
+    for s in sims:
+        L.lbm_destroy(s)
+
+
+def test_large_lattice_windows_match_oracle(env):
+    L, bench, torch = env
+    wl = "cylinder_D160_8192x4096"
+    (m,) = bench.WORKLOADS[wl]
+    kind, tau, init = bench.member_geometry(m)
+    ny, nx = kind.shape
+    stream = torch.cuda.Stream()
+    (s,), _, _ = bench._make_members(L, wl, "fp32", stream.cuda_stream)
+    L.lbm_set_geometry(s, kind)
+    L.lbm_init_equilibrium(s, *init)
+    L.lbm_set_tiling(s, 16, 3)
+    t0 = 10
+    L.lbm_step(s, t0)
+    solid_x = np.nonzero(kind.any(axis=0))[0]
+    xc = int((solid_x.min() + solid_x.max()) // 2)
+    w = 256
+    windows = [(0, w), (xc - w // 2, xc + w // 2), (nx - w, nx)]
+
+    def grab():
+        out = []
+        for x0, x1 in windows:
+            buf = torch.empty((9, ny, x1 - x0), dtype=torch.float64, device="cuda")
+            L.lbm_copy_columns(s, x0, x1 - x0, buf)
+            L.lbm_sync(s)
+            out.append(buf.cpu().numpy())
+        return out
+
+    before = grab()
+    L.lbm_step(s, 1)
+    after = grab()
+    for (x0, x1), f0, got in zip(windows, before, after):
+        o = lbm.Solver(lbm.Config(nx=x1 - x0, ny=ny, tau=tau, collision=m["collision"],
+                                  u_in=m["U"]), kind[:, x0:x1])
+        o.f = f0.copy()
+        o.t = t0
+        o.step(1)
+        # inner columns: the window's artificial edges (treated as inlet / outflow
+        # by the oracle) are excluded unless they are the lattice's own
+        lo = 0 if x0 == 0 else 2
+        hi = (x1 - x0) if x1 == nx else (x1 - x0) - 2
+        fl = kind[:, x0:x1][:, lo:hi] == 0
+        err = np.abs(got[:, :, lo:hi] - o.f[:, :, lo:hi])[:, fl].max()
+        assert err < 2e-6, (x0, x1, err)
+    L.lbm_destroy(s)
