@@ -469,7 +469,7 @@ def run_ours(args):
         rows, variant = args.rows, args.variant          # fixed tiling (profiling)
         batch.set_tiling(rows, variant)
     else:
-        rows, variant, _ = batch.autotune(30, flush_bytes)
+        rows, variant, _ = batch.autotune(100, flush_bytes)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda") if flush_mode else None
 
     with torch.cuda.stream(stream):
