@@ -11,9 +11,6 @@ Measured on GB300 (FP32, BGK; errors relative to the long run):
 The network's lift carries high-frequency acoustic oscillations, so its C_L
 RMS error is larger than Zou & He's; the test asserts only the gains and
 records the rest."""
-import json
-import os
-
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -31,10 +28,6 @@ def test_trained_network_beats_zou_he_on_the_truncated_domain(L):
     from paper_2506_05293_gb300 import workflow
     st = workflow.Study(zh_wakes_d=())
     res = workflow.run_study(st)
-    out = os.path.join(os.path.dirname(__file__), "..", "gpurun_out")
-    if os.path.isdir(out):
-        with open(os.path.join(out, "nn_gain_study.json"), "w") as fh:
-            json.dump(res, fh, indent=1)
     ref, runs, tr = res["reference"], res["runs"], res["training"]
     # the reference sheds vortices (Re = 100: St near 0.17)
     assert 0.15 < ref["st"] < 0.19 and ref["cl_rms"] > 0.1

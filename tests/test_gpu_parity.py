@@ -1,6 +1,6 @@
 """Parity of the CUDA path with the FP64 oracle, node by node, through the C ABI.
 
-Tolerances (derived in DESIGN.md, "Tolerances"):
+Tolerances (from the rounding of one FP32 step, accumulated over the run):
   FP64 storage:   populations and fields within 1e-12 absolute, forces within
                   1e-10 of the largest force.
   FP32 storage:   rho within 1e-5 relative at every fluid node; u within 1e-5
