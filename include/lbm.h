@@ -394,15 +394,21 @@ lbm_status lbm_device_state(lbm_sim* sim, void** base, int64_t* pitch, int64_t* 
  * fixed share of the strips through its ring; 5 = the staged kernel on a
  * resident-sized grid whose blocks take strips from a global counter (dynamic
  * balance; the counter is reset by the last block, so launches of one sim or
- * batch must not overlap).  Staged variants need rows >= 2.
+ * batch must not overlap); 6 = variant 3 ordered by per-strip completion
+ * flags instead of whole launches: a strip's step waits only for the 3 x 3
+ * strips around it to finish the previous step, so the next step's blocks
+ * fill the GPU while one step drains (waits give up after 2 s and latch
+ * LBM_ERR_TIMEOUT; with the NN or characteristic outflow, and inside a
+ * caller's stream capture, it runs as variant 3).  Staged variants need
+ * rows >= 2.
  * Populations do not depend on the tiling; the FP64 force sum may differ in
  * its last bits (partial sums change order). */
 lbm_status lbm_set_tiling(lbm_sim* sim, int32_t rows, int32_t variant);
 lbm_status lbm_get_tiling(lbm_sim* sim, int32_t* rows, int32_t* variant);
 
 /* Autotuner: time `steps` (1..10000) steps of every candidate tiling (rows 2,
- * 4, 8, 12, 16, 20, 24, 32, 40, 48, 64 x the six variants) with CUDA events on
- * the sim's stream, back to back as a run executes them, and keep the fastest;
+ * 4, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128 x the seven variants) with
+ * CUDA events on the sim's stream, back to back as a run executes them, and keep the fastest;
  * *best_ms (nullable) gets its mean step time.  With flush_bytes > 0 a scratch
  * buffer of that size is written before each step, which is then timed alone,
  * so every step starts from a cold L2.  The populations, step

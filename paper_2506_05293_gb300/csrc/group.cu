@@ -248,6 +248,10 @@ void build_table(Group& g) {
                          cudaMemcpyHostToDevice, g.stream), "strip table copy");
     }
   }
+  // dataflow between launches: one block per strip, no boundary blocks
+  g.flow = step_variant_dataflow(g.variant) && !g.aa && g.nn_blocks == 0 &&
+           strip_total <= g.done_cap;
+  g.flow_t = -1;
   g.use_strip_force = !force.empty();
   if (g.use_strip_force) {
     if ((int)force.size() > g.force_cap) {
@@ -308,7 +312,23 @@ StepParams params(const Group& g, int q) {
   p.strip_order = g.use_strip_force ? g.d_strip_order : nullptr;
   p.dyn_strips = 0;
   for (const lbm_sim* s : g.sims) p.dyn_strips += step_strips(s->nx, s->ny, g.rows);
+  const bool flow = g.flow && !g.capturing;
+  p.strip_done = flow ? g.d_strip_done : nullptr;
+  p.reduced = flow ? g.d_reduced : nullptr;
   return p;
+}
+
+// Dataflow variant: before a launch of step t from the host, make the flags
+// say "steps < t completed" unless the last launch left them so.  The reset
+// is an ordinary launch, so it runs after all earlier work of the stream.
+void prepare_flow(Group& g, int64_t t) {
+  if (!g.flow || g.capturing || g.flow_t == t) return;
+  // forces of step t-1 still pending: its partials are reduced by the next launch
+  const int64_t r = g.pending ? t - 1 : t;
+  launch_dataflow_reset(g.d_strip_done, g.done_cap, t, g.d_reduced, (int)g.sims.size(), r,
+                        g.stream);
+  ck(cudaGetLastError(), "dataflow reset launch");
+  g.flow_t = t;
 }
 
 // One step launch with source buffer index q.  graph_k < 0: a direct launch
@@ -324,6 +344,10 @@ void enqueue(Group& g, int q, int64_t t, int graph_k, bool reduce_prev) {
     p.t_offset = graph_k;
   }
   p.reduce_prev = reduce_prev ? 1 : 0;
+  if (graph_k < 0) {
+    prepare_flow(g, t);
+    g.flow_t = g.flow && !g.capturing ? t + 1 : -1;
+  }
   if (g.aa) launch_aa(g.prec, g.coll_mode, p, g.variant, g.blocks, g.stream);
   else launch_step(g.prec, g.coll_mode, p, g.variant, g.blocks, g.stream);
   ck(cudaGetLastError(), "step launch");
@@ -455,6 +479,11 @@ void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single) {
     g.owned.push_back(p);
     return p;
   };
+  g.d_strip_done = (int64_t*)alloc(sizeof(int64_t) * (size_t)strips1);
+  g.d_reduced = (int64_t*)alloc(sizeof(int64_t) * sims.size());
+  g.done_cap = strips1;
+  g.flow = false;
+  g.flow_t = -1;
   g.d_members = (Member*)alloc(sizeof(Member) * sims.size());
   g.d_strip_member = sims.size() > 1 ? (int32_t*)alloc(sizeof(int32_t) * (size_t)strips1) : nullptr;
   g.partials = (double*)alloc(sizeof(double) * 4 * (size_t)g.partial_stride);
@@ -505,7 +534,10 @@ void group_step(Group& g, int64_t n) {
       g.pending = false;
     }
   for (lbm_sim* s : g.sims)
-    if (s->last_group != &g) g.pending = false;
+    if (s->last_group != &g) {
+      g.pending = false;
+      g.flow_t = -1;   // another group's launch came last: reset (and order) the flags
+    }
   if (table_stale(g)) {
     group_finalize(g);
     build_table(g);
@@ -513,6 +545,9 @@ void group_step(Group& g, int64_t n) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   ck(cudaStreamIsCapturing(g.stream, &cap), "capture query");
   const bool use_graphs = cap == cudaStreamCaptureStatusNone;
+  // a caller's capture may replay the same step indices: no dataflow flags there
+  g.capturing = !use_graphs;
+  if (g.capturing) g.flow_t = -1;
   while (n > 0) {
     const int q = g.sims[0]->cur;
     const int64_t t = g.sims[0]->t_host;
@@ -526,7 +561,9 @@ void group_step(Group& g, int64_t n) {
       group_finalize(g);
       launch_set_t(g.t_base, t, g.stream);
       ck(cudaGetLastError(), "set_t launch");
+      prepare_flow(g, t);
       ck(cudaGraphLaunch(ex, g.stream), "graph launch");
+      if (g.flow) g.flow_t = t + len;
       advance_members(g, len);
       n -= len;
     } else {
@@ -536,6 +573,7 @@ void group_step(Group& g, int64_t n) {
     }
     g.pending = true;
   }
+  g.capturing = false;
 }
 
 void group_set_tiling(Group& g, int rows, int variant) {
@@ -602,7 +640,7 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
       ck(cudaStreamSynchronize(g.stream), "sync");
       g.pending = false;
     };
-    const int rows_c[] = {2, 4, 8, 12, 16, 20, 24, 32, 40, 48, 64};
+    const int rows_c[] = {2, 4, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128};
     float best = 1e30f;
     int best_rows = g.rows, best_var = g.variant;
     for (int v = 0; v < step_variants(); ++v) {

@@ -86,6 +86,10 @@ struct StepParams {
   int32_t dyn_strips;            // variant 5: strips of the whole table
   int32_t nn_blocks;             // boundary blocks (the first blocks of the grid)
   const int32_t* nn_block_member;  // member of each boundary block (multi-member)
+  int64_t* strip_done;           // variant 6: per strip of the table, the number of steps it
+                                 // has completed; null: wait for the whole previous launch
+  int64_t* reduced;              // variant 6: per member, the number of steps whose forces
+                                 // are in its ring (partials of older steps may be reused)
   Member m0;                     // copy of the only member when n_members == 1: the
                                  // kernels then read it from the parameter bank
 };
@@ -117,6 +121,10 @@ int step_ext_blocks(int ny, int variant, int ext_kind);  // boundary blocks of o
 bool step_variant_is_bulk(int variant);
 bool step_variant_streams(int variant);   // staged variant with a fixed share per block
 bool step_variant_dynamic(int variant);   // staged variant taking strips from a counter
+bool step_variant_dataflow(int variant);  // staged variant ordered by per-strip completion
+// every strip of the table has completed steps < t; the forces of steps < r are reduced
+void launch_dataflow_reset(int64_t* strip_done, int n_strips, int64_t t, int64_t* reduced,
+                           int n_members, int64_t r, cudaStream_t s);
 int step_variants();
 // resident blocks per GPU (occupancy x SMs) of a variant; coll 2 = per member
 int step_max_blocks(int prec, int coll, int variant);
@@ -245,6 +253,13 @@ struct Group {
   int aa_max_blocks[3] = {0, 0, 0};   // resident blocks of the in-place kernel per variant
   std::vector<uint64_t> built_versions;   // member versions the table was built from
   bool pending = false;          // forces of the last launched step not yet in the rings
+  // variant 6 (dataflow between consecutive step launches)
+  int64_t* d_strip_done = nullptr;   // per strip: steps completed
+  int64_t* d_reduced = nullptr;      // per member: steps whose forces are reduced
+  int done_cap = 0;                  // entries of d_strip_done
+  bool flow = false;                 // the current table runs the dataflow variant
+  bool capturing = false;            // steps enqueued into a caller's stream capture
+  int64_t flow_t = -1;               // the flags hold "steps < flow_t completed" (-1: unknown)
   int max_blocks_v[8] = {0};
   std::map<int64_t, cudaGraphExec_t> graphs;   // chunk graphs keyed by length and parity
   std::vector<void*> owned;      // allocations owned by a batch group

@@ -35,6 +35,14 @@ namespace lbm {
 
 __global__ void finalize_force_kernel(const StepParams p, int64_t tt) {
   reduce_force(p, blockIdx.x, tt);
+  publish_reduced(p, blockIdx.x, tt);
+}
+
+__global__ void dataflow_reset_kernel(int64_t* strip_done, int n_strips, int64_t t,
+                                      int64_t* reduced, int n_members, int64_t r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_strips) strip_done[i] = t;
+  if (i < n_members) reduced[i] = r;
 }
 
 __global__ void set_t_kernel(int64_t* t_base, int64_t value) { *t_base = value; }
@@ -45,6 +53,13 @@ void launch_finalize_force(const StepParams& p, int64_t tt, cudaStream_t s) {
 
 void launch_set_t(int64_t* t_base, int64_t value, cudaStream_t s) {
   set_t_kernel<<<1, 1, 0, s>>>(t_base, value);
+}
+
+void launch_dataflow_reset(int64_t* strip_done, int n_strips, int64_t t, int64_t* reduced,
+                           int n_members, int64_t r, cudaStream_t s) {
+  const int n = n_strips > n_members ? n_strips : n_members;
+  dataflow_reset_kernel<<<(n + 255) / 256, 256, 0, s>>>(strip_done, n_strips, t, reduced,
+                                                         n_members, r);
 }
 
 size_t step_bulk_smem(int prec, int stages) {
@@ -68,6 +83,7 @@ int step_ext_blocks(int ny, int variant, int ext_kind) {
 bool step_variant_is_bulk(int variant) { return variant >= 3; }
 bool step_variant_streams(int variant) { return variant == 4; }
 bool step_variant_dynamic(int variant) { return variant == 5; }
+bool step_variant_dataflow(int variant) { return variant == 6; }
 
 int step_variants() { return kVariants; }
 

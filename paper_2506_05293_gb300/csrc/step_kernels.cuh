@@ -100,6 +100,96 @@ __device__ __forceinline__ int64_t step_index(const StepParams& p) {
   return p.t_base ? *p.t_base + p.t_offset : p.t;
 }
 
+// ---- dataflow between consecutive step launches (variant 6) ------------------
+// A strip's step t reads the populations that step t-1 wrote in the 3 x 3
+// strips around it (pull halo of one node, both axes periodic at worst) and
+// overwrites the buffer that those strips read in step t-1.  So instead of
+// waiting for the whole previous launch (griddepcontrol.wait) a block waits
+// until those nine strips have completed step t-1, and the next launch's
+// blocks fill the SMs while this one drains.  Every block of a launch starts
+// before any block of the next one does (a dependent launch begins once all
+// blocks of its predecessor have triggered it, which they do on entry), so a
+// block only ever waits for blocks that are already running.  Flags count
+// completed steps and are published with release/acquire at GPU scope; waits
+// are bounded in time and latch DEV_TIMEOUT when they give up.
+__device__ __forceinline__ int64_t ld_acquire(const int64_t* ptr) {
+  int64_t v;
+  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(ptr) : "memory");
+  return v;
+}
+__device__ __forceinline__ int64_t ld_relaxed(const int64_t* ptr) {
+  int64_t v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(ptr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int64_t* ptr, int64_t v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(ptr), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+}
+
+constexpr uint64_t kFlagWaitNs = 2000000000ull;   // a flag wait gives up after 2 s
+
+// Bounded wait until *ptr >= v; false if it gave up.
+__device__ inline bool wait_at_least(const int64_t* ptr, int64_t v) {
+  if (ld_acquire(ptr) >= v) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t k = 0; k < (1u << 24); ++k) {
+    __nanosleep(200);
+    if (ld_acquire(ptr) >= v) return true;
+    if (global_ns() - t0 > kFlagWaitNs) return false;
+  }
+  return false;
+}
+
+// Local strip ls of member m: wait until its 3 x 3 neighbourhood (periodic
+// in both axes: the edge columns read the opposite edge) has completed t steps.
+// The nine flags are read with relaxed loads issued together (one round trip
+// instead of nine serialised acquires); the fence after the last poll makes
+// the whole wait an acquire of every flag it saw.
+__device__ inline bool wait_strip_neighbours(const StepParams& p, const Member& m, int ls,
+                                             int64_t t) {
+  const int tiles = m.tiles_x;
+  const int nrow = (m.ny + p.rows - 1) / p.rows;
+  const int r0 = ls / tiles, c0 = ls % tiles;
+  const int64_t* f[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    const int r = (r0 + j / 3 - 1 + nrow) % nrow;
+    const int c = (c0 + j % 3 - 1 + tiles) % tiles;
+    f[j] = p.strip_done + m.strip_first + r * tiles + c;
+  }
+  uint64_t t0 = 0;
+  for (uint32_t k = 0; k < (1u << 24); ++k) {
+    int64_t v[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) v[j] = ld_relaxed(f[j]);
+    bool all = true;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) all &= v[j] >= t;
+    if (all) {
+      __threadfence();
+      return true;
+    }
+    if (k == 0) t0 = global_ns();
+    else if (global_ns() - t0 > kFlagWaitNs) break;
+    __nanosleep(200);
+  }
+  __threadfence();
+  return false;
+}
+
+// after a reduction of member k's forces through step index tt
+__device__ __forceinline__ void publish_reduced(const StepParams& p, int k, int64_t tt) {
+  if (p.reduced && threadIdx.x == 0) {
+    __threadfence();
+    st_release(p.reduced + k, tt + 1);
+  }
+}
+
 // Fixed-order sum of member k's block partials of step tt into its force ring
 // (one block of 128 threads).
 __device__ inline void reduce_force(const StepParams& p, int k, int64_t tt) {
@@ -140,7 +230,7 @@ __device__ __forceinline__ void solid_node(const S* __restrict__ A, S* __restric
     for (int i = 1; i < 9; ++i) {
       if ((lk >> (i - 1)) & 1u) {
         // f_i arriving now + f_ibar that bounce-back stored here last step
-        const R v = h[i] + to_r<R>(ldg(A + opp(i) * m.plane + o)) + R(2) * wgt<R>(i);
+        const R v = h[i] + to_r<R>(__ldcg(A + opp(i) * m.plane + o)) + R(2) * wgt<R>(i);
         sx += R(cx(i)) * v;
         sy += R(cy(i)) * v;
       }
@@ -697,7 +787,7 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * Lay::STAGE_BYTES);
   uint64_t* empty = full + NS;
   __shared__ int s_abort;
-  const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
+  const S* A = static_cast<const S*>(m.buf[p.q]);
   S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
   const int plane = m.plane, pitch = m.pitch;
   const int nx = m.nx, ny = m.ny, tiles_x = m.tiles_x, rows = p.rows;
@@ -712,11 +802,18 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  const int64_t t = step_index(p);
+  const bool flow = p.strip_done != nullptr;   // one strip per block (variant 6)
+  if (p.strip_done && threadIdx.x == kConsumerWarps * 32) {
+    // the producer lane: wait for the strips around this one to complete step
+    // t-1; the fence orders that acquire before its bulk copies (async proxy)
+    if (!wait_strip_neighbours(p, m, lb, t)) atomicOr(m.status, DEV_TIMEOUT);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
   __syncthreads();
   // set-up done: wait for the previous step to complete before touching the
   // populations (it may still be reading the buffer this step writes)
-  pdl_wait();
-  const int64_t t = step_index(p);
+  if (!flow) pdl_wait();
 
   // strip geometry
   struct Strip {
@@ -806,6 +903,8 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
           // periodic wrap of the x +- 1 neighbours at the lattice edges
           const int ym = y == 0 ? ny - 1 : y - 1;
           const int yp = y == ny - 1 ? 0 : y + 1;
+          // (A is not __restrict__: these plain loads must not take the
+          // non-coherent path, the previous launch may still be writing A)
           if (x == 0) {
             h[1] = to_r<R>(A[1 * plane + y * pitch + nx - 1]);
             h[5] = to_r<R>(A[5 * plane + ym * pitch + nx - 1]);
@@ -848,7 +947,24 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
   // (recomputed here rather than kept live through the loop)
   const int bb = (int)blockIdx.x - p.nn_blocks - p.n_members;
   const int sgb = p.strip_order ? p.strip_order[bb] : bb;
-  write_partial(p, t, p.strip_force ? p.strip_force[sgb] : sgb, fx, fy, touched, bad, m.status);
+  const int slot = p.strip_force ? p.strip_force[sgb] : sgb;
+  // dataflow (one strip per block: sgb is the strip's index in the table):
+  // the partial slot of step t last held step t-2's partials; they must be
+  // reduced (by a block of launch t-1) before they are overwritten
+  if (p.strip_done && slot >= 0 && threadIdx.x == 0 &&
+      !wait_at_least(p.reduced + (p.n_members == 1 ? 0 : p.strip_member[sgb]), t - 1))
+    atomicOr(m.status, DEV_TIMEOUT);
+  write_partial(p, t, slot, fx, fy, touched, bad, m.status);
+  if (p.strip_done) {
+    // every thread's stores of this strip (ordered with the bulk copies of
+    // the next step that read them), then its completion of step t
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(p.strip_done + sgb, t + 1);
+    }
+  }
 }
 
 // Persistent staged kernel with dynamic strip assignment (variant 5): a
@@ -1072,7 +1188,10 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
   if ((int)blockIdx.x < p.nn_blocks + p.n_members) {
     pdl_wait();
     const int64_t t = step_index(p);
-    if (p.reduce_prev && t >= 1) reduce_force(p, (int)blockIdx.x - p.nn_blocks, t - 1);
+    if (p.reduce_prev && t >= 1) {
+      reduce_force(p, (int)blockIdx.x - p.nn_blocks, t - 1);
+      publish_reduced(p, (int)blockIdx.x - p.nn_blocks, t - 1);
+    }
     return;
   }
   const int b = (int)blockIdx.x - p.nn_blocks - p.n_members;   // stream-and-collide block
@@ -1110,8 +1229,10 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
 // warp-specialised staged kernel (4-slot ring), one block per strip.
 // Variant 4: the same on a resident-sized grid, each block streaming a fixed
 // share of the strips through its ring.  Variant 5: the resident-sized grid
-// taking strips from a global counter (dynamic balance).
-constexpr int kVariants = 6;
+// taking strips from a global counter (dynamic balance).  Variant 6: variant 3
+// ordered by per-strip completion flags instead of whole launches (dataflow
+// between consecutive steps; launches with boundary blocks fall back to 3).
+constexpr int kVariants = 7;
 constexpr int kBulkSlots = 4;
 
 template <typename S>

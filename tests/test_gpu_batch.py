@@ -49,7 +49,8 @@ def _make(L, precision, stream=None):
     return sims, setups
 
 
-@pytest.mark.parametrize("tiling", [(8, 1), (4, 3), (2, 0), (16, 4), (4, 5), (2, 5)])
+@pytest.mark.parametrize("tiling", [(8, 1), (4, 3), (2, 0), (16, 4), (4, 5), (2, 5), (4, 6),
+                                    (2, 6)])
 def test_batch_matches_oracle_fp64(L, tiling):
     import torch
     stream = torch.cuda.Stream()

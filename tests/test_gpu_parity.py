@@ -294,7 +294,7 @@ def test_every_tiling_gives_the_same_populations(L, precision):
     kw = dict(tau=0.58, u_in=0.04, v_pert_amp=1e-3, seed=2)
     ref = None
     for rows, variant in [(8, 1), (1, 0), (3, 2), (2, 3), (5, 3), (16, 4), (64, 4), (7, 4), (4, 5),
-                          (9, 5), (100, 5)]:
+                          (9, 5), (100, 5), (2, 6), (5, 6), (16, 6), (100, 6)]:
         cfg = L.lbm_config_default(nx=nx, ny=ny, precision=precision, **kw)
         sim = L.lbm_create(cfg)
         L.lbm_set_tiling(sim, rows, variant)
@@ -318,14 +318,15 @@ def test_every_tiling_gives_the_same_populations(L, precision):
         assert np.allclose(fy, ref[2], rtol=0, atol=1e-12 * np.abs(ref[1]).max())
 
 
-def test_periodic_x_with_staged_kernel(L):
-    """x-periodic box through the staged variant: edge columns wrap."""
+@pytest.mark.parametrize("variant", [3, 6])
+def test_periodic_x_with_staged_kernel(L, variant):
+    """x-periodic box through the staged variants: edge columns wrap."""
     nx, ny = 200, 64
     kind = cylinder_mask(nx, ny, 60.5, 30.1, 16)
     init = random_smooth_state(nx, ny, seed=4)
     cfg = L.lbm_config_default(nx=nx, ny=ny, tau=0.7, precision="fp64", x_periodic=1)
     sim = L.lbm_create(cfg)
-    L.lbm_set_tiling(sim, 4, 3)
+    L.lbm_set_tiling(sim, 4, variant)
     L.lbm_set_geometry(sim, kind)
     L.lbm_init_equilibrium(sim, *init)
     L.lbm_step(sim, 20)
