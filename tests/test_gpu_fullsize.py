@@ -1,7 +1,8 @@
 """Parity at the benchmark's full sizes and in its launch configuration: the
-12-lattice truncation sweep (6,963,200 nodes, FP32, one batch, strips of 16
-rows on the staged kernel with one block per strip) and the 8192 x 4096
-cylinder.  The GPU state after some steps is exported; one more GPU step is
+12-lattice truncation sweep (6,963,200 nodes, FP32, one batch, strips of 40
+rows on the staged kernel with one block per strip, in the dataflow order)
+and the 8192 x 4096 cylinder (strips of 64 rows, dataflow order).  The GPU
+state after some steps is exported; one more GPU step is
 compared with one oracle step from that same state -- every node of the sweep,
 and for the large lattice windows around the inlet, the cylinder and the
 outflow (an interior node's step depends only on its neighbours, so a window's
@@ -42,7 +43,7 @@ def test_sweep_batch_one_step_matches_oracle(env):
         L.lbm_set_geometry(s, kind)
         L.lbm_init_equilibrium(s, *init)
     batch = L.lbm_batch_create(sims)
-    L.lbm_batch_set_tiling(batch, 16, 3)
+    L.lbm_batch_set_tiling(batch, 40, 6)
     t0 = 20
     L.lbm_batch_step(batch, t0)
     L.lbm_batch_sync(batch)
@@ -76,7 +77,7 @@ def test_large_lattice_windows_match_oracle(env):
     (s,), _, _ = bench._make_members(L, wl, "fp32", stream.cuda_stream)
     L.lbm_set_geometry(s, kind)
     L.lbm_init_equilibrium(s, *init)
-    L.lbm_set_tiling(s, 16, 3)
+    L.lbm_set_tiling(s, 64, 6)
     t0 = 10
     L.lbm_step(s, t0)
     solid_x = np.nonzero(kind.any(axis=0))[0]
