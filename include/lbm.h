@@ -398,9 +398,9 @@ lbm_status lbm_device_state(lbm_sim* sim, void** base, int64_t* pitch, int64_t* 
  * flags instead of whole launches: a strip's step waits only for the 3 x 3
  * strips around it to finish the previous step, so the next step's blocks
  * fill the GPU while one step drains (waits give up after 2 s and latch
- * LBM_ERR_TIMEOUT; with the NN or characteristic outflow, and inside a
- * caller's stream capture, it runs as variant 3).  Staged variants need
- * rows >= 2.
+ * LBM_ERR_TIMEOUT; the east boundary blocks of the NN and characteristic
+ * outflows take part with flags of their own; inside a caller's stream
+ * capture it runs as variant 3).  Staged variants need rows >= 2.
  * Populations do not depend on the tiling; the FP64 force sum may differ in
  * its last bits (partial sums change order). */
 lbm_status lbm_set_tiling(lbm_sim* sim, int32_t rows, int32_t variant);

@@ -248,9 +248,9 @@ void build_table(Group& g) {
                          cudaMemcpyHostToDevice, g.stream), "strip table copy");
     }
   }
-  // dataflow between launches: one block per strip, no boundary blocks
-  g.flow = step_variant_dataflow(g.variant) && !g.aa && g.nn_blocks == 0 &&
-           strip_total <= g.done_cap;
+  // dataflow between launches: one block per strip (and per boundary block)
+  g.flow = step_variant_dataflow(g.variant) && !g.aa && strip_total <= g.done_cap &&
+           g.nn_blocks <= g.done_cap;
   g.flow_t = -1;
   g.use_strip_force = !force.empty();
   if (g.use_strip_force) {
@@ -315,6 +315,7 @@ StepParams params(const Group& g, int q) {
   const bool flow = g.flow && !g.capturing;
   p.strip_done = flow ? g.d_strip_done : nullptr;
   p.reduced = flow ? g.d_reduced : nullptr;
+  p.ext_flags = g.done_cap;
   return p;
 }
 
@@ -325,7 +326,7 @@ void prepare_flow(Group& g, int64_t t) {
   if (!g.flow || g.capturing || g.flow_t == t) return;
   // forces of step t-1 still pending: its partials are reduced by the next launch
   const int64_t r = g.pending ? t - 1 : t;
-  launch_dataflow_reset(g.d_strip_done, g.done_cap, t, g.d_reduced, (int)g.sims.size(), r,
+  launch_dataflow_reset(g.d_strip_done, 2 * g.done_cap, t, g.d_reduced, (int)g.sims.size(), r,
                         g.stream);
   ck(cudaGetLastError(), "dataflow reset launch");
   g.flow_t = t;
@@ -479,7 +480,8 @@ void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single) {
     g.owned.push_back(p);
     return p;
   };
-  g.d_strip_done = (int64_t*)alloc(sizeof(int64_t) * (size_t)strips1);
+  // strip flags, then boundary-block flags (at most one boundary block per row)
+  g.d_strip_done = (int64_t*)alloc(sizeof(int64_t) * 2 * (size_t)strips1);
   g.d_reduced = (int64_t*)alloc(sizeof(int64_t) * sims.size());
   g.done_cap = strips1;
   g.flow = false;

@@ -90,6 +90,7 @@ struct StepParams {
                                  // has completed; null: wait for the whole previous launch
   int64_t* reduced;              // variant 6: per member, the number of steps whose forces
                                  // are in its ring (partials of older steps may be reused)
+  int32_t ext_flags;             // variant 6: strip_done index of boundary block 0's flag
   Member m0;                     // copy of the only member when n_members == 1: the
                                  // kernels then read it from the parameter bank
 };
@@ -256,7 +257,8 @@ struct Group {
   // variant 6 (dataflow between consecutive step launches)
   int64_t* d_strip_done = nullptr;   // per strip: steps completed
   int64_t* d_reduced = nullptr;      // per member: steps whose forces are reduced
-  int done_cap = 0;                  // entries of d_strip_done
+  int done_cap = 0;                  // strip flags (d_strip_done holds 2 done_cap entries:
+                                     // strips, then boundary blocks)
   bool flow = false;                 // the current table runs the dataflow variant
   bool capturing = false;            // steps enqueued into a caller's stream capture
   int64_t flow_t = -1;               // the flags hold "steps < flow_t completed" (-1: unknown)

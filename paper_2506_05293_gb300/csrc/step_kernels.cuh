@@ -381,7 +381,7 @@ __device__ __forceinline__ R post_stream_h(const S* __restrict__ A, const Member
   int sy = y - cy(k);
   sy = sy < 0 ? sy + m.ny : (sy >= m.ny ? sy - m.ny : sy);
   const int sx = x - cx(k);
-  return to_r<R>(ldg(A + k * m.plane + sy * m.pitch + sx));
+  return to_r<R>(__ldcg(A + k * m.plane + sy * m.pitch + sx));
 }
 
 template <typename S>
@@ -469,15 +469,15 @@ __device__ __noinline__ void nn_block(const StepParams& p, const Member& m, int 
   const int xm = L - 1;
   // pulled populations (those from x = L + 1 are rebuilt below)
   R h[9];
-  h[0] = to_r<R>(ldg(A + 0 * m.plane + rc + L));
-  h[1] = to_r<R>(ldg(A + 1 * m.plane + rc + xm));
-  h[2] = to_r<R>(ldg(A + 2 * m.plane + rm + L));
-  h[3] = to_r<R>(ldg(A + 3 * m.plane + rc));
-  h[4] = to_r<R>(ldg(A + 4 * m.plane + rp + L));
-  h[5] = to_r<R>(ldg(A + 5 * m.plane + rm + xm));
-  h[6] = to_r<R>(ldg(A + 6 * m.plane + rm));
-  h[7] = to_r<R>(ldg(A + 7 * m.plane + rp));
-  h[8] = to_r<R>(ldg(A + 8 * m.plane + rp + xm));
+  h[0] = to_r<R>(__ldcg(A + 0 * m.plane + rc + L));
+  h[1] = to_r<R>(__ldcg(A + 1 * m.plane + rc + xm));
+  h[2] = to_r<R>(__ldcg(A + 2 * m.plane + rm + L));
+  h[3] = to_r<R>(__ldcg(A + 3 * m.plane + rc));
+  h[4] = to_r<R>(__ldcg(A + 4 * m.plane + rp + L));
+  h[5] = to_r<R>(__ldcg(A + 5 * m.plane + rm + xm));
+  h[6] = to_r<R>(__ldcg(A + 6 * m.plane + rm));
+  h[7] = to_r<R>(__ldcg(A + 7 * m.plane + rp));
+  h[8] = to_r<R>(__ldcg(A + 8 * m.plane + rp + xm));
   const R scale = (R)m.nn_out_scale;
   const R s3 = scale * act[n * kNnMaxW + 0];
   const R s6 = scale * act[n * kNnMaxW + 1];
@@ -533,7 +533,7 @@ __device__ __forceinline__ void node_macros(const S* __restrict__ A, const Membe
                                             R& drho, R& u, R& v) {
   R h[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) h[i] = to_r<R>(ldg(A + i * m.plane + y * m.pitch + x));
+  for (int i = 0; i < 9; ++i) h[i] = to_r<R>(__ldcg(A + i * m.plane + y * m.pitch + x));
   R jx, jy;
   moments_shifted(h, drho, jx, jy);
   const R rho = R(1) + drho;
@@ -632,12 +632,12 @@ __device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int
   // post-stream node (the pulls from x = L + 1 are rebuilt below)
   const int rc = y * m.pitch, rmo = ym * m.pitch, rpo = yp * m.pitch;
   R h[9];
-  h[0] = to_r<R>(ldg(A + 0 * m.plane + rc + L));
-  h[1] = to_r<R>(ldg(A + 1 * m.plane + rc + L - 1));
-  h[2] = to_r<R>(ldg(A + 2 * m.plane + rmo + L));
-  h[4] = to_r<R>(ldg(A + 4 * m.plane + rpo + L));
-  h[5] = to_r<R>(ldg(A + 5 * m.plane + rmo + L - 1));
-  h[8] = to_r<R>(ldg(A + 8 * m.plane + rpo + L - 1));
+  h[0] = to_r<R>(__ldcg(A + 0 * m.plane + rc + L));
+  h[1] = to_r<R>(__ldcg(A + 1 * m.plane + rc + L - 1));
+  h[2] = to_r<R>(__ldcg(A + 2 * m.plane + rmo + L));
+  h[4] = to_r<R>(__ldcg(A + 4 * m.plane + rpo + L));
+  h[5] = to_r<R>(__ldcg(A + 5 * m.plane + rmo + L - 1));
+  h[8] = to_r<R>(__ldcg(A + 8 * m.plane + rpo + L - 1));
   // Zou & He with the prescribed state, then Eq. 28 on f_0
   const R sknown = (h[0] + h[2] + h[4]) + R(2) * (h[1] + h[5] + h[8]);   // rho0 + 2 rho+ - 1
   R heq[9];
@@ -769,6 +769,87 @@ struct BulkLayout {
 };
 
 
+constexpr int kConsumerWarps = 4;
+constexpr int kBulkThreads = 32 * (kConsumerWarps + 1);
+
+// ---- dataflow around the east boundary blocks --------------------------------
+// With the NN or characteristic outflow a launch also holds boundary blocks:
+// block j of a member rebuilds the east fluid nodes of rows [j e, (j+1) e),
+// e = kNnNodes (NN) or the block size (CBC), reading the source columns
+// L-4 .. L of rows y0-2 .. y1+2 (NN features are pulled populations of three
+// columns and rows; the CBC stencil is narrower) and writing column L.  Their
+// flags follow the strips' (p.ext_flags + the block's index in the launch).
+// A boundary block of step t waits for the strips of the east tiles and the
+// boundary blocks of step t-1 that meet its rows +- 2; a strip of an east
+// tile (one that holds a column in L-4 .. L) also waits for the boundary
+// blocks of step t-1 that meet its rows +- 2 (they wrote its column L, and read
+// what it overwrites).
+__device__ __forceinline__ int wrap_row(int y, int ny) {
+  y %= ny;
+  return y < 0 ? y + ny : y;
+}
+
+// Calls fn(s, e) for the wrapped row segments [s, e] covering rows a..b.
+template <typename F>
+__device__ __forceinline__ void row_segments(int a, int b, int ny, F fn) {
+  if (b - a + 1 >= ny) {
+    fn(0, ny - 1);
+    return;
+  }
+  const int s = wrap_row(a, ny), e = wrap_row(b, ny);
+  if (s <= e) {
+    fn(s, e);
+  } else {
+    fn(s, ny - 1);
+    fn(0, e);
+  }
+}
+
+// rows of one boundary block of member m
+__device__ __forceinline__ int ext_rows(const Member& m) {
+  return m.ext_kind == 1 ? kNnNodes : kBulkThreads;
+}
+
+// One poll: have the east-tile strips (if `strips`) and the boundary blocks (if
+// `exts`) of member m whose rows meet a..b completed t steps?
+__device__ inline bool east_ready(const StepParams& p, const Member& m, int a, int b, int64_t t,
+                                 bool strips, bool exts) {
+  bool ok = true;
+  const int L = m.nx - 1;
+  const int c0 = (L >= 4 ? L - 4 : 0) >> 7, c1 = L >> 7;
+  const int per = ext_rows(m);
+  row_segments(a, b, m.ny, [&](int s, int e) {
+    if (exts) {
+      const int64_t* f = p.strip_done + p.ext_flags + m.nn_first;
+#pragma unroll 4
+      for (int j = s / per; j <= e / per; ++j) ok &= ld_relaxed(f + j) >= t;
+    }
+    if (strips) {
+      for (int r = s / p.rows; r <= e / p.rows; ++r)
+        for (int c = c0; c <= c1; ++c)
+          ok &= ld_relaxed(p.strip_done + m.strip_first + r * m.tiles_x + c) >= t;
+    }
+  });
+  return ok;
+}
+
+// Bounded wait for east_ready; the fence after the last poll makes it an acquire.
+__device__ inline bool wait_east(const StepParams& p, const Member& m, int a, int b, int64_t t,
+                                 bool strips, bool exts) {
+  uint64_t t0 = 0;
+  for (uint32_t k = 0; k < (1u << 24); ++k) {
+    if (east_ready(p, m, a, b, t, strips, exts)) {
+      __threadfence();
+      return true;
+    }
+    if (k == 0) t0 = global_ns();
+    else if (global_ns() - t0 > kFlagWaitNs) break;
+    __nanosleep(200);
+  }
+  __threadfence();
+  return false;
+}
+
 // One block streams the rows of its strips (local strips lb, lb + gk, ... of
 // member m) through an NS-slot ring with warp specialisation: warp 4 is the
 // producer -- its lane 0 waits until a slot is released ("empty" barrier,
@@ -776,9 +857,6 @@ struct BulkLayout {
 // cp.async.bulk completing on the slot's "full" barrier -- and warps 0-3 are
 // consumers, each waiting on "full", colliding its 32 columns and releasing
 // the slot.  No block-wide barrier per row: warps run ahead independently.
-constexpr int kConsumerWarps = 4;
-constexpr int kBulkThreads = 32 * (kConsumerWarps + 1);
-
 template <typename S, int COLL, int NS>
 __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, int lb, int gk,
                                          unsigned char* smem) {
@@ -805,9 +883,16 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
   const int64_t t = step_index(p);
   const bool flow = p.strip_done != nullptr;   // one strip per block (variant 6)
   if (p.strip_done && threadIdx.x == kConsumerWarps * 32) {
-    // the producer lane: wait for the strips around this one to complete step
-    // t-1; the fence orders that acquire before its bulk copies (async proxy)
-    if (!wait_strip_neighbours(p, m, lb, t)) atomicOr(m.status, DEV_TIMEOUT);
+    // the producer lane: wait for the strips around this one (and, in an east
+    // tile, the boundary blocks next to it) to complete step t-1; the fence
+    // orders those acquires before its bulk copies (async proxy)
+    bool ok = wait_strip_neighbours(p, m, lb, t);
+    const int c = lb % m.tiles_x, L = m.nx - 1;
+    if (ok && m.ext_kind != 0 && (c << 7) + 127 >= L - 4) {
+      const int y0 = (lb / m.tiles_x) * p.rows;
+      ok = wait_east(p, m, y0 - 2, min(y0 + p.rows, m.ny) + 1, t, false, true);
+    }
+    if (!ok) atomicOr(m.status, DEV_TIMEOUT);
     asm volatile("fence.proxy.async.global;" ::: "memory");
   }
   __syncthreads();
@@ -1179,8 +1264,31 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
   extern __shared__ __align__(128) unsigned char smem[];
   pdl_launch_dependents();
   if (EXT && (int)blockIdx.x < p.nn_blocks) {
-    pdl_wait();
-    ext_dispatch<S>(p, (int)blockIdx.x, smem);
+    const int blk = (int)blockIdx.x;
+    if (p.strip_done) {
+      // dataflow: wait for the east strips and boundary blocks of step t-1
+      // that meet this block's rows +- 2
+      if (threadIdx.x == 0) {
+        const Member& m = p.n_members == 1 ? p.m0 : p.members[p.nn_block_member[blk]];
+        const int y0 = (blk - m.nn_first) * ext_rows(m);
+        if (!wait_east(p, m, y0 - 2, min(y0 + ext_rows(m), m.ny) + 1, step_index(p), true,
+                       true))
+          atomicOr(m.status, DEV_TIMEOUT);
+      }
+      __syncthreads();
+    } else {
+      pdl_wait();
+    }
+    ext_dispatch<S>(p, blk, smem);
+    if (p.strip_done) {
+      // this block's east nodes (read next by bulk copies), then its flag
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(p.strip_done + p.ext_flags + blk, step_index(p) + 1);
+      }
+    }
     return;
   }
   // force-reduction blocks of the previous step come next, ahead of the
@@ -1231,7 +1339,7 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
 // share of the strips through its ring.  Variant 5: the resident-sized grid
 // taking strips from a global counter (dynamic balance).  Variant 6: variant 3
 // ordered by per-strip completion flags instead of whole launches (dataflow
-// between consecutive steps; launches with boundary blocks fall back to 3).
+// between consecutive steps).
 constexpr int kVariants = 7;
 constexpr int kBulkSlots = 4;
 

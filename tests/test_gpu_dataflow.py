@@ -5,12 +5,13 @@ in batches of lattices of different sizes (one 128-column tile, ragged strip
 rows, two strip rows whose neighbours coincide), through graph chunks and
 single launches, across the calls that rewind the step counter (autotuner,
 checkpoint load) or serialise the stream (force reads), with the oracle as
-the FP64 reference."""
+the FP64 reference; and with the east boundary blocks of the network and
+characteristic outflows, whose blocks take part in the same order."""
 import numpy as np
 import pytest
 
-from oracle import lbm
-from synth import add_walls, cylinder_mask, random_smooth_state
+from oracle import lbm, mlp
+from synth import add_walls, cylinder_mask, glorot_mlp, random_smooth_state
 
 pytestmark = pytest.mark.gpu
 
@@ -166,9 +167,70 @@ def test_single_lattice_rewinds(L, tmp_path):
         L.lbm_destroy(x)
 
 
-def test_dataflow_with_boundary_blocks_runs_as_staged(L):
-    """With the characteristic outflow the launch has boundary blocks; variant
-    6 then waits for whole launches, as variant 3 does."""
+def _nn_args(seed):
+    rng = np.random.default_rng(seed)
+    layers = [(np.asarray(W, np.float32).astype(np.float64), np.zeros(W.shape[0]))
+              for W, _ in glorot_mlp([81, 16, 3], seed)]
+    mean = np.asarray(np.tile(lbm.W, 9), np.float32).astype(np.float64)
+    std = np.asarray(rng.uniform(0.005, 0.02, 81), np.float32).astype(np.float64)
+    return layers, "tanh", mean, std, float(np.float32(5e-4)), 0.2
+
+
+# east boundary blocks: characteristic outflow (160-row blocks; two of them),
+# network outflow (8-row blocks, the last one partial; columns L-4 .. L span
+# two tiles), Zou & He, and a 5 x 3 network lattice (one tile, one block)
+EAST = [dict(nx=200, ny=200, out="cbc"), dict(nx=130, ny=67, out="nn"),
+        dict(nx=300, ny=96, out="zouhe"), dict(nx=5, ny=3, out="nn")]
+
+
+def _east_batch(L, precision, rows, variant, stream):
+    sims, made = [], []
+    for i, m in enumerate(EAST):
+        nx, ny = m["nx"], m["ny"]
+        kind = cylinder_mask(nx, ny, nx * 0.3, ny * 0.45, ny * 0.2) if nx > 20 else \
+            np.zeros((ny, nx), np.uint8)
+        rho, ux, uy = random_smooth_state(nx, ny, seed=50 + i, amp_u=0.01, amp_rho=0.003)
+        init = (rho, np.where(kind == 0, 0.04 + ux, 0.0), np.where(kind == 0, uy, 0.0))
+        kw = dict(tau=0.6, collision="mrt" if i % 2 else "bgk", u_in=0.04, v_pert_amp=1e-3,
+                  seed=i)
+        s = L.lbm_create(L.lbm_config_default(nx=nx, ny=ny, precision=precision, stream=stream,
+                                              **kw))
+        L.lbm_set_geometry(s, kind)
+        if m["out"] == "cbc":
+            L.lbm_set_outflow_cbc(s, 0.25, 0.1, 0.1)
+        elif m["out"] == "nn":
+            L.lbm_set_outflow_nn(s, *_nn_args(i))
+        L.lbm_init_equilibrium(s, *init)
+        sims.append(s)
+        made.append((s, kind, init, kw))
+    b = L.lbm_batch_create(sims)
+    L.lbm_batch_set_tiling(b, rows, variant)
+    return b, sims, made
+
+
+@pytest.mark.parametrize("rows", [2, 16, 40])
+def test_boundary_blocks_dataflow_equals_staged_bitwise_fp32(L, rows):
+    import torch
+    stream = torch.cuda.Stream().cuda_stream
+    out = {}
+    for variant in (3, 6):
+        b, sims, _ = _east_batch(L, "fp32", rows, variant, stream)
+        L.lbm_batch_step(b, 70)
+        L.lbm_batch_sync(b)
+        mid = _state(L, sims)
+        for _ in range(3):
+            L.lbm_batch_step(b, 1)
+        L.lbm_batch_step(b, 40)
+        L.lbm_batch_sync(b)
+        out[variant] = (mid, _state(L, sims))
+        _free(L, b, sims)
+    for k in range(len(EAST)):
+        for part in (0, 1):
+            assert np.array_equal(out[3][part][k][0], out[6][part][k][0]), (k, part)
+            assert np.array_equal(out[3][part][k][1], out[6][part][k][1]), (k, part)
+
+
+def test_single_cbc_lattice_dataflow_equals_staged(L):
     nx, ny = 160, 96
     init = random_smooth_state(nx, ny, seed=12, amp_u=0.02, amp_rho=0.004)
     res = {}
@@ -179,6 +241,25 @@ def test_dataflow_with_boundary_blocks_runs_as_staged(L):
         L.lbm_init_equilibrium(s, *init)
         L.lbm_set_tiling(s, 4, variant)
         L.lbm_step(s, 37)
+        L.lbm_sync(s)
         res[variant] = L.lbm_get_populations(s)
         L.lbm_destroy(s)
     assert np.array_equal(res[3], res[6])
+
+
+def test_nn_member_dataflow_matches_oracle_fp64(L):
+    import torch
+    stream = torch.cuda.Stream().cuda_stream
+    b, sims, made = _east_batch(L, "fp64", 8, 6, stream)
+    L.lbm_batch_step(b, 45)
+    L.lbm_batch_sync(b)
+    s, kind, init, kw = made[1]
+    ny, nx = kind.shape
+    layers, act, mean, std, scale, drho = _nn_args(1)
+    net = mlp.MLP(layers, act, mean, std, scale)
+    o = lbm.Solver(lbm.Config(nx=nx, ny=ny, outflow="nn", nn=lbm.NNOutflow(net, drho), **kw),
+                   kind)
+    o.init_equilibrium(*init)
+    o.step(45)
+    assert np.abs(L.lbm_get_populations(s) - o.f)[:, kind == 0].max() < 1e-12
+    _free(L, b, sims)
