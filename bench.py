@@ -639,7 +639,8 @@ def main():
     ap.add_argument("--no-tuner", action="store_true",
                     help="skip the CBC tuner training study (a few seconds)")
     ap.add_argument("--rows", type=int, default=0, help="fixed tiling instead of the autotuner")
-    ap.add_argument("--variant", type=int, default=3)
+    ap.add_argument("--variant", type=int, default=6,
+                    help="kernel variant of the fixed tiling (with --rows; see lbm_set_tiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
