@@ -406,6 +406,15 @@ lbm_status lbm_device_state(lbm_sim* sim, void** base, int64_t* pitch, int64_t* 
 lbm_status lbm_set_tiling(lbm_sim* sim, int32_t rows, int32_t variant);
 lbm_status lbm_get_tiling(lbm_sim* sim, int32_t* rows, int32_t* variant);
 
+/* Test hook for the bounded waits of the dataflow order (variant 6; no
+ * counterpart in the paper).  With hold != 0 the flags that the sim's next
+ * launches start from (after a reset) claim one step fewer than has completed,
+ * so no block's wait can be satisfied: each gives up after 2 s, the blocks
+ * finish their strips anyway, and the step latches LBM_ERR_TIMEOUT, which
+ * lbm_sync reports; the device stays usable.  hold = 0 restores normal resets.
+ * LBM_ERR_STATE unless the sim's own tiling is variant 6. */
+lbm_status lbm_debug_hold_dataflow(lbm_sim* sim, int32_t hold);
+
 /* Autotuner: time `steps` (1..10000) steps of every candidate tiling (rows 2,
  * 4, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128 x the seven variants) with
  * CUDA events on the sim's stream, back to back as a run executes them, and keep the fastest;

@@ -102,6 +102,7 @@ SIGNATURES = {
     "lbm_device_state": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_int64), POINTER(c_int64)]),
     "lbm_set_tiling": (c_int, [c_void_p, c_int32, c_int32]),
     "lbm_get_tiling": (c_int, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
+    "lbm_debug_hold_dataflow": (c_int, [c_void_p, c_int32]),
     "lbm_autotune": (c_int, [c_void_p, c_int32, c_int64, POINTER(c_float)]),
     "lbm_step_noalloc": (c_int, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_int64,
                                  c_int64, c_void_p]),

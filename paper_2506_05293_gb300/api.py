@@ -435,6 +435,11 @@ def lbm_set_tiling(sim, rows, variant):
     _check(_lib.load().lbm_set_tiling(sim.handle, int(rows), int(variant)))
 
 
+def lbm_debug_hold_dataflow(sim, hold):
+    """Test hook: make the dataflow variant's flag waits run out (see lbm.h)."""
+    _check(_lib.load().lbm_debug_hold_dataflow(sim.handle, int(hold)))
+
+
 def lbm_get_tiling(sim):
     r = ctypes.c_int32()
     v = ctypes.c_int32()

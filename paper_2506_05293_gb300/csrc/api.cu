@@ -70,7 +70,8 @@ lbm_status read_status(lbm_sim* s) {
      "status copy");
   ck(cudaStreamSynchronize(s->stream), "stream sync");
   if (st & lbm::DEV_TIMEOUT)
-    return fail(LBM_ERR_TIMEOUT, "a bounded device wait gave up (bulk-copy pipeline)");
+    return fail(LBM_ERR_TIMEOUT,
+                "a bounded device wait gave up (bulk-copy pipeline or dataflow flags)");
   if (st & lbm::DEV_NONFINITE)
     return fail(LBM_ERR_NONFINITE, "non-finite density on the device (the run diverged)");
   return LBM_OK;
@@ -306,6 +307,10 @@ lbm_status upload_net(lbm_sim* s, const lbm_mlp* net, int n_in, int64_t np) {
 }
 
 }  // namespace
+
+namespace lbm {
+void group_hold_flags(Group& g, bool hold);   // group.cu: test hook of the flag waits
+}
 
 extern "C" {
 
@@ -922,6 +927,16 @@ lbm_status lbm_set_tiling(lbm_sim* s, int32_t rows, int32_t variant) {
     return fail(LBM_ERR_UNSUPPORTED, "the in-place (AA) layout runs on variants 0-2");
   LBM_GUARD_BEGIN
   lbm::group_set_tiling(s->own, rows, variant);
+  return LBM_OK;
+  LBM_GUARD_END
+}
+
+lbm_status lbm_debug_hold_dataflow(lbm_sim* s, int32_t hold) {
+  if (lbm_status st = check_sim(s)) return st;
+  if (!lbm::step_variant_dataflow(s->own.variant))
+    return fail(LBM_ERR_STATE, "the sim's tiling is not the dataflow variant (6)");
+  LBM_GUARD_BEGIN
+  lbm::group_hold_flags(s->own, hold != 0);
   return LBM_OK;
   LBM_GUARD_END
 }

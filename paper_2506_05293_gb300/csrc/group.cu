@@ -11,6 +11,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <set>
 #include <vector>
 
 #include "sim.cuh"
@@ -319,6 +321,21 @@ StepParams params(const Group& g, int q) {
   return p;
 }
 
+// Test hook of the bounded flag waits (lbm_debug_hold_dataflow): groups whose
+// flag resets claim one step fewer than has completed.
+std::mutex& held_mutex() {
+  static std::mutex m;
+  return m;
+}
+std::set<const Group*>& held_groups() {
+  static std::set<const Group*> held;
+  return held;
+}
+bool flags_held(const Group& g) {
+  std::lock_guard<std::mutex> lock(held_mutex());
+  return held_groups().count(&g) != 0;
+}
+
 // Dataflow variant: before a launch of step t from the host, make the flags
 // say "steps < t completed" unless the last launch left them so.  The reset
 // is an ordinary launch, so it runs after all earlier work of the stream.
@@ -326,8 +343,9 @@ void prepare_flow(Group& g, int64_t t) {
   if (!g.flow || g.capturing || g.flow_t == t) return;
   // forces of step t-1 still pending: its partials are reduced by the next launch
   const int64_t r = g.pending ? t - 1 : t;
-  launch_dataflow_reset(g.d_strip_done, 2 * g.done_cap, t, g.d_reduced, (int)g.sims.size(), r,
-                        g.stream);
+  const int64_t done = flags_held(g) ? t - 1 : t;
+  launch_dataflow_reset(g.d_strip_done, 2 * g.done_cap, done, g.d_reduced, (int)g.sims.size(),
+                        r, g.stream);
   ck(cudaGetLastError(), "dataflow reset launch");
   g.flow_t = t;
 }
@@ -504,7 +522,17 @@ void group_clear_graphs(Group& g) {
   g.graphs.clear();
 }
 
+void group_hold_flags(Group& g, bool hold) {
+  {
+    std::lock_guard<std::mutex> lock(held_mutex());
+    if (hold) held_groups().insert(&g);
+    else held_groups().erase(&g);
+  }
+  g.flow_t = -1;   // the next launch resets the flags
+}
+
 void group_release(Group& g) {
+  group_hold_flags(g, false);
   group_clear_graphs(g);
   if (g.stream) cudaStreamSynchronize(g.stream);
   const lbm_allocator* a = (!g.sims.empty() && g.sims[0]->have_alloc) ? &g.sims[0]->alloc : nullptr;

@@ -263,3 +263,44 @@ def test_nn_member_dataflow_matches_oracle_fp64(L):
     o.step(45)
     assert np.abs(L.lbm_get_populations(s) - o.f)[:, kind == 0].max() < 1e-12
     _free(L, b, sims)
+
+
+def test_a_flag_that_nothing_sets_times_out(L):
+    """The bounded waits: with the flags held one step back, no block's wait
+    can be satisfied; every wait gives up after 2 s, the step completes, and
+    lbm_sync reports LBM_ERR_TIMEOUT (6).  The device stays usable."""
+    import time
+    nx, ny = 256, 16                  # 2 x 2 strips of 8 rows: every block resident
+    init = random_smooth_state(nx, ny, seed=3, amp_u=0.01, amp_rho=0.003)
+
+    def make():
+        s = L.lbm_create(L.lbm_config_default(nx=nx, ny=ny, tau=0.7, precision="fp32",
+                                              x_periodic=1))
+        L.lbm_set_geometry(s, np.zeros((ny, nx), np.uint8))
+        L.lbm_init_equilibrium(s, *init)
+        L.lbm_set_tiling(s, 8, 6)
+        return s
+
+    other = L.lbm_create(L.lbm_config_default(nx=nx, ny=ny, precision="fp32", x_periodic=1))
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_debug_hold_dataflow(other, 1)            # its tiling is not variant 6
+    assert ei.value.status == 2
+    L.lbm_destroy(other)
+    s = make()
+    L.lbm_debug_hold_dataflow(s, 1)
+    t0 = time.time()
+    L.lbm_step(s, 1)
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_sync(s)
+    assert ei.value.status == 6
+    assert 1.5 < time.time() - t0 < 60
+    L.lbm_destroy(s)
+    # the same device, a new lattice: runs and equals the whole-launch order
+    a, b = make(), make()
+    L.lbm_set_tiling(b, 8, 3)
+    for x in (a, b):
+        L.lbm_step(x, 20)
+        L.lbm_sync(x)
+    assert np.array_equal(L.lbm_get_populations(a), L.lbm_get_populations(b))
+    for x in (a, b):
+        L.lbm_destroy(x)
