@@ -1,0 +1,78 @@
+"""Host logic of the benchmark (CPU): the workloads' sizes and parameters,
+the whole-job rate, the throttle-reason decoding and the lookup of the DRAM
+traffic in the committed ncu summaries."""
+import math
+import os
+import re
+
+import numpy as np
+
+import bench
+
+
+def test_sweep_workload_is_the_truncation_study():
+    ms = bench.WORKLOADS["cylinder_sweep_D40"]
+    assert len(ms) == 12
+    # D = 40, height 16D, wake 4D / 8D / 32D behind the centre at 8D
+    assert sorted({m["nx"] for m in ms}) == [480, 640, 1600]
+    assert {m["ny"] for m in ms} == {640}
+    assert bench.workload_nodes("cylinder_sweep_D40") == 6963200
+    assert sorted({m["Re"] for m in ms}) == [100, 200]
+    assert sorted({m["collision"] for m in ms}) == ["bgk", "mrt"]
+    for m in ms:
+        kind, tau, init = bench.member_geometry(m)
+        assert kind.shape == (640, m["nx"])
+        # tau = 3 nu + 1/2 with nu = U D / Re
+        assert math.isclose(tau, 3 * 0.05 * 40 / m["Re"] + 0.5)
+        # the cylinder: its area and centre (8D, ny/2)
+        solid = kind != 0
+        assert abs(solid.sum() - math.pi * 20 ** 2) < 0.05 * math.pi * 20 ** 2
+        ys, xs = np.nonzero(solid)
+        assert abs(xs.mean() - 320) < 1 and abs(ys.mean() - 320) < 1
+        # started from f_eq(1, (U, 0)) on fluid nodes
+        assert init[0] is None and init[2] is None
+        assert np.all(init[1][~solid] == 0.05) and np.all(init[1][solid] == 0)
+
+
+def test_other_workloads():
+    assert bench.workload_nodes("cylinder_D160_8192x4096") == 8192 * 4096
+    assert bench.workload_nodes("naca0012_4000x1600_aoa4") == 4000 * 1600
+    vs = bench.WORKLOADS["vortex_batch_256"]
+    assert len(vs) == 256
+    assert all(128 <= m["nx"] <= 1024 and 128 <= m["ny"] <= 512 for m in vs)
+    assert bench.workload_nodes("vortex_batch_256") == 49153467
+
+
+def test_job_rate_counts_every_replica_at_the_slowest_time():
+    # 2 replicas x 1e6 nodes x 1000 steps in 2 s: 1 G node updates per second
+    assert math.isclose(bench.job_glups(2, 1_000_000, 1000, 2000.0), 1.0)
+    assert math.isclose(bench.job_glups(1, 1_000_000, 1000, 2000.0), 0.5)
+
+
+def test_clock_reasons_decode():
+    c = bench.ClockSampler(0)
+    c.samples = [(2070, 0x4), (1900, 0x0), (2070, 0x8 | 0x40)]
+    c.max_mhz = 2070
+    s = c.summary()
+    assert s["sm_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
+    empty = bench.ClockSampler(0)
+    assert empty.summary()["reasons"][0].startswith("unsampled")
+
+
+def test_traffic_lookup_follows_the_summary_and_its_source_hash():
+    assert bench.step_kernel_traffic("fp32", "no_such_workload") is None
+    for layout, wl in (("ab", "cylinder_sweep_D40"), ("aa", "cylinder_D160_8192x4096")):
+        tag = "" if layout == "ab" else "_aa"
+        path = os.path.join(bench.ROOT, "profiles", f"step_kernel{tag}_{wl}_fp32.md")
+        txt = open(path).read()
+        sha = re.search(r"source_sha256:\s*([0-9a-f]+)", txt).group(1)
+        value = float(re.search(r"dram_bytes_per_launch:\s*([0-9.e+]+)", txt).group(1))
+        got = bench.step_kernel_traffic("fp32", wl, layout)
+        if sha == bench.kernel_source_hash(layout):
+            assert got == value
+        else:                                  # sources changed since the capture
+            assert got is None
+        # the committed captures show no wasted re-reads: the measured traffic
+        # stays at or below the algorithmic 72 B per node
+        assert value <= 72 * bench.workload_nodes(wl)
