@@ -3,9 +3,9 @@
 // A group owns the device launch table (one Member per sim, strip layout for
 // the current tiling), the force partials, the step index used by captured
 // graphs, the completion flags of the dataflow variant (and the step up to
-// which they are valid), and the CUDA graphs of chunks of steps.  A single lbm_sim is a group
-// of one; lbm_batch is a group of many sims of different sizes and parameters
-// in lockstep.  Every numerical step runs in step.cu.
+// which they are valid), and the CUDA graphs of chunks of steps.  A single
+// lbm_sim is a group of one; lbm_batch is a group of many sims of different
+// sizes and parameters in lockstep.  Every numerical step runs in step.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
