@@ -58,6 +58,8 @@ class Sim:
 
 
 def lbm_config_default(**kw):
+    """Default lbm_config with the given fields set (collision "bgk"/"mrt", precision
+    "fp64"/"fp32"/"fp16dev", layout "ab"/"aa", stream a CUDA stream handle or 0)."""
     cfg = LbmConfig()
     _check(_lib.load().lbm_config_default(byref(cfg)))
     for k, v in kw.items():
@@ -78,18 +80,22 @@ def lbm_config_default(**kw):
 
 
 def lbm_create(cfg):
+    """Create a simulation from a config; returns a Sim handle."""
     h = c_void_p()
     _check(_lib.load().lbm_create(byref(cfg), byref(h)))
     return Sim(h, cfg)
 
 
 def lbm_destroy(sim):
+    """Destroy a simulation (fails while a batch holds it)."""
     if sim.handle:
         _check(_lib.load().lbm_destroy(sim.handle))
         sim.handle = None
 
 
 def lbm_set_geometry(sim, kind):
+    """Cell kinds, uint8 of shape (ny, nx): 0 fluid, 1 solid body (its links count in
+    the force), 2 wall (solid, not counted)."""
     k = np.ascontiguousarray(kind, dtype=np.uint8)
     if k.shape != (sim.ny, sim.nx):
         raise ValueError("kind must have shape (ny, nx)")
@@ -97,6 +103,8 @@ def lbm_set_geometry(sim, kind):
 
 
 def lbm_init_equilibrium(sim, rho=None, ux=None, uy=None):
+    """Populations f_eq(rho, u) from (ny, nx) fields; None means rho = 1, u = 0.
+    Resets the step counter, the force series and the boundary state."""
     shape = (sim.ny, sim.nx)
     arrs = [None if a is None else _f64(a, shape) for a in (rho, ux, uy)]
     ptrs = [None if a is None else _dptr(a) for a in arrs]
@@ -104,6 +112,7 @@ def lbm_init_equilibrium(sim, rho=None, ux=None, uy=None):
 
 
 def lbm_set_outflow_zouhe(sim, rho_out=1.0):
+    """Zou & He pressure outflow at x = nx - 1 with density rho_out."""
     _check(_lib.load().lbm_set_outflow_zouhe(sim.handle, float(rho_out)))
 
 
@@ -157,6 +166,7 @@ def lbm_set_outflow_cbc(sim, sigma=0.0, kappa2=0.0, mach=0.0, length=0.0, tuner=
 
 
 def lbm_nn_fallbacks(sim):
+    """Number of network-outflow nodes that fell back to Zou & He so far."""
     c = c_int64()
     _check(_lib.load().lbm_nn_fallbacks(sim.handle, byref(c)))
     return c.value
@@ -194,14 +204,17 @@ def lbm_capture_snapshot(sim, x_begin, x_end, rows):
 
 
 def lbm_save(sim, path):
+    """Write a checkpoint (populations and step counter) to a file."""
     _check(_lib.load().lbm_save(sim.handle, str(path).encode()))
 
 
 def lbm_load(sim, path):
+    """Read a checkpoint written by lbm_save for a sim of the same size and precision."""
     _check(_lib.load().lbm_load(sim.handle, str(path).encode()))
 
 
 def lbm_capture_count(sim):
+    """Rows written so far by lbm_capture_plane."""
     c = c_int64()
     _check(_lib.load().lbm_capture_count(sim.handle, byref(c)))
     return c.value
@@ -221,6 +234,7 @@ def lbm_nn_dataset_stats(rows, n_rows=None, stream=None):
 
 
 def lbm_train_opts_default(**kw):
+    """Default training options with the given fields set."""
     o = LbmTrainOpts()
     _check(_lib.load().lbm_train_opts_default(byref(o)))
     for k, v in kw.items():
@@ -374,14 +388,17 @@ def unflatten(flat, like):
 
 
 def lbm_step(sim, n=1):
+    """Enqueue n time steps on the sim's stream (returns at once)."""
     _check(_lib.load().lbm_step(sim.handle, int(n)))
 
 
 def lbm_sync(sim):
+    """Wait for the sim's stream; raises LbmError for a latched device fault."""
     _check(_lib.load().lbm_sync(sim.handle))
 
 
 def lbm_time(sim):
+    """Step counter (time steps taken since the last initialisation or load)."""
     t = c_int64()
     _check(_lib.load().lbm_time(sim.handle, byref(t)))
     return t.value
@@ -399,6 +416,7 @@ def lbm_forces(sim, cap=None):
 
 
 def lbm_fields(sim):
+    """Macroscopic fields: (rho, ux, uy), each float64 of shape (ny, nx)."""
     rho = np.empty((sim.ny, sim.nx))
     ux = np.empty((sim.ny, sim.nx))
     uy = np.empty((sim.ny, sim.nx))
@@ -407,23 +425,28 @@ def lbm_fields(sim):
 
 
 def lbm_get_populations(sim):
+    """Populations f_i(x, y) as float64 of shape (9, ny, nx)."""
     f = np.empty((9, sim.ny, sim.nx))
     _check(_lib.load().lbm_get_populations(sim.handle, _dptr(f)))
     return f
 
 
 def lbm_set_populations(sim, f):
+    """Replace the populations by a float64 array of shape (9, ny, nx)."""
     f = _f64(f, (9, sim.ny, sim.nx))
     _check(_lib.load().lbm_set_populations(sim.handle, _dptr(f)))
 
 
 def lbm_mass(sim):
+    """Total mass (sum of rho over fluid nodes, FP64)."""
     m = c_double()
     _check(_lib.load().lbm_mass(sim.handle, byref(m)))
     return m.value
 
 
 def lbm_device_state(sim):
+    """Zero-copy view of the current populations: (device address, pitch, plane)
+    in elements of the storage type (see lbm.h for the layout)."""
     base = c_void_p()
     pitch = c_int64()
     plane = c_int64()
@@ -432,6 +455,7 @@ def lbm_device_state(sim):
 
 
 def lbm_set_tiling(sim, rows, variant):
+    """Strip height (rows) and kernel variant of the sim's own step launch (see lbm.h)."""
     _check(_lib.load().lbm_set_tiling(sim.handle, int(rows), int(variant)))
 
 
@@ -441,6 +465,7 @@ def lbm_debug_hold_dataflow(sim, hold):
 
 
 def lbm_get_tiling(sim):
+    """Returns (rows, variant) of the sim's own step launch."""
     r = ctypes.c_int32()
     v = ctypes.c_int32()
     _check(_lib.load().lbm_get_tiling(sim.handle, byref(r), byref(v)))
@@ -480,6 +505,7 @@ class Batch:
 
 
 def lbm_batch_create(sims):
+    """Batch of sims of one precision and stream, advanced together; returns a Batch."""
     arr = (c_void_p * len(sims))(*[s.handle.value if isinstance(s.handle, c_void_p) else s.handle
                                    for s in sims])
     h = c_void_p()
@@ -488,24 +514,29 @@ def lbm_batch_create(sims):
 
 
 def lbm_batch_destroy(batch):
+    """Destroy a batch (its sims stay valid)."""
     if batch.handle:
         _check(_lib.load().lbm_batch_destroy(batch.handle))
         batch.handle = None
 
 
 def lbm_batch_step(batch, n=1):
+    """Enqueue n time steps of every member (one launch per step)."""
     _check(_lib.load().lbm_batch_step(batch.handle, int(n)))
 
 
 def lbm_batch_sync(batch):
+    """Wait for the batch's stream; raises LbmError for a latched fault of any member."""
     _check(_lib.load().lbm_batch_sync(batch.handle))
 
 
 def lbm_batch_set_tiling(batch, rows, variant):
+    """Strip height and kernel variant of the batch launch."""
     _check(_lib.load().lbm_batch_set_tiling(batch.handle, int(rows), int(variant)))
 
 
 def lbm_batch_get_tiling(batch):
+    """Returns (rows, variant) of the batch launch."""
     r = ctypes.c_int32()
     v = ctypes.c_int32()
     _check(_lib.load().lbm_batch_get_tiling(batch.handle, byref(r), byref(v)))
@@ -513,6 +544,7 @@ def lbm_batch_get_tiling(batch):
 
 
 def lbm_batch_autotune(batch, steps=20, flush_bytes=0):
+    """Returns (rows, variant, mean step ms) of the fastest batch tiling, now in use."""
     ms = c_float()
     _check(_lib.load().lbm_batch_autotune(batch.handle, int(steps), int(flush_bytes), byref(ms)))
     r, v = lbm_batch_get_tiling(batch)
@@ -520,6 +552,7 @@ def lbm_batch_autotune(batch, steps=20, flush_bytes=0):
 
 
 def lbm_strouhal(cl, length, u):
+    """Strouhal number of a lift-coefficient series (dominant frequency x length / u)."""
     cl = np.ascontiguousarray(cl, dtype=np.float64)
     st = c_double()
     _check(_lib.load().lbm_strouhal(_dptr(cl), cl.size, float(length), float(u), byref(st)))
@@ -527,4 +560,5 @@ def lbm_strouhal(cl, length, u):
 
 
 def lbm_version():
+    """Version string of the library."""
     return _lib.load().lbm_version().decode()
