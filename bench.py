@@ -254,6 +254,74 @@ def dist_env():
 ORACLE_MEMBERS = 12   # lattices the CPU sample cycles through (bounds its memory)
 
 
+def _oracle_solver(wl, idx):
+    """The FP64 oracle set up on member idx (mod ORACLE_MEMBERS) of a workload."""
+    from oracle import cbc, lbm
+    ms = WORKLOADS[wl][:ORACLE_MEMBERS]
+    m = ms[idx % len(ms)]
+    kind, tau, init = member_geometry(m)
+    extra = {}
+    if m["outflow"] == "cbc":
+        extra = dict(outflow="cbc", cbc=cbc.CBCOutflow(sigma=0.25, kappa2=m["mach"],
+                                                       mach=m["mach"]))
+    s = lbm.Solver(lbm.Config(nx=m["nx"], ny=m["ny"], tau=tau, collision=m["collision"],
+                              u_in=m["U"], **extra), kind)
+    s.init_equilibrium(*init)
+    return s, m["nx"] * m["ny"]
+
+
+def _oracle_worker(wl, idx, steps, barrier, out):
+    """One process of the all-core leg: its own lattice, one untimed step, then
+    `steps` steps started together with every other worker."""
+    s, nodes = _oracle_solver(wl, idx)
+    s.step(1)
+    barrier.wait()
+    for _ in range(steps):
+        s.step(1)
+    out.put(nodes * steps)
+
+
+def oracle_all_cores(wl, steps, workers):
+    """All-core leg, run in a child process with no GPU: `workers` spawned
+    processes (one thread each), worker k stepping member k (mod
+    ORACLE_MEMBERS) `steps` times, all released together; the rate counts every
+    worker's node updates over the wall time from the release to the last
+    finish.  Returns (GLUPS, seconds)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers + 1)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(wl, k, steps, barrier, out))
+             for k in range(workers)]
+    for p in procs:
+        p.start()
+    barrier.wait()
+    t0 = time.perf_counter()
+    total = sum(out.get() for _ in procs)
+    dt = time.perf_counter() - t0
+    for p in procs:
+        p.join()
+    return total / dt / 1e9, dt
+
+
+def cpu_oracle_all_cores(wl, steps, workers=None):
+    """oracle_all_cores in a child interpreter that never sees the GPU.
+    Returns (GLUPS, seconds, workers)."""
+    workers = workers or os.cpu_count() or 1
+    code = ("import sys, json; sys.path.insert(0, %r)\n"
+            "import bench\n"
+            "v, dt = bench.oracle_all_cores(%r, %d, %d)\n"
+            "print(json.dumps({'value': v, 'dt': dt}))\n" % (ROOT, wl, steps, workers))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("all-core oracle timing failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["value"], d["dt"], workers
+
+
 def cpu_oracle_sample(wl, steps, warmup=1):
     """Time the FP64 oracle on the workload in a single-threaded child process:
     bench step k advances member k mod n (of the first ORACLE_MEMBERS lattices)
@@ -300,18 +368,21 @@ def run_reference(args):
     if rank != 0:
         return 0
     wl = args.workload
-    value, total, per_step, nodes = cpu_oracle_sample(wl, args.steps, args.warmup)
-    sample = (f"{args.steps} oracle time steps, one member lattice of {wl} per bench step "
-              f"(round robin over its first {min(ORACLE_MEMBERS, len(WORKLOADS[wl]))} lattices), "
-              f"numpy FP64, 1 thread")
+    # every host core: each bench step is one time step of `workers` member
+    # lattices at once (one per process), a bounded sample of the batch step
+    workers = os.cpu_count() or 1
+    value, total, _ = cpu_oracle_all_cores(wl, args.steps, workers)
+    sample = (f"{args.steps} oracle time steps in each of {workers} processes (one thread each), "
+              f"process k stepping member k mod {min(ORACLE_MEMBERS, len(WORKLOADS[wl]))} of "
+              f"{wl}; numpy FP64")
     line = {
         "impl": "reference", "metric": "GLUPS", "value": value, "unit": "GLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl, "lattices": len(WORKLOADS[wl]), "nodes": workload_nodes(wl),
-                   "outflow": workload_outflow(wl), "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+        "config": workload_config(wl, args.precision, args.layout, args.gpus),
+        "sample": sample,
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": workers, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -321,6 +392,46 @@ def run_reference(args):
 
 def workload_outflow(wl):
     return "+".join(sorted({m["outflow"] for m in WORKLOADS[wl]}))
+
+
+def workload_config(wl, prec, layout, world):
+    """The `config` of the JSON line, the same dict for both arms."""
+    nodes = workload_nodes(wl)
+    bpn = BYTES_PER_NODE[prec]
+    working_set = bpn * nodes // (2 if layout == "aa" else 1)
+    flush_mode = working_set < L2_BYTES
+    return {"workload": wl, "lattices": len(WORKLOADS[wl]), "nodes": nodes,
+            "members": ([member_label(m) for m in WORKLOADS[wl]]
+                        if len(WORKLOADS[wl]) <= 16 else
+                        f"{len(WORKLOADS[wl])} lattices, first: "
+                        f"{member_label(WORKLOADS[wl][0])}"),
+            "outflow": workload_outflow(wl), "storage": prec, "layout": layout,
+            "working_set_bytes": working_set,
+            "l2": ("flushed before each timed step (256 MB device write), steps timed one "
+                   "by one") if flush_mode else
+                  "working set larger than L2: no flush, steps back to back",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def graph_chunks(n):
+    """How group_step cuts a run of n steps: chunks of 32, 16, 8 or 4 steps
+    replayed from graphs, the remaining 0-3 steps launched directly.
+    Returns (chunks, direct launches)."""
+    chunks = 0
+    while n >= 4:
+        c = 32
+        while c > n:
+            c //= 2
+        n -= c
+        chunks += 1
+    return chunks, n
+
+
+def step_launches(n):
+    """Kernel launches of n back-to-back steps: one step kernel per step plus,
+    before each graph chunk, a force-finalise and a step-index launch."""
+    chunks, _ = graph_chunks(n)
+    return n + 2 * chunks
 
 
 class _Stepper:
@@ -477,6 +588,11 @@ def run_ours(args):
             batch.step(1)
             if flush is not None:
                 flush.fill_(1.0)
+        if not flush_mode:
+            # instantiate the graphs the timed call replays (its chunk lengths from
+            # either starting buffer), so no capture runs inside the timed region
+            batch.step(args.steps)
+            batch.step(args.steps)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -504,6 +620,25 @@ def run_ours(args):
             wall = time.perf_counter() - wall0
         if world > 1:
             torch.distributed.barrier()
+    # the same call over 2000 steps right after, for comparison with the K-step
+    # figure, with the clocks sampled over its longer region
+    long_run = None
+    if not flush_mode and args.steps < 2000 and not args.no_long_run:
+        with torch.cuda.stream(stream):
+            batch.step(2000)
+            batch.step(2000)
+            torch.cuda.synchronize()
+            with ClockSampler(local) as clk_long:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                batch.step(2000)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                long_ms = e0.elapsed_time(e1)
+        long_run = {"steps": 2000, "ms_per_step": long_ms / 2000,
+                    "value": nodes * 2000 / (long_ms * 1e-3) / 1e9, "unit": "GLUPS",
+                    "clocks": clk_long.summary()}
     # lattices that went non-finite (the work per node is the same either way)
     diverged = []
     for m, s in zip(WORKLOADS[wl], sims):
@@ -576,28 +711,31 @@ def run_ours(args):
     if world == 1 and not args.no_tuner:
         tuner = tuner_study()
     if world == 1 and not args.no_cpu_baseline:
+        # all host cores (the figure the line carries) and one thread beside it
+        workers = os.cpu_count() or 1
+        glups_all, dt_all, _ = cpu_oracle_all_cores(wl, args.cpu_steps_all, workers)
         glups_cpu, dt_cpu, _, _ = cpu_oracle_sample(wl, args.cpu_steps)
-        cpu = {"value": glups_cpu, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_steps} oracle time steps, one member lattice of {wl} per "
-                         f"step, round robin ({dt_cpu:.1f} s), numpy FP64, 1 thread"}
+        cpu = {"value": glups_all, "unit": "GLUPS", "cores": workers, "kind": "oracle",
+               "sample": f"{args.cpu_steps_all} oracle time steps in each of {workers} processes "
+                         f"(one thread each, process k on member k mod "
+                         f"{min(ORACLE_MEMBERS, len(WORKLOADS[wl]))} of {wl}; {dt_all:.1f} s), "
+                         f"numpy FP64",
+               "single_thread": {"value": glups_cpu, "unit": "GLUPS", "cores": 1,
+                                 "sample": f"{args.cpu_steps} oracle time steps, one member "
+                                           f"lattice of {wl} per step, round robin "
+                                           f"({dt_cpu:.1f} s), numpy FP64, 1 thread"}}
     line = {
         "metric": "GLUPS", "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16"}[prec], "data": "synthetic",
-        "config": {"workload": wl, "lattices": len(WORKLOADS[wl]), "nodes": nodes,
-                   "members": ([member_label(m) for m in WORKLOADS[wl]]
-                               if len(WORKLOADS[wl]) <= 16 else
-                               f"{len(WORKLOADS[wl])} lattices, first: "
-                               f"{member_label(WORKLOADS[wl][0])}"),
-                   "outflow": workload_outflow(wl), "storage": prec, "layout": args.layout,
-                   "working_set_bytes": working_set,
-                   "l2": ("flushed before each timed step (256 MB device write), steps timed one "
-                          "by one") if flush_mode else
-                         "working set larger than L2: no flush, steps back to back",
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "tiling": {"rows": rows, "variant": variant}, "wall_s": wall,
-                   "diverged_during_run": diverged},
+        "config": workload_config(wl, prec, args.layout, world),
+        "run": {"tiling": {"rows": rows, "variant": variant}, "wall_s": wall,
+                "diverged_during_run": diverged,
+                "graph_warmup": None if flush_mode else
+                f"after the {args.warmup} warm-up steps, two untimed calls of {args.steps} steps "
+                f"instantiate the graph chunks the timed call replays"},
+        "long_run": long_run,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "note": f"{bpn} B/node/step algorithmic x {nodes} nodes per launch; peak "
@@ -607,10 +745,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h / e2e_steps,
                 "note": f"per lattice lbm_set_geometry + lbm_init_equilibrium from pinned host; "
                         f"{e2e_steps} batch steps; lbm_forces + lbm_fields to host"},
-        # one step-kernel launch per step; steps run back to back go in 32-step
-        # graph chunks, each preceded by one force-finalise and one step-index
-        # launch (the pattern of the committed launch list)
-        "gpu_launches": args.steps if flush_mode else args.steps + 2 * (-(-args.steps // 32)),
+        # one step-kernel launch per step; steps run back to back go in graph
+        # chunks of 32/16/8/4 steps, each preceded by one force-finalise and one
+        # step-index launch (the pattern of the committed launch list)
+        "gpu_launches": args.steps if flush_mode else step_launches(args.steps),
         "clocks": clk.summary(),
         "accuracy": accuracy,
         "cbc_tuner": tuner,
@@ -630,6 +768,10 @@ def main():
     ap.add_argument("--workload", default="cylinder_sweep_D40", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=sorted(BYTES_PER_NODE))
     ap.add_argument("--cpu-steps", type=int, default=120)
+    ap.add_argument("--cpu-steps-all", type=int, default=30,
+                    help="oracle steps per process of the all-core CPU leg")
+    ap.add_argument("--no-long-run", action="store_true",
+                    help="skip the 2000-step comparison run after the timed region")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the NN vs Zou & He truncation study (about a minute)")

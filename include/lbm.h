@@ -63,21 +63,35 @@ typedef enum { LBM_OUTFLOW_ZOUHE = 0, LBM_OUTFLOW_NN = 1, LBM_OUTFLOW_CBC = 2 } 
 enum { LBM_CELL_FLUID = 0, LBM_CELL_SOLID = 1, LBM_CELL_WALL = 2 };
 
 /* Optional device allocator (for instance backed by a framework's caching
- * allocator).  alloc returns NULL on failure; free accepts what alloc gave. */
+ * allocator).  alloc returns NULL on failure (the call then fails with
+ * LBM_ERR_OOM and frees what it had taken); free accepts what alloc gave.
+ * The library frees a block only after the work that used it has completed
+ * on the device, so a pool may hand it out again at once. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);
   void* ctx;
 } lbm_allocator;
 
+/* Process-wide default allocator (the paper has no counterpart): every device
+ * allocation made for a call that names no allocator of its own goes through
+ * it -- sims created with lbm_config.alloc NULL (populations, geometry, force
+ * ring, scratch) and their batches, the autotuner's scratch, and the scratch of
+ * the training and statistics calls.  The struct is copied; NULL restores
+ * cudaMalloc / cudaFree.  A sim keeps the allocator it was created with.  The
+ * Python binding installs one backed by PyTorch's caching allocator. */
+lbm_status lbm_set_default_allocator(const lbm_allocator* alloc);
+
 typedef struct {
   int32_t nx, ny;           /* lattice size; nx >= 3 (>= 5 for NN/CBC outflow) unless x_periodic;
                                ny <= 65535, 9 * ny * pitch < 2^31 (pitch = nx rounded up to 64) */
   double tau;               /* BGK relaxation time (Eq. 2), tau > 1/2; nu = (tau - 1/2) / 3 */
   int32_t collision;        /* lbm_collision */
-  double mrt_rates[9];      /* MRT rates in moment order (rho, e, eps, jx, qx, jy, qy, pxx, pxy);
-                               the conserved ones (0, 3, 5) are ignored; the stress rates 7, 8
-                               default to 1/tau.  All zero: e, eps, q rates 1, stress 1/tau. */
+  double mrt_rates[9];      /* MRT rates in moment order (rho, e, eps, jx, qx, jy, qy, pxx, pxy),
+                               each in [0, 2) (else LBM_ERR_ARG); the conserved ones (0, 3, 5)
+                               are ignored, the other six relax their moments independently;
+                               a zero stress rate (7 or 8) means 1/tau.  All nine zero: e, eps,
+                               q rates 1, stress rates 1/tau. */
   int32_t precision;        /* lbm_precision */
   int32_t x_periodic;       /* 1: x wraps too (no inlet, no outflow); 0: open in x */
   double u_in;              /* west inlet velocity (Zou & He, Sec. 2.2 "by symmetry") */
@@ -86,7 +100,9 @@ typedef struct {
   double rho_out;           /* outflow density for Zou & He (Eq. 7) */
   void* stream;             /* cudaStream_t to run on; NULL: the library creates one */
   const lbm_allocator* alloc; /* NULL: cudaMalloc / cudaFree */
-  int64_t force_capacity;   /* device ring of per-step forces; 0: 1 << 20 steps */
+  int64_t force_capacity;   /* device ring of per-step forces (steps); 0: the ring starts at
+                               4096 steps and doubles, up to 2^20, before a run of steps would
+                               overwrite forces not yet drained by lbm_forces */
   int64_t ramp_steps;       /* > 0: the inlet velocity of step t is u_in min(1, (t+1)/ramp_steps)
                                (a smooth start; the paper does not state how its runs start) */
   int32_t layout;           /* lbm_layout: LBM_LAYOUT_AB (default) or LBM_LAYOUT_AA */
@@ -437,27 +453,32 @@ lbm_status lbm_autotune(lbm_sim* sim, int32_t steps, int64_t flush_bytes, float*
  * kind is a device uint8[ny][nx] of cell kinds as for lbm_set_geometry; t is
  * the step index (it keys the seeded inlet perturbation); force is a device
  * double[2] that receives (F_x, F_y) of the step.  From cfg it uses nx, ny,
- * tau, collision, mrt_rates, x_periodic, u_in, v_pert_amp, seed, rho_out and
- * stream (NULL: the legacy default stream); precision must be LBM_FP32 and
+ * tau, collision, mrt_rates, x_periodic, u_in, v_pert_amp, seed, rho_out,
+ * ramp_steps and stream (NULL: the legacy default stream); precision must be LBM_FP32 and
  * alloc and force_capacity are ignored.  The call only enqueues work and
  * reports launch errors; it does not synchronise.
  *
  * Scratch: the per-block force partials live in a 128 KiB static device
  * array that every GPU loading the library holds until exit, so the lattice
  * may have at most 8192 strips of 128 x 8 nodes (8,388,608 nodes); larger
- * lattices are rejected with LBM_ERR_ARG.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture.  All calls share the array:
- * calls that overlap on the GPU (for instance on two streams) race on it and
- * must be ordered by the caller. */
+ * lattices are rejected with LBM_ERR_ARG.  Every call made outside a stream
+ * capture looks up that array's device address (cudaGetSymbolAddress) with
+ * the current device; a call inside a capture reuses the address of the last
+ * call on that device, so make the first call on a device before any stream
+ * capture (a captured first call returns LBM_ERR_STATE).  MRT rates outside
+ * [0, 2) are rejected with LBM_ERR_ARG as in lbm_create.  All calls share the
+ * array: calls that overlap on the GPU (for instance on two streams) race on
+ * it and must be ordered by the caller. */
 lbm_status lbm_step_noalloc(const lbm_config* cfg, const float* src, float* dst,
                             const uint8_t* kind, int64_t pitch, int64_t t, double* force);
 
 /* Batches.  A batch advances several sims -- of any sizes, relaxation times,
  * collision operators, inlet velocities and outflows -- by one kernel launch
- * per time step (plus one east-column launch per NN-outflow member), the
- * launch table listing every member's strips; chunks of 32 steps replay from
- * CUDA graphs.  Members must share one precision and one stream
+ * per time step (the east boundary blocks of NN and characteristic outflows
+ * run inside it), the launch table listing every member's strips; runs of
+ * steps are cut into chunks of 32, 16, 8 or 4 steps that replay from CUDA
+ * graphs (a graph is instantiated the first time its length and starting
+ * buffer occur, then reused).  Members must share one precision and one stream
  * (lbm_config.stream) and be at the same step (for instance all freshly
  * initialised); the batch keeps them in lockstep.  Members remain ordinary
  * sims for every other call (lbm_forces, lbm_fields, ...); stepping a member

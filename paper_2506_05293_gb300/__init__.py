@@ -3,6 +3,7 @@
 include/lbm.h; this package is its Python binding."""
 from . import _lib
 from .api import *  # noqa: F401,F403
-from .api import LbmError, Sim, make_mlp, unflatten
+from .api import LbmError, Sim, make_mlp, unflatten, use_torch_allocator
 
-__all__ = [n for n in dir() if n.startswith("lbm_")] + ["LbmError", "Sim", "make_mlp", "unflatten"]
+__all__ = [n for n in dir() if n.startswith("lbm_")] + ["LbmError", "Sim", "make_mlp", "unflatten",
+                                                        "use_torch_allocator"]

@@ -114,6 +114,7 @@ SIGNATURES = {
     "lbm_batch_get_tiling": (c_int, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     "lbm_batch_autotune": (c_int, [c_void_p, c_int32, c_int64, POINTER(c_float)]),
     "lbm_strouhal": (c_int, [POINTER(c_double), c_int64, c_double, c_double, POINTER(c_double)]),
+    "lbm_set_default_allocator": (c_int, [POINTER(LbmAllocator)]),
     "lbm_last_error": (c_char_p, []),
     "lbm_version": (c_char_p, []),
 }
@@ -136,4 +137,7 @@ def load():
         fn.restype = res
         fn.argtypes = args
     _lib = lib
+    # device memory from torch's caching allocator (LBM_TORCH_ALLOCATOR=0: cudaMalloc)
+    from . import _torch_alloc
+    _torch_alloc.install_default(lib, LbmAllocator)
     return lib

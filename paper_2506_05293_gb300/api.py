@@ -8,8 +8,9 @@ from ctypes import POINTER, byref, c_double, c_float, c_int64, c_uint8, c_void_p
 
 import numpy as np
 
-from . import _lib
+from . import _lib, _torch_alloc
 from ._lib import LbmConfig, LbmMlp, LbmTrainOpts
+from ._torch_alloc import use_torch_allocator  # noqa: F401
 
 LBM_BGK, LBM_MRT = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV = 0, 1, 2
@@ -47,14 +48,26 @@ class Sim:
         self.handle = handle
         self.nx, self.ny = cfg.nx, cfg.ny
         self.cfg = cfg
+        _torch_alloc.track(self)
+
+    def close(self):
+        if self.handle:
+            _lib.load().lbm_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:
-            if self.handle:
-                _lib.load().lbm_destroy(self.handle)
-                self.handle = None
+            self.close()
         except Exception:
             pass
+
+
+def lbm_set_default_allocator(alloc):
+    """Install an LbmAllocator (a ctypes struct whose callbacks the caller
+    keeps alive) as the library's default device allocator; None restores
+    cudaMalloc / cudaFree.  The binding installs torch's caching allocator on
+    load (see use_torch_allocator)."""
+    _check(_lib.load().lbm_set_default_allocator(byref(alloc) if alloc is not None else None))
 
 
 def lbm_config_default(**kw):
@@ -494,12 +507,16 @@ class Batch:
     def __init__(self, handle, sims):
         self.handle = handle
         self.sims = list(sims)
+        _torch_alloc.track(self)
+
+    def close(self):
+        if self.handle:
+            _lib.load().lbm_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:
-            if self.handle:
-                _lib.load().lbm_batch_destroy(self.handle)
-                self.handle = None
+            self.close()
         except Exception:
             pass
 

@@ -41,12 +41,32 @@ lbm_status from_cuda(const CudaError& ce) {
   catch (const std::bad_alloc&) { return fail(LBM_ERR_OOM, "host allocation failed"); } \
   catch (const std::exception& ex) { return fail(LBM_ERR_CUDA, ex.what()); }
 
-constexpr int64_t kDefaultRing = int64_t(1) << 20;
+// force ring of a sim created with force_capacity 0: it starts at this many
+// steps and grows on demand (see lbm::sim_reserve_ring)
+constexpr int64_t kInitialRing = int64_t(1) << 12;
+// import/export scratch: at most this many doubles (64 MiB), whole rows
+constexpr int64_t kScratchDoubles = int64_t(8) << 20;
 
 void* dev_alloc(lbm_sim* s, size_t bytes) {
   void* p = lbm::dev_alloc_raw(s->have_alloc ? &s->alloc : nullptr, bytes);
   s->owned.push_back(p);
   return p;
+}
+
+// Scratch for row chunks of per_node doubles per node: allocated at the first
+// import or export, min(9 nx ny, kScratchDoubles) doubles but at least one row
+// of nine populations.  *rows gets the rows one chunk holds.
+double* field_scratch(lbm_sim* s, int per_node, int* rows) {
+  if (!s->scratch_fields) {
+    const int64_t cells = (int64_t)s->nx * s->ny;
+    const int64_t want =
+        std::min<int64_t>(9 * cells, std::max<int64_t>(kScratchDoubles, 9 * (int64_t)s->nx));
+    s->scratch_fields = (double*)dev_alloc(s, (size_t)want * sizeof(double));
+    s->scratch_doubles = want;
+  }
+  *rows = (int)std::max<int64_t>(
+      1, std::min<int64_t>(s->ny, s->scratch_doubles / ((int64_t)per_node * s->nx)));
+  return s->scratch_fields;
 }
 
 void release_all(lbm_sim* s) {
@@ -108,12 +128,21 @@ void set_last_error(const std::string& msg) { g_err = msg; }
 
 namespace {
 
-// Device buffer freed when the scope ends (training calls own their memory).
+// Device buffer freed when the scope ends (training calls own their memory),
+// taken from the process-wide default allocator (lbm_set_default_allocator).
 struct DevBuf {
   void* p = nullptr;
-  explicit DevBuf(size_t bytes) { ck(cudaMalloc(&p, bytes ? bytes : 16), "cudaMalloc"); }
+  lbm_allocator a{};
+  bool have = false;
+  explicit DevBuf(size_t bytes) {
+    have = lbm::default_allocator(&a);
+    p = lbm::dev_alloc_raw(have ? &a : nullptr, bytes ? bytes : 16);
+  }
   ~DevBuf() {
-    if (p) cudaFree(p);
+    // an injected allocator may hand the memory out again at once: on an
+    // early exit kernels of this call could still be using it
+    if (have && p) cudaDeviceSynchronize();
+    lbm::dev_free_raw(have ? &a : nullptr, p);
   }
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
@@ -287,8 +316,29 @@ lbm_status upload_net(lbm_sim* s, const lbm_mlp* net, int n_in, int64_t np) {
   }
   LBM_GUARD_BEGIN
   if (!s->nn.params_f || s->nn.blob_elems != (int32_t)blob_n) {
-    s->nn.params_f = (float*)dev_alloc(s, blob.size() * sizeof(float));
-    s->nn.params_d = (double*)dev_alloc(s, blob.size() * sizeof(double));
+    // both copies or neither: a failed allocation leaves the current network
+    const lbm_allocator* a = s->have_alloc ? &s->alloc : nullptr;
+    float* pf = (float*)lbm::dev_alloc_raw(a, blob.size() * sizeof(float));
+    double* pd = nullptr;
+    try {
+      pd = (double*)lbm::dev_alloc_raw(a, blob.size() * sizeof(double));
+    } catch (...) {
+      lbm::dev_free_raw(a, pf);
+      throw;
+    }
+    if (s->nn.params_f) {
+      // launch tables may still name the old copies: free them once the stream is idle
+      lbm::sim_settle(s);
+      ck(cudaStreamSynchronize(s->stream), "net sync");
+      for (void* q : {(void*)s->nn.params_f, (void*)s->nn.params_d}) {
+        s->owned.erase(std::remove(s->owned.begin(), s->owned.end(), q), s->owned.end());
+        lbm::dev_free_raw(a, q);
+      }
+    }
+    s->nn.params_f = pf;
+    s->nn.params_d = pd;
+    s->owned.push_back(pf);
+    s->owned.push_back(pd);
   }
   std::vector<double> blob_d(blob.begin(), blob.end());
   ck(cudaMemcpyAsync(s->nn.params_f, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice,
@@ -315,6 +365,13 @@ void group_hold_flags(Group& g, bool hold);   // group.cu: test hook of the flag
 extern "C" {
 
 const char* lbm_last_error(void) { return g_err.c_str(); }
+
+lbm_status lbm_set_default_allocator(const lbm_allocator* alloc) {
+  if (alloc && (!alloc->alloc || !alloc->free))
+    return fail(LBM_ERR_ARG, "allocator needs both alloc and free");
+  lbm::set_default_allocator(alloc);
+  return LBM_OK;
+}
 
 const char* lbm_version(void) { return "gb300-lbm 0.1 (sm_103a)"; }
 
@@ -353,9 +410,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   if (cfg->ramp_steps < 0) return fail(LBM_ERR_ARG, "ramp_steps must be >= 0");
   if (cfg->alloc && (!cfg->alloc->alloc || !cfg->alloc->free))
     return fail(LBM_ERR_ARG, "allocator needs both alloc and free");
-  for (int k = 0; k < 9; ++k)
-    if (!std::isfinite(cfg->mrt_rates[k]) || cfg->mrt_rates[k] < 0.0 || cfg->mrt_rates[k] >= 2.0)
-      return fail(LBM_ERR_ARG, "MRT rates must lie in [0, 2)");
+  if (!lbm::mrt_rates_valid(*cfg)) return fail(LBM_ERR_ARG, "MRT rates must lie in [0, 2)");
 
   lbm_sim* s = new (std::nothrow) lbm_sim();
   if (!s) return fail(LBM_ERR_OOM, "host allocation failed");
@@ -373,6 +428,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   if (cfg->alloc) {
     s->alloc = *cfg->alloc;
     s->have_alloc = true;
+  } else {
+    s->have_alloc = lbm::default_allocator(&s->alloc);
   }
   s->cfg.alloc = nullptr;
   if (cfg->stream) {
@@ -398,10 +455,10 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   s->solid_bits = (uint32_t*)dev_alloc(s, (size_t)s->words_per_row * s->ny * 4);
   s->links = (uint8_t*)dev_alloc(s, cells);
   s->near_bits = (uint32_t*)dev_alloc(s, (size_t)s->words_per_row * s->ny * 4);
-  s->ring_cap = cfg->force_capacity > 0 ? cfg->force_capacity : kDefaultRing;
+  s->ring_auto = cfg->force_capacity == 0;
+  s->ring_cap = s->ring_auto ? kInitialRing : cfg->force_capacity;
   s->ring = (double*)dev_alloc(s, (size_t)2 * s->ring_cap * sizeof(double));
   s->status = (int*)dev_alloc(s, sizeof(int));
-  s->scratch_fields = (double*)dev_alloc(s, (size_t)9 * cells * sizeof(double));
   s->scratch_sums = (double*)dev_alloc(s, ((size_t)s->ny + 1) * sizeof(double));
   s->nn_fallbacks = (unsigned long long*)dev_alloc(s, sizeof(unsigned long long));
   ck(cudaMemsetAsync(s->kind, 0, cells, s->stream), "memset");
@@ -482,28 +539,33 @@ static void reset_counters(lbm_sim* s) {
 
 lbm_status lbm_init_equilibrium(lbm_sim* s, const double* rho, const double* ux, const double* uy) {
   if (lbm_status st = check_sim(s)) return st;
-  const int64_t cells = (int64_t)s->nx * s->ny;
   LBM_GUARD_BEGIN
-  double* d = s->scratch_fields;
-  const double* dr = nullptr;
-  const double* du = nullptr;
-  const double* dv = nullptr;
-  if (rho) {
-    ck(cudaMemcpyAsync(d, rho, cells * 8, cudaMemcpyHostToDevice, s->stream), "rho copy");
-    dr = d;
-  }
-  if (ux) {
-    ck(cudaMemcpyAsync(d + cells, ux, cells * 8, cudaMemcpyHostToDevice, s->stream), "ux copy");
-    du = d + cells;
-  }
-  if (uy) {
-    ck(cudaMemcpyAsync(d + 2 * cells, uy, cells * 8, cudaMemcpyHostToDevice, s->stream), "uy copy");
-    dv = d + 2 * cells;
-  }
   s->cur = 0;
-  lbm::launch_init_equilibrium(s->prec, s->buf[0], s->nx, s->ny, s->pitch, s->plane, dr, du, dv,
-                               s->stream, lbm::pop_map(s, 0));
-  ck(cudaGetLastError(), "init launch");
+  if (!rho && !ux && !uy) {
+    lbm::launch_init_equilibrium(s->prec, s->buf[0], s->nx, s->ny, s->pitch, s->plane, nullptr,
+                                 nullptr, nullptr, s->stream, lbm::pop_map(s, 0));
+    ck(cudaGetLastError(), "init launch");
+  } else {
+    // the fields stream through the scratch in chunks of whole rows
+    int rows = 0;
+    double* d = field_scratch(s, 3, &rows);
+    const size_t nx = (size_t)s->nx;
+    for (int y0 = 0; y0 < s->ny; y0 += rows) {
+      const int r = std::min(rows, s->ny - y0);
+      const size_t n = (size_t)r * nx;
+      const double* src[3] = {rho, ux, uy};
+      const double* dev[3] = {nullptr, nullptr, nullptr};
+      for (int k = 0; k < 3; ++k) {
+        if (!src[k]) continue;
+        ck(cudaMemcpyAsync(d + k * n, src[k] + (size_t)y0 * nx, n * 8, cudaMemcpyHostToDevice,
+                           s->stream), "field copy");
+        dev[k] = d + k * n;
+      }
+      lbm::launch_init_equilibrium(s->prec, s->buf[0], s->nx, s->ny, s->pitch, s->plane, dev[0],
+                                   dev[1], dev[2], s->stream, lbm::pop_map(s, 0), y0, r);
+      ck(cudaGetLastError(), "init launch");
+    }
+  }
   reset_counters(s);
   ck(cudaStreamSynchronize(s->stream), "init sync");
   return LBM_OK;
@@ -777,15 +839,22 @@ lbm_status lbm_forces(lbm_sim* s, double* fx, double* fy, int64_t cap, int64_t* 
 
 lbm_status lbm_fields(lbm_sim* s, double* rho, double* ux, double* uy) {
   if (lbm_status st = check_sim(s)) return st;
-  const int64_t cells = (int64_t)s->nx * s->ny;
   LBM_GUARD_BEGIN
-  double* d = s->scratch_fields;
-  lbm::launch_export(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane, nullptr, d,
-                     d + cells, d + 2 * cells, s->stream, lbm::pop_map(s, s->t_host));
-  ck(cudaGetLastError(), "export launch");
-  if (rho) ck(cudaMemcpyAsync(rho, d, cells * 8, cudaMemcpyDeviceToHost, s->stream), "copy");
-  if (ux) ck(cudaMemcpyAsync(ux, d + cells, cells * 8, cudaMemcpyDeviceToHost, s->stream), "copy");
-  if (uy) ck(cudaMemcpyAsync(uy, d + 2 * cells, cells * 8, cudaMemcpyDeviceToHost, s->stream), "copy");
+  int rows = 0;
+  double* d = field_scratch(s, 3, &rows);
+  const size_t nx = (size_t)s->nx;
+  for (int y0 = 0; y0 < s->ny; y0 += rows) {
+    const int r = std::min(rows, s->ny - y0);
+    const size_t n = (size_t)r * nx;
+    lbm::launch_export(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane, nullptr, d,
+                       d + n, d + 2 * n, s->stream, lbm::pop_map(s, s->t_host), y0, r);
+    ck(cudaGetLastError(), "export launch");
+    double* dst[3] = {rho, ux, uy};
+    for (int k = 0; k < 3; ++k)
+      if (dst[k])
+        ck(cudaMemcpyAsync(dst[k] + (size_t)y0 * nx, d + k * n, n * 8, cudaMemcpyDeviceToHost,
+                           s->stream), "field copy");
+  }
   return read_status(s);
   LBM_GUARD_END
 }
@@ -793,14 +862,21 @@ lbm_status lbm_fields(lbm_sim* s, double* rho, double* ux, double* uy) {
 lbm_status lbm_get_populations(lbm_sim* s, double* f) {
   if (lbm_status st = check_sim(s)) return st;
   if (!f) return fail(LBM_ERR_ARG, "f is NULL");
-  const int64_t cells = (int64_t)s->nx * s->ny;
+  const size_t cells = (size_t)s->nx * s->ny;
   LBM_GUARD_BEGIN
-  lbm::launch_export(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane,
-                     s->scratch_fields, nullptr, nullptr, nullptr, s->stream,
-                     lbm::pop_map(s, s->t_host));
-  ck(cudaGetLastError(), "export launch");
-  ck(cudaMemcpyAsync(f, s->scratch_fields, 9 * cells * 8, cudaMemcpyDeviceToHost, s->stream),
-     "copy");
+  int rows = 0;
+  double* d = field_scratch(s, 9, &rows);
+  const size_t nx = (size_t)s->nx;
+  for (int y0 = 0; y0 < s->ny; y0 += rows) {
+    const int r = std::min(rows, s->ny - y0);
+    const size_t n = (size_t)r * nx;
+    lbm::launch_export(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane, d, nullptr,
+                       nullptr, nullptr, s->stream, lbm::pop_map(s, s->t_host), y0, r);
+    ck(cudaGetLastError(), "export launch");
+    // nine planes of r rows into the host planes of ny rows
+    ck(cudaMemcpy2DAsync(f + (size_t)y0 * nx, cells * 8, d, n * 8, n * 8, 9,
+                         cudaMemcpyDeviceToHost, s->stream), "population copy");
+  }
   return read_status(s);
   LBM_GUARD_END
 }
@@ -808,13 +884,20 @@ lbm_status lbm_get_populations(lbm_sim* s, double* f) {
 lbm_status lbm_set_populations(lbm_sim* s, const double* f) {
   if (lbm_status st = check_sim(s)) return st;
   if (!f) return fail(LBM_ERR_ARG, "f is NULL");
-  const int64_t cells = (int64_t)s->nx * s->ny;
+  const size_t cells = (size_t)s->nx * s->ny;
   LBM_GUARD_BEGIN
-  ck(cudaMemcpyAsync(s->scratch_fields, f, 9 * cells * 8, cudaMemcpyHostToDevice, s->stream),
-     "copy");
-  lbm::launch_import(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane,
-                     s->scratch_fields, s->stream, lbm::pop_map(s, s->t_host));
-  ck(cudaGetLastError(), "import launch");
+  int rows = 0;
+  double* d = field_scratch(s, 9, &rows);
+  const size_t nx = (size_t)s->nx;
+  for (int y0 = 0; y0 < s->ny; y0 += rows) {
+    const int r = std::min(rows, s->ny - y0);
+    const size_t n = (size_t)r * nx;
+    ck(cudaMemcpy2DAsync(d, n * 8, f + (size_t)y0 * nx, cells * 8, n * 8, 9,
+                         cudaMemcpyHostToDevice, s->stream), "population copy");
+    lbm::launch_import(s->prec, s->buf[s->cur], s->nx, s->ny, s->pitch, s->plane, d, s->stream,
+                       lbm::pop_map(s, s->t_host), y0, r);
+    ck(cudaGetLastError(), "import launch");
+  }
   ck(cudaStreamSynchronize(s->stream), "sync");
   return LBM_OK;
   LBM_GUARD_END

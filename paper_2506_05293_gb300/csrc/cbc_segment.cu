@@ -832,15 +832,21 @@ __global__ void copy_columns_kernel(const S* src, int ny, int64_t pitch, int64_t
   out[k] = (double)to_r<double>(src[i * plane + (int64_t)y * pitch + x0 + j]) + wgt<double>(i);
 }
 
+// Device scratch of one call, from the process-wide default allocator
+// (lbm_set_default_allocator), freed when the call returns.
 struct Scratch {
   std::vector<void*> ptrs;
+  lbm_allocator a{};
+  bool have = default_allocator(&a);
   ~Scratch() {
-    for (void* q : ptrs) cudaFree(q);
+    // an injected allocator may hand the memory out again at once: on an
+    // early exit kernels of this call could still be using it
+    if (have && !ptrs.empty()) cudaDeviceSynchronize();
+    for (void* q : ptrs) dev_free_raw(have ? &a : nullptr, q);
   }
   template <typename T>
   T* get(size_t n) {
-    void* q = nullptr;
-    ck(cudaMalloc(&q, std::max<size_t>(n * sizeof(T), 16)), "cudaMalloc");
+    void* q = dev_alloc_raw(have ? &a : nullptr, std::max<size_t>(n * sizeof(T), 16));
     ptrs.push_back(q);
     return static_cast<T*>(q);
   }

@@ -39,26 +39,12 @@ void fill_member(const lbm_sim* s, Member& m) {
   m.links = s->links;
   m.near_bits = s->near_bits;
   m.omega = 1.0 / s->cfg.tau;
-  const double* r = s->cfg.mrt_rates;
-  bool any = false;
-  for (int k = 0; k < 9; ++k) any |= r[k] != 0.0;
-  if (any) {
-    m.mrt_se = r[1];
-    m.mrt_seps = r[2];
-    m.mrt_sq = r[4];
-    m.mrt_snu = r[7] != 0.0 ? r[7] : 1.0 / s->cfg.tau;
-  } else {
-    m.mrt_se = m.mrt_seps = m.mrt_sq = 1.0;
-    m.mrt_snu = 1.0 / s->cfg.tau;
-  }
+  mrt_rates_of(s->cfg, m.mrt);
   m.u_in = s->cfg.u_in;
   m.v_amp = s->cfg.v_pert_amp;
   m.rho_out = s->rho_out;
   m.omega_f = (float)m.omega;
-  m.mrt_f[0] = (float)m.mrt_se;
-  m.mrt_f[1] = (float)m.mrt_seps;
-  m.mrt_f[2] = (float)m.mrt_sq;
-  m.mrt_f[3] = (float)m.mrt_snu;
+  for (int k = 0; k < 6; ++k) m.mrt_f[k] = (float)m.mrt[k];
   m.u_in_f = (float)m.u_in;
   m.rho_out_f = (float)m.rho_out;
   m.seed = s->cfg.seed;
@@ -447,6 +433,59 @@ void enqueue_captures(Group& g, int q, int64_t t) {
 
 }  // namespace
 
+std::mutex& default_alloc_mutex() {
+  static std::mutex m;
+  return m;
+}
+lbm_allocator g_default_alloc{};
+bool g_have_default_alloc = false;
+
+bool default_allocator(lbm_allocator* out) {
+  std::lock_guard<std::mutex> lock(default_alloc_mutex());
+  if (g_have_default_alloc) *out = g_default_alloc;
+  return g_have_default_alloc;
+}
+
+void set_default_allocator(const lbm_allocator* a) {
+  std::lock_guard<std::mutex> lock(default_alloc_mutex());
+  g_have_default_alloc = a != nullptr;
+  g_default_alloc = a ? *a : lbm_allocator{};
+}
+
+// The largest force ring that grows on demand (2^20 steps, 16 MiB).
+constexpr int64_t kMaxAutoRing = int64_t(1) << 20;
+
+void sim_reserve_ring(lbm_sim* s, int64_t n) {
+  if (!s->ring_auto || s->ring_cap >= kMaxAutoRing) return;
+  const int64_t need = s->t_host + n - s->drained;
+  if (need <= s->ring_cap) return;
+  int64_t cap = s->ring_cap;
+  while (cap < need && cap < kMaxAutoRing) cap *= 2;
+  // the forces of the last step must be in the ring before it moves
+  sim_settle(s);
+  const lbm_allocator* a = s->have_alloc ? &s->alloc : nullptr;
+  double* ring = (double*)dev_alloc_raw(a, (size_t)2 * cap * sizeof(double));
+  s->owned.push_back(ring);
+  ck(cudaMemsetAsync(ring, 0, (size_t)2 * cap * sizeof(double), s->stream), "ring memset");
+  // undrained steps keep their values: step tt lives in slot tt % capacity
+  const int64_t t1 = s->t_host;
+  const int64_t t0 = std::max(s->drained, t1 - s->ring_cap);
+  for (int64_t tt = t0; tt < t1;) {
+    const int64_t a_off = tt % s->ring_cap, b_off = tt % cap;
+    const int64_t run = std::min({t1 - tt, s->ring_cap - a_off, cap - b_off});
+    ck(cudaMemcpyAsync(ring + 2 * b_off, s->ring + 2 * a_off, (size_t)run * 16,
+                       cudaMemcpyDeviceToDevice, s->stream), "ring copy");
+    tt += run;
+  }
+  ck(cudaStreamSynchronize(s->stream), "ring sync");
+  double* old = s->ring;
+  s->owned.erase(std::remove(s->owned.begin(), s->owned.end(), (void*)old), s->owned.end());
+  dev_free_raw(a, old);
+  s->ring = ring;
+  s->ring_cap = cap;
+  s->version++;   // every launch table holding the sim takes the new ring
+}
+
 void* dev_alloc_raw(const lbm_allocator* a, size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
@@ -491,9 +530,14 @@ void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single) {
     most = std::max(most, g.max_blocks_v[v]);
   }
   int strips1 = 0;   // strips at one row per strip: the most any tiling launches
-  for (const lbm_sim* s : sims) strips1 += step_strips(s->nx, s->ny, 1);
-  // the dynamic staged variant writes one partial per strip and consumer warp
-  g.partial_stride = std::max(most, kPartialsPerStrip * strips1);
+  int strips2 = 0;   // strips at two rows, the least a staged variant takes
+  for (const lbm_sim* s : sims) {
+    strips1 += step_strips(s->nx, s->ny, 1);
+    strips2 += step_strips(s->nx, s->ny, 2);
+  }
+  // one partial per block (at most one block per strip), or, in the dynamic
+  // staged variant, one per strip and consumer warp
+  g.partial_stride = std::max({most, strips1, kPartialsPerStrip * strips2});
   auto alloc = [&](size_t bytes) {
     void* p = dev_alloc_raw(a, bytes);
     g.owned.push_back(p);
@@ -558,6 +602,14 @@ void sim_settle(lbm_sim* s) {
 void group_step(Group& g, int64_t n) {
   if (n <= 0) return;
   check_lockstep(g);
+  {
+    // automatic force rings grow before the run (not inside a caller's stream
+    // capture, where nothing may be allocated: there the oldest entries go)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    ck(cudaStreamIsCapturing(g.stream, &cs), "capture query");
+    if (cs == cudaStreamCaptureStatusNone)
+      for (lbm_sim* s : g.sims) sim_reserve_ring(s, n);
+  }
   // a member last stepped by another group: settle that group's forces first
   for (lbm_sim* s : g.sims)
     if (s->last_group && s->last_group != &g) {
@@ -587,7 +639,10 @@ void group_step(Group& g, int64_t n) {
     // steps that may run before the next capture
     const int64_t room = dcap <= 0 ? n : std::min<int64_t>(n, dcap);
     if (use_graphs && dcap != 0 && room >= kMinGraphChunk) {
-      const int64_t len = std::min<int64_t>(room, kGraphChunk);
+      // chunk lengths are powers of two (32, 16, 8, 4), so a run of any
+      // length replays graphs that earlier runs already instantiated
+      int64_t len = kGraphChunk;
+      while (len > room) len >>= 1;
       cudaGraphExec_t ex = chunk_graph(g, len, q);
       group_finalize(g);
       launch_set_t(g.t_base, t, g.stream);
@@ -621,17 +676,20 @@ void group_set_tiling(Group& g, int rows, int variant) {
 float group_autotune(Group& g, int steps, int64_t flush_bytes) {
   for (lbm_sim* s : g.sims) sim_settle(s);
   check_lockstep(g);
+  // the timed steps write forces past the undrained ones: make room first
+  for (lbm_sim* s : g.sims) sim_reserve_ring(s, steps + 2);
   ck(cudaStreamSynchronize(g.stream), "sync");
   const size_t nsims = g.sims.size();
+  // scratch from the members' allocator
+  const lbm_allocator* ta = g.sims[0]->have_alloc ? &g.sims[0]->alloc : nullptr;
   std::vector<void*> snaps(nsims, nullptr);
   void* flush = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto cleanup = [&]() {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    for (void* p : snaps)
-      if (p) cudaFree(p);
-    if (flush) cudaFree(flush);
+    for (void* p : snaps) dev_free_raw(ta, p);
+    dev_free_raw(ta, flush);
   };
   try {
     struct Saved { int cur; int64_t t, drained; unsigned long long fb; int st; lbm::Group* lg; };
@@ -639,7 +697,7 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
     for (size_t k = 0; k < nsims; ++k) {
       lbm_sim* s = g.sims[k];
       const size_t bytes = ((size_t)9 * s->plane + 256) * s->elem;
-      ck(cudaMalloc(&snaps[k], bytes), "autotune snapshot");
+      snaps[k] = dev_alloc_raw(ta, bytes);
       ck(cudaMemcpyAsync(snaps[k], state_alloc(s), bytes, cudaMemcpyDeviceToDevice, g.stream),
          "snapshot");
       saved[k].cur = s->cur;
@@ -649,7 +707,7 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
       ck(cudaMemcpyAsync(&saved[k].fb, s->nn_fallbacks, 8, cudaMemcpyDeviceToHost, g.stream), "snap");
       ck(cudaMemcpyAsync(&saved[k].st, s->status, 4, cudaMemcpyDeviceToHost, g.stream), "snap");
     }
-    if (flush_bytes > 0) ck(cudaMalloc(&flush, (size_t)flush_bytes), "autotune flush buffer");
+    if (flush_bytes > 0) flush = dev_alloc_raw(ta, (size_t)flush_bytes);
     ck(cudaEventCreate(&e0), "event");
     ck(cudaEventCreate(&e1), "event");
     ck(cudaStreamSynchronize(g.stream), "sync");

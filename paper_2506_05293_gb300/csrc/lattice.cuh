@@ -123,10 +123,10 @@ __device__ __forceinline__ void collide_bgk(R h[9], R omega, R& drho_out, R& ux_
 
 // MRT with Lallemand & Luo's orthogonal basis (rho, e, eps, jx, qx, jy, qy,
 // pxx, pxy).  Only the six non-conserved moments of the non-equilibrium part
-// n = h - h^eq relax: h* = h - M^-1 S M n, and M^-1 = M^T diag(1 / |row_k|^2)
-// with |row|^2 = (9, 36, 36, 6, 12, 6, 12, 4, 4).
+// n = h - h^eq relax, each at its own rate: h* = h - M^-1 S M n, and
+// M^-1 = M^T diag(1 / |row_k|^2) with |row|^2 = (9, 36, 36, 6, 12, 6, 12, 4, 4).
 template <typename R>
-struct MrtRates { R se, seps, sq, snu; };
+struct MrtRates { R se, seps, sqx, sqy, snxx, snxy; };
 
 template <typename R>
 __device__ __forceinline__ void collide_mrt(R h[9], const MrtRates<R>& s, R& drho_out, R& ux_out,
@@ -151,10 +151,10 @@ __device__ __forceinline__ void collide_mrt(R h[9], const MrtRates<R>& s, R& drh
   // relaxed amounts divided by the row norms
   const R de = s.se * m_e * (R(1) / R(36));
   const R deps = s.seps * m_eps * (R(1) / R(36));
-  const R dqx = s.sq * m_qx * (R(1) / R(12));
-  const R dqy = s.sq * m_qy * (R(1) / R(12));
-  const R dpxx = s.snu * m_pxx * R(0.25);
-  const R dpxy = s.snu * m_pxy * R(0.25);
+  const R dqx = s.sqx * m_qx * (R(1) / R(12));
+  const R dqy = s.sqy * m_qy * (R(1) / R(12));
+  const R dpxx = s.snxx * m_pxx * R(0.25);
+  const R dpxy = s.snxy * m_pxy * R(0.25);
   // h* = h - M^T d (columns of M)
   h[0] -= R(-4) * de + R(4) * deps;
   h[1] -= -de - R(2) * deps - R(2) * dqx + dpxx;

@@ -162,7 +162,11 @@ __global__ void noalloc_reduce_kernel(const double* partials, int n, double* for
   }
 }
 
-// Device address of g_noalloc_partials, looked up once per device.
+// Device address of g_noalloc_partials per device, as last looked up.  It is
+// looked up again on every call made outside a stream capture (a cheap host
+// call), so a context that was reset or replaced since is never served a
+// stale address; inside a capture, where a first lookup could load the
+// module, the address of the last call on that device is used.
 std::mutex g_setup_mutex;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
@@ -190,6 +194,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const float* src, 
   if (!(cfg->tau > 0.5) || !std::isfinite(cfg->tau)) return bad(LBM_ERR_ARG, "tau must be > 1/2");
   if (cfg->collision != LBM_BGK && cfg->collision != LBM_MRT)
     return bad(LBM_ERR_ARG, "unknown collision");
+  if (!mrt_rates_valid(*cfg)) return bad(LBM_ERR_ARG, "MRT rates must lie in [0, 2)");
   if (!(std::fabs(cfg->u_in) < 1.0)) return bad(LBM_ERR_ARG, "|u_in| must be < 1");
   if (!(cfg->rho_out > 0.0)) return bad(LBM_ERR_ARG, "rho_out must be > 0");
   if (t < 0) return bad(LBM_ERR_ARG, "t must be >= 0");
@@ -204,15 +209,24 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const float* src, 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return bad(LBM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return bad(LBM_ERR_UNSUPPORTED, "device index out of range");
+  cudaStream_t st = (cudaStream_t)cfg->stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess)
+    return bad(LBM_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
       if (e != cudaSuccess || !ptr)
         return bad(LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_scratch_ptr[dev] = static_cast<double*>(ptr);
+    } else if (!g_scratch_ptr[dev]) {
+      return bad(LBM_ERR_STATE,
+                 "the first lbm_step_noalloc call on a device must come before any stream "
+                 "capture (it looks up the scratch array's device address)");
     }
     scratch = g_scratch_ptr[dev];
   }
@@ -227,14 +241,10 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const float* src, 
   p.omega = (float)(1.0 / cfg->tau);
   p.u_in = (float)cfg->u_in;
   p.rho_out = (float)cfg->rho_out;
-  bool any = false;
-  for (int k = 0; k < 9; ++k) any |= cfg->mrt_rates[k] != 0.0;
-  if (any) {
-    p.mrt = {(float)cfg->mrt_rates[1], (float)cfg->mrt_rates[2], (float)cfg->mrt_rates[4],
-             (float)(cfg->mrt_rates[7] != 0.0 ? cfg->mrt_rates[7] : 1.0 / cfg->tau)};
-  } else {
-    p.mrt = {1.f, 1.f, 1.f, (float)(1.0 / cfg->tau)};
-  }
+  double rates[6];
+  mrt_rates_of(*cfg, rates);
+  p.mrt = {(float)rates[0], (float)rates[1], (float)rates[2],
+           (float)rates[3], (float)rates[4], (float)rates[5]};
   p.v_amp = cfg->v_pert_amp;
   p.u_in_d = cfg->u_in;
   p.ramp_steps = cfg->ramp_steps;
@@ -244,7 +254,6 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config* cfg, const float* src, 
   p.t = t;
   p.partials = scratch;
   p.force = force;
-  cudaStream_t st = (cudaStream_t)cfg->stream;
   noalloc_step_kernel<<<(unsigned)strips, 128, 0, st>>>(p);
   noalloc_reduce_kernel<<<1, 128, 0, st>>>(scratch, (int)strips, force);
   e = cudaGetLastError();

@@ -29,8 +29,8 @@ struct Member {
   const uint8_t* links;   // per node: bit i-1 set for a counted link in direction i (a solid
                           // node: to the fluid node s - c_i; a fluid node: to the solid x + c_i)
   const uint32_t* near_bits;   // fluid nodes with a counted link (layout of solid_bits)
-  double omega, mrt_se, mrt_seps, mrt_sq, mrt_snu, u_in, v_amp, rho_out;
-  float omega_f, mrt_f[4], u_in_f, rho_out_f;   // FP32 copies for the FP32/FP16 kernels
+  double omega, mrt[6], u_in, v_amp, rho_out;   // mrt: rates of e, eps, qx, qy, pxx, pxy
+  float omega_f, mrt_f[6], u_in_f, rho_out_f;   // FP32 copies for the FP32/FP16 kernels
   uint64_t seed;
   int64_t ramp_steps;     // > 0: inlet velocity u_in min(1, (t+1)/ramp_steps)
   int32_t east_mode;      // EastMode
@@ -153,14 +153,17 @@ __host__ __device__ __forceinline__ int64_t pop_offset(const PopMap& pm, int i, 
   return (int64_t)i * plane + (int64_t)y * pitch + x;
 }
 
+// rows [y0, y0 + rows) of the lattice (rows < 0: to the last row); the dense
+// field and population arrays hold those rows only
 void launch_init_equilibrium(int prec, void* dst, int nx, int ny, int64_t pitch, int64_t plane,
                              const double* rho, const double* ux, const double* uy,
-                             cudaStream_t s, PopMap pm = PopMap{});
+                             cudaStream_t s, PopMap pm = PopMap{}, int y0 = 0, int rows = -1);
 void launch_export(int prec, const void* src, int nx, int ny, int64_t pitch, int64_t plane,
                    double* f_out, double* rho, double* ux, double* uy, cudaStream_t s,
-                   PopMap pm = PopMap{});
+                   PopMap pm = PopMap{}, int y0 = 0, int rows = -1);
 void launch_import(int prec, void* dst, int nx, int ny, int64_t pitch, int64_t plane,
-                   const double* f_in, cudaStream_t s, PopMap pm = PopMap{});
+                   const double* f_in, cudaStream_t s, PopMap pm = PopMap{}, int y0 = 0,
+                   int rows = -1);
 void launch_mass(int prec, const void* src, int nx, int ny, int64_t pitch, int64_t plane,
                  double* partials, int n_partials, double* out, cudaStream_t s,
                  PopMap pm = PopMap{});
@@ -217,6 +220,33 @@ cudaError_t launch_train(const TrainParams& p, int cluster, cudaStream_t s);
 
 // message returned by lbm_last_error() on this thread
 void set_last_error(const std::string& msg);
+
+// The six relaxed MRT rates (e, eps, qx, qy, pxx, pxy) of a config: all nine
+// entries zero gives e, eps, q rates 1 and stress rates 1/tau; otherwise
+// entries 1, 2, 4, 6 are taken as given and the stress rates 7, 8 default to
+// 1/tau where they are zero.
+inline bool mrt_rates_valid(const lbm_config& c) {
+  for (int k = 0; k < 9; ++k)
+    if (!(c.mrt_rates[k] >= 0.0 && c.mrt_rates[k] < 2.0)) return false;   // NaN fails too
+  return true;
+}
+inline void mrt_rates_of(const lbm_config& c, double out[6]) {
+  const double* r = c.mrt_rates;
+  bool any = false;
+  for (int k = 0; k < 9; ++k) any |= r[k] != 0.0;
+  const double snu = 1.0 / c.tau;
+  if (!any) {
+    out[0] = out[1] = out[2] = out[3] = 1.0;
+    out[4] = out[5] = snu;
+    return;
+  }
+  out[0] = r[1];
+  out[1] = r[2];
+  out[2] = r[4];
+  out[3] = r[6];
+  out[4] = r[7] != 0.0 ? r[7] : snu;
+  out[5] = r[8] != 0.0 ? r[8] : snu;
+}
 
 }  // namespace lbm
 
@@ -288,8 +318,10 @@ struct lbm_sim {
   std::vector<uint8_t> solid_tile_rows;   // per 128-column tile and row: holds a counted solid
   double* ring = nullptr;
   int64_t ring_cap = 0;
+  bool ring_auto = false;            // force_capacity 0: the ring grows on demand
   int* status = nullptr;
-  double* scratch_fields = nullptr;  // 9 * ny * nx doubles (import/export)
+  double* scratch_fields = nullptr;  // import/export rows, allocated at first use:
+  int64_t scratch_doubles = 0;       // min(9 nx ny, about 8 Mi) doubles
   double* scratch_sums = nullptr;    // ny doubles (mass rows) + 1 (total)
   unsigned long long* nn_fallbacks = nullptr;
   int64_t t_host = 0;
@@ -326,6 +358,11 @@ namespace lbm {
 // group.cu
 void* dev_alloc_raw(const lbm_allocator* a, size_t bytes);
 void dev_free_raw(const lbm_allocator* a, void* p);
+// the process-wide default allocator (lbm_set_default_allocator); false: none
+bool default_allocator(lbm_allocator* out);
+void set_default_allocator(const lbm_allocator* a);
+// grow an automatic force ring so that n more steps overwrite no undrained force
+void sim_reserve_ring(lbm_sim* s, int64_t n);
 void group_init(Group& g, const std::vector<lbm_sim*>& sims, bool single);
 void group_release(Group& g);
 void group_clear_graphs(Group& g);

@@ -184,14 +184,17 @@ void launch_geometry_prep(const uint8_t* kind, int nx, int ny, int x_periodic, u
 }
 
 // ---- initialisation, import and export --------------------------------------
+// Each works on rows [y0, y0 + rows) of the lattice; the dense host-side
+// arrays (fields, or populations [9][rows][nx]) hold those rows only, so the
+// host can stream a large lattice through a bounded scratch buffer.
 template <typename S>
 __global__ void init_eq_kernel(S* dst, int nx, int ny, int64_t pitch, int64_t plane,
                                const double* rho, const double* ux, const double* uy,
-                               PopMap pm) {
+                               PopMap pm, int y0) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
+  const int y = y0 + (int)blockIdx.y;
   if (x >= nx) return;
-  const int64_t c = (int64_t)y * nx + x;
+  const int64_t c = (int64_t)blockIdx.y * nx + x;
   const double r = rho ? rho[c] : 1.0;
   const double u = ux ? ux[c] : 0.0;
   const double v = uy ? uy[c] : 0.0;
@@ -202,25 +205,31 @@ __global__ void init_eq_kernel(S* dst, int nx, int ny, int64_t pitch, int64_t pl
 
 void launch_init_equilibrium(int prec, void* dst, int nx, int ny, int64_t pitch, int64_t plane,
                              const double* rho, const double* ux, const double* uy,
-                             cudaStream_t s, PopMap pm) {
-  dim3 grid((nx + 127) / 128, ny);
+                             cudaStream_t s, PopMap pm, int y0, int rows) {
+  if (rows < 0) rows = ny - y0;
+  if (rows <= 0) return;
+  dim3 grid((nx + 127) / 128, rows);
   if (prec == LBM_FP64)
-    init_eq_kernel<double><<<grid, 128, 0, s>>>((double*)dst, nx, ny, pitch, plane, rho, ux, uy, pm);
+    init_eq_kernel<double><<<grid, 128, 0, s>>>((double*)dst, nx, ny, pitch, plane, rho, ux, uy,
+                                                pm, y0);
   else if (prec == LBM_FP32)
-    init_eq_kernel<float><<<grid, 128, 0, s>>>((float*)dst, nx, ny, pitch, plane, rho, ux, uy, pm);
+    init_eq_kernel<float><<<grid, 128, 0, s>>>((float*)dst, nx, ny, pitch, plane, rho, ux, uy,
+                                               pm, y0);
   else
-    init_eq_kernel<__half><<<grid, 128, 0, s>>>((__half*)dst, nx, ny, pitch, plane, rho, ux, uy, pm);
+    init_eq_kernel<__half><<<grid, 128, 0, s>>>((__half*)dst, nx, ny, pitch, plane, rho, ux, uy,
+                                                pm, y0);
 }
 
 // f_i = h_i + w_i into a dense double[9][ny][nx]; moments into rho/ux/uy.
 template <typename S>
 __global__ void export_kernel(const S* src, int nx, int ny, int64_t pitch, int64_t plane,
-                              double* f_out, double* rho, double* ux, double* uy, PopMap pm) {
+                              double* f_out, double* rho, double* ux, double* uy, PopMap pm,
+                              int y0) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
+  const int y = y0 + (int)blockIdx.y;
   if (x >= nx) return;
-  const int64_t c = (int64_t)y * nx + x;
-  const int64_t n = (int64_t)nx * ny;
+  const int64_t c = (int64_t)blockIdx.y * nx + x;
+  const int64_t n = (int64_t)nx * gridDim.y;
   double f[9];
   for (int i = 0; i < 9; ++i) {
     f[i] = (double)to_r<double>(src[pop_offset(pm, i, x, y, nx, ny, pitch, plane)]) +
@@ -240,40 +249,44 @@ __global__ void export_kernel(const S* src, int nx, int ny, int64_t pitch, int64
 
 void launch_export(int prec, const void* src, int nx, int ny, int64_t pitch, int64_t plane,
                    double* f_out, double* rho, double* ux, double* uy, cudaStream_t s,
-                   PopMap pm) {
-  dim3 grid((nx + 127) / 128, ny);
+                   PopMap pm, int y0, int rows) {
+  if (rows < 0) rows = ny - y0;
+  if (rows <= 0) return;
+  dim3 grid((nx + 127) / 128, rows);
   if (prec == LBM_FP64)
     export_kernel<double><<<grid, 128, 0, s>>>((const double*)src, nx, ny, pitch, plane, f_out,
-                                               rho, ux, uy, pm);
+                                               rho, ux, uy, pm, y0);
   else if (prec == LBM_FP32)
     export_kernel<float><<<grid, 128, 0, s>>>((const float*)src, nx, ny, pitch, plane, f_out, rho,
-                                              ux, uy, pm);
+                                              ux, uy, pm, y0);
   else
     export_kernel<__half><<<grid, 128, 0, s>>>((const __half*)src, nx, ny, pitch, plane, f_out,
-                                               rho, ux, uy, pm);
+                                               rho, ux, uy, pm, y0);
 }
 
 template <typename S>
 __global__ void import_kernel(S* dst, int nx, int ny, int64_t pitch, int64_t plane,
-                              const double* f_in, PopMap pm) {
+                              const double* f_in, PopMap pm, int y0) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
+  const int y = y0 + (int)blockIdx.y;
   if (x >= nx) return;
-  const int64_t c = (int64_t)y * nx + x;
-  const int64_t n = (int64_t)nx * ny;
+  const int64_t c = (int64_t)blockIdx.y * nx + x;
+  const int64_t n = (int64_t)nx * gridDim.y;
   for (int i = 0; i < 9; ++i)
     dst[pop_offset(pm, i, x, y, nx, ny, pitch, plane)] = from_r<S>(f_in[i * n + c] - wgt<double>(i));
 }
 
 void launch_import(int prec, void* dst, int nx, int ny, int64_t pitch, int64_t plane,
-                   const double* f_in, cudaStream_t s, PopMap pm) {
-  dim3 grid((nx + 127) / 128, ny);
+                   const double* f_in, cudaStream_t s, PopMap pm, int y0, int rows) {
+  if (rows < 0) rows = ny - y0;
+  if (rows <= 0) return;
+  dim3 grid((nx + 127) / 128, rows);
   if (prec == LBM_FP64)
-    import_kernel<double><<<grid, 128, 0, s>>>((double*)dst, nx, ny, pitch, plane, f_in, pm);
+    import_kernel<double><<<grid, 128, 0, s>>>((double*)dst, nx, ny, pitch, plane, f_in, pm, y0);
   else if (prec == LBM_FP32)
-    import_kernel<float><<<grid, 128, 0, s>>>((float*)dst, nx, ny, pitch, plane, f_in, pm);
+    import_kernel<float><<<grid, 128, 0, s>>>((float*)dst, nx, ny, pitch, plane, f_in, pm, y0);
   else
-    import_kernel<__half><<<grid, 128, 0, s>>>((__half*)dst, nx, ny, pitch, plane, f_in, pm);
+    import_kernel<__half><<<grid, 128, 0, s>>>((__half*)dst, nx, ny, pitch, plane, f_in, pm, y0);
 }
 
 // ---- total mass: per-row partial sums, then one block sums the rows --------

@@ -78,14 +78,14 @@ template <> struct Scalars<float> {
   MrtRates<float> mrt;
   __device__ explicit Scalars(const Member& m)
       : omega(m.omega_f), u_in(m.u_in_f), rho_out(m.rho_out_f),
-        mrt{m.mrt_f[0], m.mrt_f[1], m.mrt_f[2], m.mrt_f[3]} {}
+        mrt{m.mrt_f[0], m.mrt_f[1], m.mrt_f[2], m.mrt_f[3], m.mrt_f[4], m.mrt_f[5]} {}
 };
 template <> struct Scalars<double> {
   double omega, u_in, rho_out;
   MrtRates<double> mrt;
   __device__ explicit Scalars(const Member& m)
       : omega(m.omega), u_in(m.u_in), rho_out(m.rho_out),
-        mrt{m.mrt_se, m.mrt_seps, m.mrt_sq, m.mrt_snu} {}
+        mrt{m.mrt[0], m.mrt[1], m.mrt[2], m.mrt[3], m.mrt[4], m.mrt[5]} {}
 };
 
 // Programmatic dependent launch: a step kernel lets the next one be
@@ -133,14 +133,22 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 constexpr uint64_t kFlagWaitNs = 2000000000ull;   // a flag wait gives up after 2 s
 
+// A wait that has not been satisfied at once also gives up as soon as its
+// member's status word holds DEV_TIMEOUT: once one wait of a launch has run
+// out, the flags it depends on cannot all arrive, and every further block
+// would otherwise spend its own 2 s before the host can see the fault.
+__device__ __forceinline__ bool timed_out_already(const int* status) {
+  return (*reinterpret_cast<const volatile int*>(status) & DEV_TIMEOUT) != 0;
+}
+
 // Bounded wait until *ptr >= v; false if it gave up.
-__device__ inline bool wait_at_least(const int64_t* ptr, int64_t v) {
+__device__ inline bool wait_at_least(const int64_t* ptr, int64_t v, const int* status) {
   if (ld_acquire(ptr) >= v) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t k = 0; k < (1u << 24); ++k) {
     __nanosleep(200);
     if (ld_acquire(ptr) >= v) return true;
-    if (global_ns() - t0 > kFlagWaitNs) return false;
+    if (global_ns() - t0 > kFlagWaitNs || timed_out_already(status)) return false;
   }
   return false;
 }
@@ -175,7 +183,7 @@ __device__ inline bool wait_strip_neighbours(const StepParams& p, const Member& 
       return true;
     }
     if (k == 0) t0 = global_ns();
-    else if (global_ns() - t0 > kFlagWaitNs) break;
+    else if (global_ns() - t0 > kFlagWaitNs || timed_out_already(m.status)) break;
     __nanosleep(200);
   }
   __threadfence();
@@ -843,7 +851,7 @@ __device__ inline bool wait_east(const StepParams& p, const Member& m, int a, in
       return true;
     }
     if (k == 0) t0 = global_ns();
-    else if (global_ns() - t0 > kFlagWaitNs) break;
+    else if (global_ns() - t0 > kFlagWaitNs || timed_out_already(m.status)) break;
     __nanosleep(200);
   }
   __threadfence();
@@ -1037,7 +1045,7 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
   // the partial slot of step t last held step t-2's partials; they must be
   // reduced (by a block of launch t-1) before they are overwritten
   if (p.strip_done && slot >= 0 && threadIdx.x == 0 &&
-      !wait_at_least(p.reduced + (p.n_members == 1 ? 0 : p.strip_member[sgb]), t - 1))
+      !wait_at_least(p.reduced + (p.n_members == 1 ? 0 : p.strip_member[sgb]), t - 1, m.status))
     atomicOr(m.status, DEV_TIMEOUT);
   write_partial(p, t, slot, fx, fy, touched, bad, m.status);
   if (p.strip_done) {

@@ -13,6 +13,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from synth import convected_vortex, cylinder_mask
+
 from . import api as L
 
 
@@ -64,15 +66,8 @@ class Study:
         return 3.0 * self.u * self.D / self.re + 0.5
 
 
-def cylinder_kind(nx, ny, xc, yc, d):
-    """Cell kinds of a cylinder of diameter d at (xc, yc): a node is solid iff
-    its squared distance to the centre is at most (d/2)^2."""
-    y, x = np.mgrid[0:ny, 0:nx]
-    return (((x - xc) ** 2 + (y - yc) ** 2) <= (d / 2.0) ** 2).astype(np.uint8)
-
-
 def make_sim(st: Study, nx):
-    kind = cylinder_kind(nx, st.ny, st.centre_d * st.D, st.ny / 2.0, st.D)
+    kind = cylinder_mask(nx, st.ny, st.centre_d * st.D, st.ny / 2.0, st.D)
     cfg = L.lbm_config_default(nx=nx, ny=st.ny, tau=st.tau, collision=st.collision,
                                precision=st.precision, u_in=st.u, v_pert_amp=st.v_pert_amp,
                                seed=st.seed, stream=st.stream)
@@ -276,7 +271,7 @@ class SnapshotStudy:
 
 
 def _cyl_sim(st, nx, tau, u, stream):
-    kind = cylinder_kind(nx, st.ny, st.centre_d * st.D, st.ny / 2.0, st.D)
+    kind = cylinder_mask(nx, st.ny, st.centre_d * st.D, st.ny / 2.0, st.D)
     cfg = L.lbm_config_default(nx=nx, ny=st.ny, tau=tau, collision=st.collision,
                                precision=st.precision, u_in=u, v_pert_amp=st.v_pert_amp,
                                seed=st.seed, stream=stream)
@@ -437,17 +432,10 @@ class VortexCase:
 
 
 def vortex_fields(case: VortexCase, nx):
-    """Isothermal vortex of Sec. 4.1 (read with a dimensionless Gaussian,
-    gamma = 2, C_v = c_s^2) on a lattice nx wide, centred at the case's x0."""
-    y, x = np.mgrid[0:case.ny, 0:nx].astype(np.float64)
-    x0, y0, rc = case.x0_frac * case.nx, case.ny / 2.0, case.rc_frac * case.ny
-    r2 = (x - x0) ** 2 + (y - y0) ** 2
-    g = np.exp(-r2 / (2.0 * rc * rc))
-    bu = case.strength * CS
-    u = case.u0 - bu * (y - y0) / rc * g
-    v = bu * (x - x0) / rc * g
-    rho = 1.0 - bu * bu / (2.0 * CS * CS) * np.exp(-r2 / (rc * rc))
-    return rho, u, v
+    """Isothermal vortex of Sec. 4.1 on a lattice nx wide, centred at the
+    case's x0 (a fraction of the truncated lattice's width)."""
+    return convected_vortex(nx, case.ny, case.x0_frac * case.nx, case.ny / 2.0,
+                            case.rc_frac * case.ny, case.strength * CS, case.u0)
 
 
 def vortex_sim(case: VortexCase, nx, outflow, stream=0, precision="fp32"):

@@ -149,3 +149,25 @@ def test_tuner_training_rejects_bad_arguments_before_touching_the_device(L):
             L.lbm_cbc_tuner_train(bank, 20, 4, 0.6, 0.5, 0.1, 0.1, [0, 1], [2, 2], net, order,
                                   batch, lr=lr)
         assert ei.value.status == 1
+
+
+def test_default_allocator_needs_both_callbacks(L):
+    """lbm_set_default_allocator copies a complete allocator or clears it
+    (NULL); one without alloc or free is rejected on the host."""
+    lib = L._lib.load()
+    T = L._lib.LbmAllocator
+    free_only = T()
+    free_only.free = T._fields_[1][1](lambda p, c: None)
+    assert lib.lbm_set_default_allocator(ctypes.byref(free_only)) == 1
+    assert "alloc and free" in lib.lbm_last_error().decode()
+    assert lib.lbm_set_default_allocator(None) == 0
+    L.use_torch_allocator(True)
+
+
+def test_create_rejects_mrt_rates_outside_their_range(L):
+    for bad in (float("nan"), -0.1, 2.0):
+        cfg = L.lbm_config_default(nx=32, ny=16, collision=1,
+                                   mrt_rates=[0, 1, 1, 0, 1, 0, bad, 1.5, 1.5])
+        with pytest.raises(L.LbmError) as ei:
+            L.lbm_create(cfg)
+        assert ei.value.status == 1

@@ -6,6 +6,7 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 import bench
 
@@ -76,3 +77,29 @@ def test_traffic_lookup_follows_the_summary_and_its_source_hash():
         # the committed captures show no wasted re-reads: the measured traffic
         # stays at or below the algorithmic 72 B per node
         assert value <= 72 * bench.workload_nodes(wl)
+
+
+def test_graph_chunks_and_launch_count():
+    # runs are cut into chunks of 32, 16, 8 or 4 steps; 0-3 steps stay direct
+    assert bench.graph_chunks(20) == (2, 0)          # 16 + 4
+    assert bench.graph_chunks(2000) == (63, 0)       # 62 x 32 + 16
+    assert bench.graph_chunks(37) == (2, 1)          # 32 + 4 + 1
+    assert bench.graph_chunks(3) == (0, 3)
+    assert bench.step_launches(20) == 24
+    assert bench.step_launches(2000) == 2126
+
+
+def test_both_arms_print_the_same_config():
+    a = bench.workload_config("cylinder_sweep_D40", "fp32", "ab", 1)
+    b = bench.workload_config("cylinder_sweep_D40", "fp32", "ab", 1)
+    assert a == b and a["nodes"] == 6963200 and a["working_set_bytes"] == 72 * 6963200
+    assert "no flush" in a["l2"]
+    small = bench.workload_config("cylinder_D40_L32D_Re100", "fp32", "ab", 1)
+    assert "flushed" in small["l2"]
+
+
+def test_all_core_oracle_leg_runs_every_worker():
+    v, dt = bench.oracle_all_cores("cylinder_sweep_D40", 1, 2)
+    # two workers, one 480 x 640 and one 640 x 640 lattice, one step each
+    assert v > 0 and dt > 0
+    assert v * dt * 1e9 == pytest.approx(480 * 640 + 640 * 640)

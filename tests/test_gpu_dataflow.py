@@ -304,3 +304,31 @@ def test_a_flag_that_nothing_sets_times_out(L):
     assert np.array_equal(L.lbm_get_populations(a), L.lbm_get_populations(b))
     for x in (a, b):
         L.lbm_destroy(x)
+
+
+def test_later_waves_give_up_at_once_after_a_timeout(L):
+    """A launch with several waves of blocks (more strips than resident
+    blocks) whose flags are all held back: the first wave's waits run out after
+    2 s and latch LBM_ERR_TIMEOUT; the blocks of later waves see the latched
+    status and give up at their first unsatisfied poll instead of waiting 2 s
+    each, so the step ends in about 2 s, not 2 s per wave."""
+    import time
+    nx, ny = 1024, 4096               # 8 x 512 strips of 8 rows: several waves on 152 SMs
+    s = L.lbm_create(L.lbm_config_default(nx=nx, ny=ny, tau=0.7, precision="fp32",
+                                          x_periodic=1))
+    L.lbm_set_geometry(s, np.zeros((ny, nx), np.uint8))
+    L.lbm_init_equilibrium(s)
+    L.lbm_set_tiling(s, 8, 6)
+    L.lbm_step(s, 2)
+    L.lbm_sync(s)
+    L.lbm_debug_hold_dataflow(s, 1)
+    L.lbm_init_equilibrium(s)          # a rewind: the next launch resets the (held) flags
+    t0 = time.time()
+    L.lbm_step(s, 1)
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_sync(s)
+    dt = time.time() - t0
+    assert ei.value.status == 6
+    assert 1.5 < dt < 5.0, dt
+    L.lbm_debug_hold_dataflow(s, 0)
+    L.lbm_destroy(s)

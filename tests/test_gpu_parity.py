@@ -343,3 +343,30 @@ def test_inlet_ramp_fp64(L):
     g = _gpu_run(L, C1_KIND, 90, "fp64", ramp_steps=40, **kw)
     o = _oracle_run(C1_KIND, 90, u_ramp_steps=40, **kw)
     _assert_fp64(g, o, C1_KIND)
+
+
+# every one of the six relaxed MRT rates different: q_y != q_x and p_xy != p_xx
+MRT_RATES_ALL = [0.0, 1.1, 1.3, 0.0, 1.2, 0.0, 1.6, 1.0 / 0.62, 1.0 / 0.58]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mrt_with_nine_independent_rates(L, precision):
+    """lbm_config.mrt_rates is honoured entry by entry (the q_y and p_xy rates
+    independently of q_x and p_xx), as the oracle's diagonal S does."""
+    kind = add_walls(cylinder_mask(120, 50, 30, 25.3, 10))
+    init = random_smooth_state(120, 50, seed=21, amp_u=0.01, amp_rho=0.003)
+    init = (init[0], np.where(kind == 0, init[1] + 0.04, 0.0), init[2])
+    kw = dict(tau=0.6, u_in=0.04, v_pert_amp=1e-3, seed=4)
+    o = _oracle_run(kind, 300, init=init, collision="mrt", mrt_rates=np.array(MRT_RATES_ALL), **kw)
+    g = _gpu_run(L, kind, 300, precision, init=init, collision=1, mrt_rates=MRT_RATES_ALL, **kw)
+    if precision == "fp64":
+        _assert_fp64(g, o, kind)
+    else:
+        fl = kind == 0
+        assert (np.abs(g["rho"] - o["rho"])[fl] / o["rho"][fl]).max() < 1e-5
+        assert np.hypot(g["ux"] - o["ux"], g["uy"] - o["uy"])[fl].max() < 1e-4 * 0.04
+    # the same run with q_y, p_xy tied to q_x, p_xx is a different operator
+    tied = list(MRT_RATES_ALL)
+    tied[6], tied[8] = tied[4], tied[7]
+    o2 = _oracle_run(kind, 300, init=init, collision="mrt", mrt_rates=np.array(tied), **kw)
+    assert np.abs(o2["f"] - o["f"])[:, kind == 0].max() > 1e-6
