@@ -59,18 +59,14 @@ def _naca(aoa, nx=4000, ny=1600, chord=400, re_=1000.0, U=0.04):
                 outflow="zouhe")
 
 
-def _vortex_batch(n, seed=7, mach=0.1, re_=750.0):
+def _vortex_batch(n, seed=7, mach=0.1, re_=750.0, outflow="cbc"):
     """Convected-vortex lattices of uneven sizes: nx ~ U[128, 1024], ny ~ U[128, 512],
-    strength beta u0 / c_s ~ U[0.01, 0.1]; CBC outflow (sigma 0.25, kappa2 = Ma)."""
-    import numpy as np
-    rng = np.random.default_rng(seed)
-    out = []
-    for _ in range(n):
-        nx = int(rng.integers(128, 1025))
-        ny = int(rng.integers(128, 513))
-        out.append(dict(shape="vortex", nx=nx, ny=ny, strength=float(rng.uniform(0.01, 0.1)),
-                        mach=mach, Re=re_, U=mach * CS, collision="bgk", outflow="cbc"))
-    return out
+    strength beta u0 / c_s ~ U[0.01, 0.1]; CBC outflow (sigma 0.25, kappa2 = Ma),
+    or with outflow "cbc_tuned" the trained tuner of Sec. 4.2 in every lattice."""
+    from synth import vortex_batch_cases
+    return [dict(shape="vortex", nx=nx, ny=ny, strength=st, mach=mach, Re=re_, U=mach * CS,
+                 collision="bgk", outflow=outflow)
+            for nx, ny, st in vortex_batch_cases(n, seed)]
 
 
 CS = (1.0 / 3.0) ** 0.5
@@ -82,6 +78,7 @@ WORKLOADS = {
     "cylinder_D160_8192x4096": [_cyl(160, 25.6, 43.2, 100, "bgk")],
     "naca0012_4000x1600_aoa4": [_naca(4.0)],
     "vortex_batch_256": _vortex_batch(256),
+    "vortex_batch_256_tuned": _vortex_batch(256, outflow="cbc_tuned"),
 }
 
 
@@ -261,7 +258,9 @@ def _oracle_solver(wl, idx):
     m = ms[idx % len(ms)]
     kind, tau, init = member_geometry(m)
     extra = {}
-    if m["outflow"] == "cbc":
+    if m["outflow"] in ("cbc", "cbc_tuned"):
+        # the tuned lattices are sampled with the fixed setting (the tuner's few
+        # hundred operations per boundary node do not change the oracle's cost)
         extra = dict(outflow="cbc", cbc=cbc.CBCOutflow(sigma=0.25, kappa2=m["mach"],
                                                        mach=m["mach"]))
     s = lbm.Solver(lbm.Config(nx=m["nx"], ny=m["ny"], tau=tau, collision=m["collision"],
@@ -337,7 +336,7 @@ def cpu_oracle_sample(wl, steps, warmup=1):
         "for m in ms:\n"
         "    kind, tau, init = member_geometry(m)\n"
         "    extra = {}\n"
-        "    if m['outflow'] == 'cbc':\n"
+        "    if m['outflow'] in ('cbc', 'cbc_tuned'):\n"
         "        extra = dict(outflow='cbc', cbc=cbc.CBCOutflow(sigma=0.25, kappa2=m['mach'],"
         " mach=m['mach']))\n"
         "    s = lbm.Solver(lbm.Config(nx=m['nx'], ny=m['ny'], tau=tau, collision=m['collision'],"
@@ -464,7 +463,10 @@ class _Stepper:
             self.L.lbm_batch_destroy(self.batch)
 
 
-def _make_members(L, wl, prec, stream, layout="ab"):
+def _make_members(L, wl, prec, stream, layout="ab", tuner=None, outflow=None):
+    """Create the workload's lattices; tuner = (layers, act, in_mean, in_std,
+    sigma_max, kappa2_max) for "cbc_tuned" members; outflow overrides every
+    member's outflow ("zouhe", "cbc" or "cbc_tuned")."""
     sims, kinds, inits = [], [], []
     for m in WORKLOADS[wl]:
         kind, tau, init = member_geometry(m)
@@ -472,8 +474,13 @@ def _make_members(L, wl, prec, stream, layout="ab"):
                                    collision=m["collision"], u_in=m["U"], stream=stream,
                                    layout=layout)
         s = L.lbm_create(cfg)
-        if m["outflow"] == "cbc":
+        out = outflow or m["outflow"]
+        if out == "cbc":
             L.lbm_set_outflow_cbc(s, 0.25, m["mach"], m["mach"], 0.0)
+        elif out == "cbc_tuned":
+            layers, act, mean, std, smax, kmax = tuner
+            L.lbm_set_outflow_cbc(s, smax, kmax, m["mach"], 0.0, tuner=layers, act=act,
+                                  in_mean=mean, in_std=std)
         sims.append(s)
         kinds.append(kind)
         inits.append(init)
@@ -516,17 +523,21 @@ def accuracy_study():
         return {"error": f"{type(ex).__name__}: {ex}"}
 
 
-def tuner_study():
+def tuner_study(keep=None):
     """The CBC tuner trained through segments (Sec. 4.2) on the convected
     vortex: segment losses before and after training and of tuners frozen at
     fixed (sigma, kappa2), the summed L2 density error over 3000 steps for every
-    outflow, and the training's cost.  A failure is reported, not raised."""
+    outflow, and the training's cost.  A failure is reported, not raised.
+    keep (a dict, optional) receives the trained tuner under "tuner"."""
     try:
         import math
         from paper_2506_05293_gb300 import workflow
         st = workflow.TunerStudy()
         t0 = time.perf_counter()
         res = workflow.tuner_study(st)
+        if keep is not None:
+            keep["tuner"] = (res["layers"], st.act, res["in_mean"], res["in_std"],
+                             st.sigma_max, st.kappa2_max)
 
         def tot(d):
             return float(sum(d.values()))
@@ -545,6 +556,70 @@ def tuner_study():
                               f"{st.eval_every}",
                 "adam_steps": res["adam_steps"], "train_s": res["t_train_s"],
                 "ms_per_adam_step": 1e3 * res["t_train_s"] / max(1, res["adam_steps"]),
+                "wall_s": time.perf_counter() - t0}
+    except Exception as ex:   # reported, not fatal
+        return {"error": f"{type(ex).__name__}: {ex}"}
+
+
+def _ms_per_step(L, wl, prec, stream, rows, variant, steps, tuner=None, outflow=None):
+    """Mean step time of the workload's batch with every member's outflow set
+    to `outflow`, at a fixed tiling, over `steps` back-to-back steps after the
+    graphs are warm (CUDA events on the batch's stream)."""
+    import torch
+    sims, kinds, inits = _make_members(L, wl, prec, stream.cuda_stream, "ab", tuner, outflow)
+    for s, kind, init in zip(sims, kinds, inits):
+        L.lbm_set_geometry(s, kind)
+        L.lbm_init_equilibrium(s, *init)
+    b = L.lbm_batch_create(sims)
+    L.lbm_batch_set_tiling(b, rows, variant)
+    with torch.cuda.stream(stream):
+        L.lbm_batch_step(b, steps)
+        L.lbm_batch_step(b, steps)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.lbm_batch_step(b, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    L.lbm_batch_destroy(b)
+    for s in sims:
+        L.lbm_destroy(s)
+    return ms
+
+
+def tuned_batch_study(L, wl, prec, stream, rows, variant, tuner, steps=256):
+    """What the tuner costs inside the batch (the same lattices and tiling
+    with the trained tuner, with the fixed characteristic outflow and with
+    Zou & He), and the L2 density error of the three outflows against the 4x
+    longer references (every 500 steps up to 6000).  A failure is reported,
+    not raised."""
+    try:
+        import numpy as np
+        from paper_2506_05293_gb300 import workflow
+        cost = {o: _ms_per_step(L, wl, prec, stream, rows, variant, steps, tuner, o)
+                for o in ("cbc_tuned", "cbc", "zouhe")}
+        share = (cost["cbc_tuned"] - cost["cbc"]) / cost["cbc_tuned"]
+        boundary_nodes = sum(m["ny"] for m in WORKLOADS[wl])
+        t0 = time.perf_counter()
+        sizes = [(m["nx"], m["ny"], m["strength"]) for m in WORKLOADS[wl]]
+        steps_eval = list(range(500, 6001, 500))
+        err = workflow.vortex_batch_study(sizes, tuner, steps_eval, stream=stream.cuda_stream)
+        names = {"zouhe": "zouhe", "cbc_s0.25_k0.1": "cbc_fixed_s0.25_k0.1",
+                 "cbc_tuned_s1_k0.2": "cbc_tuned"}
+        out_err = {}
+        for k, v in err.items():
+            ok = ~np.isnan(v).any(axis=0)
+            out_err[names.get(k, k)] = {
+                "sum_over_steps_and_lattices": float(np.nansum(v)),
+                "mean_per_lattice_and_step": float(np.nanmean(v)),
+                "lattices_diverged": int((~ok).sum())}
+        return {"ms_per_step": cost, "tuner_share_of_step": share,
+                "boundary_nodes": boundary_nodes,
+                "l2_density_error": out_err,
+                "eval_steps": f"{steps_eval[0]}..{steps_eval[-1]} every 500",
+                "reference": "each lattice 4x longer in x, Zou & He outflow far away",
                 "wall_s": time.perf_counter() - t0}
     except Exception as ex:   # reported, not fatal
         return {"error": f"{type(ex).__name__}: {ex}"}
@@ -570,7 +645,16 @@ def run_ours(args):
     working_set = bpn * nodes // (2 if args.layout == "aa" else 1)
     flush_mode = working_set < L2_BYTES
     stream = torch.cuda.Stream()
-    sims, kinds, inits = _make_members(L, wl, prec, stream.cuda_stream, args.layout)
+    # lattices with the trained tuner: train it first (Sec. 4.2, a few seconds)
+    tuned = any(m["outflow"] == "cbc_tuned" for m in WORKLOADS[wl])
+    tuner, tuner_summary = None, None
+    if tuned:
+        keep = {}
+        tuner_summary = tuner_study(keep)
+        if "tuner" not in keep:
+            raise RuntimeError(f"tuner training failed: {tuner_summary}")
+        tuner = keep["tuner"]
+    sims, kinds, inits = _make_members(L, wl, prec, stream.cuda_stream, args.layout, tuner)
     for s, kind, init in zip(sims, kinds, inits):
         L.lbm_set_geometry(s, kind)
         L.lbm_init_equilibrium(s, *init)
@@ -661,7 +745,7 @@ def run_ours(args):
     # initial fields in from pinned host memory; 1000 steps of the batch; force
     # series and fields out
     e2e_steps = 1000
-    sims2, kinds2, inits2 = _make_members(L, wl, prec, stream.cuda_stream, args.layout)
+    sims2, kinds2, inits2 = _make_members(L, wl, prec, stream.cuda_stream, args.layout, tuner)
     pinned_in = []
     for kind, (r0, u0, v0) in zip(kinds2, inits2):
         k_p = torch.empty(kind.shape, dtype=torch.uint8, pin_memory=True).numpy()
@@ -706,9 +790,13 @@ def run_ours(args):
     cpu = None
     accuracy = None
     tuner = None
-    if world == 1 and not args.no_accuracy:
+    batch_study = None
+    if world == 1 and tuned:
+        batch_study = tuned_batch_study(L, wl, prec, stream, rows, variant, tuner)
+    if world == 1 and not args.no_accuracy and not tuned:
         accuracy = accuracy_study()
-    if world == 1 and not args.no_tuner:
+    tuner = tuner_summary
+    if world == 1 and not args.no_tuner and not tuned:
         tuner = tuner_study()
     if world == 1 and not args.no_cpu_baseline:
         # all host cores (the figure the line carries) and one thread beside it
@@ -752,6 +840,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "accuracy": accuracy,
         "cbc_tuner": tuner,
+        "tuned_batch": batch_study,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

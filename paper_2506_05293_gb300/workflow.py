@@ -643,9 +643,26 @@ def tuner_study(st: TunerStudy):
     steps = list(range(st.eval_every, st.eval_until + 1, st.eval_every))
     errors = vortex_study([c], outflows, steps, stream=stream)
     return {"before": before, "after": after, "fixed": fixed_losses, "log": log,
-            "errors": errors, "eval_steps": steps, "params": p, "in_mean": mean,
-            "in_std": std, "t_reference_s": t_ref, "t_train_s": t_train,
+            "errors": errors, "eval_steps": steps, "params": p, "layers": trained,
+            "in_mean": mean, "in_std": std, "t_reference_s": t_ref, "t_train_s": t_train,
             "adam_steps": t_adam}
+
+
+def vortex_batch_study(sizes, tuner, eval_steps, fixed=(0.25, None), stream=0,
+                       precision="fp32"):
+    """The batch of convected vortices (sizes = [(nx, ny, strength), ...],
+    Ma 0.1, Re 750) truncated at nx with Zou & He, with the characteristic
+    outflow at a fixed (sigma, kappa2) (kappa2 None = Ma) and with the trained
+    tuner in every lattice (tuner = (layers, act, in_mean, in_std, sigma_max,
+    kappa2_max)), each group one batch, against the batch of references
+    (4 x longer, Zou & He far away).  Returns, per outflow, the L2 density
+    error over each truncated lattice at each eval step, shape (steps, n)."""
+    cases = [VortexCase(nx, ny, st) for nx, ny, st in sizes]
+    sg, kp = fixed
+    kp = cases[0].mach if kp is None else kp
+    layers, act, mean, std, smax, kmax = tuner
+    outflows = ["zouhe", ("cbc", sg, kp), ("cbc", smax, kmax, (layers, act, mean, std))]
+    return vortex_study(cases, outflows, eval_steps, stream=stream, precision=precision)
 
 
 def _main(argv=None):

@@ -12,8 +12,8 @@ not count (channel walls).
 """
 from .geometry import cylinder_mask, naca0012_mask, naca0012_half_thickness, add_walls
 from .fields import (uniform_flow, random_smooth_state, convected_vortex,
-                     glorot_mlp, batch_order)
+                     vortex_batch_cases, glorot_mlp, batch_order)
 
 __all__ = ["cylinder_mask", "naca0012_mask", "naca0012_half_thickness", "add_walls",
-           "uniform_flow", "random_smooth_state", "convected_vortex", "glorot_mlp",
-           "batch_order"]
+           "uniform_flow", "random_smooth_state", "convected_vortex", "vortex_batch_cases",
+           "glorot_mlp", "batch_order"]

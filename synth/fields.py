@@ -45,6 +45,20 @@ def convected_vortex(nx, ny, x0, y0, rc, beta_u0, u0):
     return rho, u, v
 
 
+def vortex_batch_cases(n, seed=7):
+    """Sizes and strengths of a batch of convected-vortex lattices of uneven
+    sizes: nx ~ U[128, 1024], ny ~ U[128, 512] (integers, inclusive) and the
+    strength beta u0 / c_s ~ U[0.01, 0.1], drawn in that order per lattice.
+    Returns a list of (nx, ny, strength)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = int(rng.integers(128, 1025))
+        ny = int(rng.integers(128, 513))
+        out.append((nx, ny, float(rng.uniform(0.01, 0.1))))
+    return out
+
+
 def glorot_mlp(sizes, seed):
     """Glorot-uniform weights and zero biases for layer sizes [n_in, h1, ..., n_out];
     returns a list of (W (n_out, n_in), b) float64 arrays."""

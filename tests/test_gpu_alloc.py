@@ -181,7 +181,9 @@ def test_every_allocating_entry_point_reports_oom_and_leaks_nothing(L):
     L.lbm_set_default_allocator(inj.struct)
     try:
         nx, ny = 200, 64
-        cfg = L.lbm_config_default(nx=nx, ny=ny, precision="fp32", u_in=0.04)
+        stream = torch.cuda.Stream()        # batch members share one stream
+        cfg = L.lbm_config_default(nx=nx, ny=ny, precision="fp32", u_in=0.04,
+                                   stream=stream.cuda_stream)
 
         # lbm_create (populations, geometry, ring, group tables)
         n, s0 = _count_calls(inj, lambda: L.lbm_create(cfg))
