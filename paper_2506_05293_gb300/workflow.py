@@ -486,10 +486,20 @@ def vortex_study(cases, outflows, eval_steps, stream=0, precision="fp32"):
         for k, b in batches.items():
             L.lbm_batch_step(b, t - done)
         done = t
-        ref = [L.lbm_fields(s)[0] for s in groups["reference"]]
+        ref = []
+        for s in groups["reference"]:
+            try:
+                ref.append(L.lbm_fields(s)[0])
+            except L.LbmError as ex:              # a diverged reference scores nothing
+                if ex.status != 5:
+                    raise
+                ref.append(None)
         for k in names:
             row = []
             for c, s, r in zip(cases, groups[k], ref):
+                if r is None:
+                    row.append(float("nan"))
+                    continue
                 try:
                     rho = L.lbm_fields(s)[0]
                 except L.LbmError as ex:          # a diverged run scores NaN from then on
