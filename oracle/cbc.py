@@ -52,6 +52,7 @@ class CBCOutflow:
     length: Optional[float] = None   # characteristic length of Eq. 27; None -> nx
     tuner: Optional[object] = None   # oracle.mlp.MLP, 6 inputs, 1 or 2 outputs
     exact_mass: bool = False
+    tuner_bf16: bool = False    # evaluate the tuner with BF16 operands (MLP.predict_bf16)
 
 
 def d_dx_backward(q, L):
@@ -135,7 +136,8 @@ def cbc_east(solver, f, g):
     sigma = np.full(ny, float(cb.sigma))
     kappa2 = np.full(ny, float(cb.kappa2))
     if cb.tuner is not None:
-        s = np.asarray(cb.tuner.predict(tuner_features(px, uxx, vxx, py, uyy, vyy)))
+        feats = tuner_features(px, uxx, vxx, py, uyy, vyy)
+        s = np.asarray(cb.tuner.predict_bf16(feats) if cb.tuner_bf16 else cb.tuner.predict(feats))
         sigma = cb.sigma * sigmoid(s[:, 0])
         if s.shape[1] > 1:
             kappa2 = cb.kappa2 * sigmoid(s[:, 1])

@@ -22,6 +22,17 @@ import numpy as np
 LEAKY_SLOPE = 0.01
 
 
+def round_bf16(x):
+    """Round to bfloat16 (8 significand bits, the exponent range of binary32)
+    with round-to-nearest-even, returned as float64.  The value is first
+    rounded to binary32 (as a GPU holding it in FP32 does), then the low 16
+    bits of the binary32 pattern are rounded away."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return (u.astype(np.uint32)).view(np.float32).astype(np.float64)
+
+
 def act_fwd(z, act):
     if act == "tanh":
         return np.tanh(z)
@@ -92,6 +103,20 @@ class MLP:
         """Scaled output out_scale * o for raw inputs x."""
         hs, _ = self.forward(self.normalise(x))
         return self.out_scale * hs[-1]
+
+    def predict_bf16(self, x):
+        """The same network with BF16 operands, as a tensor-core GEMM with
+        BF16 inputs evaluates it: the normalised inputs (formed in binary32),
+        every weight matrix and every hidden layer's activations are rounded to
+        BF16 before they are multiplied; products are summed exactly (float64
+        here), the bias added in binary32 precision."""
+        z = np.asarray(self.normalise(x), dtype=np.float32).astype(np.float64)
+        h = round_bf16(z)
+        last = len(self.layers) - 1
+        for l, (Wl, bl) in enumerate(self.layers):
+            a = h @ round_bf16(Wl).T + np.asarray(bl, np.float32).astype(np.float64)
+            h = round_bf16(act_fwd(a, self.act)) if l < last else a
+        return self.out_scale * h
 
     def backward(self, hs, pre, d_out):
         """Gradients of a loss with dL/do = d_out (batch, n_out) with respect to

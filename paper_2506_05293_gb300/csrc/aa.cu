@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128, MINB) aa_step_kernel(const StepParams p) 
         if (COLL == 0 || (COLL == 2 && m.coll == LBM_BGK))
           collide_bgk<R>(h, sc.omega, drho, ux, uy);
         else
-          collide_mrt<R>(h, sc.mrt, drho, ux, uy);
+          collide_mrt<R>(h, mrt_of<R>(m), drho, ux, uy);
         bad |= nonfinite(drho);
         if (gather) {
           // f*_i(x) into slot i of x + c_i

@@ -293,6 +293,21 @@ namespace {
 // layer W transposed (row k = input k's weights to every unit) then b; then
 // in_mean[n_in], in_std[n_in]; padded to a multiple of 4 elements; FP32 and
 // FP64 copies.  Layer sizes are checked by the caller.
+// IEEE binary32 -> bfloat16, round to nearest even (finite inputs)
+uint16_t bf16_rn(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+// offset of layer l's W in lbm_mlp.params
+int64_t off_of(const lbm_mlp* net, int l) {
+  int64_t off = 0;
+  for (int k = 0; k < l; ++k) off += (int64_t)net->sizes[k] * net->sizes[k + 1] + net->sizes[k + 1];
+  return off;
+}
+
 lbm_status upload_net(lbm_sim* s, const lbm_mlp* net, int n_in, int64_t np) {
   for (int64_t k = 0; k < np; ++k)
     if (!std::isfinite(net->params[k])) return fail(LBM_ERR_ARG, "non-finite network parameter");
@@ -314,38 +329,65 @@ lbm_status upload_net(lbm_sim* s, const lbm_mlp* net, int n_in, int64_t np) {
     if (!std::isfinite(blob[np + k])) return fail(LBM_ERR_ARG, "in_mean must be finite");
     blob[np + n_in + k] = sd;
   }
+  // the CBC tuner's padded BF16 weights for the tensor-core path: per layer
+  // [N_pad][K_pad], K_pad = 16 for the six inputs, hidden widths padded to a
+  // multiple of 16, the last layer's N to 8; zeros in the padding
+  std::vector<uint16_t> wb;
+  if (n_in == 6) {
+    int64_t woff = 0;
+    for (int l = 0; l < net->n_layers; ++l) {
+      const int ni = net->sizes[l], no = net->sizes[l + 1];
+      const bool last = l == net->n_layers - 1;
+      const int kp = l == 0 ? 16 : (ni + 15) / 16 * 16;
+      const int npd = last ? 8 : (no + 15) / 16 * 16;
+      wb.resize(wb.size() + (size_t)npd * kp, 0);
+      for (int j = 0; j < no; ++j)
+        for (int k = 0; k < ni; ++k)
+          wb[(size_t)(woff + (int64_t)j * kp + k)] = bf16_rn(net->params[off_of(net, l) + (int64_t)j * ni + k]);
+      woff += (int64_t)npd * kp;
+    }
+  }
   LBM_GUARD_BEGIN
-  if (!s->nn.params_f || s->nn.blob_elems != (int32_t)blob_n) {
-    // both copies or neither: a failed allocation leaves the current network
+  if (!s->nn.params_f || s->nn.blob_elems != (int32_t)blob_n ||
+      s->nn.bf16_elems != (int64_t)wb.size()) {
+    // all copies or none: a failed allocation leaves the current network
     const lbm_allocator* a = s->have_alloc ? &s->alloc : nullptr;
-    float* pf = (float*)lbm::dev_alloc_raw(a, blob.size() * sizeof(float));
-    double* pd = nullptr;
+    const size_t bytes[3] = {blob.size() * sizeof(float), blob.size() * sizeof(double),
+                             wb.size() * sizeof(uint16_t)};
+    void* fresh[3] = {nullptr, nullptr, nullptr};
     try {
-      pd = (double*)lbm::dev_alloc_raw(a, blob.size() * sizeof(double));
+      for (int k = 0; k < 3; ++k)
+        if (bytes[k]) fresh[k] = lbm::dev_alloc_raw(a, bytes[k]);
     } catch (...) {
-      lbm::dev_free_raw(a, pf);
+      for (void* q : fresh) lbm::dev_free_raw(a, q);
       throw;
     }
     if (s->nn.params_f) {
       // launch tables may still name the old copies: free them once the stream is idle
       lbm::sim_settle(s);
       ck(cudaStreamSynchronize(s->stream), "net sync");
-      for (void* q : {(void*)s->nn.params_f, (void*)s->nn.params_d}) {
+      for (void* q : {(void*)s->nn.params_f, (void*)s->nn.params_d, (void*)s->nn.params_bf16}) {
+        if (!q) continue;
         s->owned.erase(std::remove(s->owned.begin(), s->owned.end(), q), s->owned.end());
         lbm::dev_free_raw(a, q);
       }
     }
-    s->nn.params_f = pf;
-    s->nn.params_d = pd;
-    s->owned.push_back(pf);
-    s->owned.push_back(pd);
+    s->nn.params_f = (float*)fresh[0];
+    s->nn.params_d = (double*)fresh[1];
+    s->nn.params_bf16 = (uint16_t*)fresh[2];
+    for (void* q : fresh)
+      if (q) s->owned.push_back(q);
   }
   std::vector<double> blob_d(blob.begin(), blob.end());
   ck(cudaMemcpyAsync(s->nn.params_f, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice,
                      s->stream), "net copy");
   ck(cudaMemcpyAsync(s->nn.params_d, blob_d.data(), blob_d.size() * 8, cudaMemcpyHostToDevice,
                      s->stream), "net copy");
+  if (!wb.empty())
+    ck(cudaMemcpyAsync(s->nn.params_bf16, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice,
+                       s->stream), "net copy");
   ck(cudaStreamSynchronize(s->stream), "net sync");
+  s->nn.bf16_elems = (int64_t)wb.size();
   s->nn.n_layers = net->n_layers;
   for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) s->nn.sizes[l] = l <= net->n_layers ? net->sizes[l] : 0;
   s->nn.act = net->act;

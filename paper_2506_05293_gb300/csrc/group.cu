@@ -61,6 +61,7 @@ void fill_member(const lbm_sim* s, Member& m) {
     // the network (NN outflow) or tuner (CBC); FP32 and FP16 storage compute in FP32
     if (s->nn.n_layers > 0) {
       m.nn_net = s->prec == LBM_FP64 ? (const void*)s->nn.params_d : (const void*)s->nn.params_f;
+      m.nn_bf16 = s->nn.params_bf16;
       m.nn_layers = s->nn.n_layers;
       m.nn_act = s->nn.act;
       for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) m.nn_sizes[l] = s->nn.sizes[l];

@@ -55,6 +55,7 @@ struct Member {
   double cbc_kfac;        // CBC: (1 - M^2) c_s / length, so kappa1 = sigma * cbc_kfac
   // network of the NN outflow, or the CBC tuner (nn_layers 0: none)
   const void* nn_net;     // compute-precision blob: per layer W^T then b, in_mean, in_std
+  const void* nn_bf16;    // CBC tuner: per layer W padded to [N_pad][K_pad] in BF16 (tensor cores)
   unsigned long long* nn_fallbacks;
   double nn_out_scale;
   double nn_drho;
@@ -104,6 +105,8 @@ struct DevMlp {
   int32_t blob_elems = 0;      // per layer W^T then b, then in_mean[81], in_std[81], padded
   float* params_f = nullptr;
   double* params_d = nullptr;
+  uint16_t* params_bf16 = nullptr;   // tuner only: padded BF16 weights of the tensor-core path
+  int64_t bf16_elems = 0;
   float out_scale = 1.f;
 };
 

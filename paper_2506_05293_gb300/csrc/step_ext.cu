@@ -14,12 +14,11 @@ void set_bulk_smem_attr() {
   using R = typename Compute<S>::R;
   static bool done = false;
   if (done) return;
-  const size_t ring = step_bulk_smem(prec_of<S>(), kBulkSlots);
-  const size_t nn = nn_smem_bytes<R>(kBulkThreads / 32);
+  const size_t smem = ext_bulk_smem<R>(step_bulk_smem(prec_of<S>(), kBulkSlots));
   cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true, false>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(ring > nn ? ring : nn));
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true, true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(ring > nn ? ring : nn));
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   done = true;
 }
 

@@ -24,6 +24,7 @@
 // next launch (or a finalise launch) sums them in a fixed order into the
 // member's force ring, so results are bitwise reproducible run to run.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -71,22 +72,28 @@ __device__ __forceinline__ R act_hidden(R a, int act) {
 }
 
 // A member's scalars in the compute precision (FP32 copies are made on the
-// host: GB300's FP64 pipe is narrow).
+// host: GB300's FP64 pipe is narrow).  The MRT rates are not among them: they
+// are read from the member record where the collision needs them (mrt_of), so
+// a strip loop does not hold six more registers.
 template <typename R> struct Scalars;
 template <> struct Scalars<float> {
   float omega, u_in, rho_out;
-  MrtRates<float> mrt;
   __device__ explicit Scalars(const Member& m)
-      : omega(m.omega_f), u_in(m.u_in_f), rho_out(m.rho_out_f),
-        mrt{m.mrt_f[0], m.mrt_f[1], m.mrt_f[2], m.mrt_f[3], m.mrt_f[4], m.mrt_f[5]} {}
+      : omega(m.omega_f), u_in(m.u_in_f), rho_out(m.rho_out_f) {}
 };
 template <> struct Scalars<double> {
   double omega, u_in, rho_out;
-  MrtRates<double> mrt;
   __device__ explicit Scalars(const Member& m)
-      : omega(m.omega), u_in(m.u_in), rho_out(m.rho_out),
-        mrt{m.mrt[0], m.mrt[1], m.mrt[2], m.mrt[3], m.mrt[4], m.mrt[5]} {}
+      : omega(m.omega), u_in(m.u_in), rho_out(m.rho_out) {}
 };
+
+template <typename R> __device__ __forceinline__ MrtRates<R> mrt_of(const Member& m);
+template <> __device__ __forceinline__ MrtRates<float> mrt_of<float>(const Member& m) {
+  return {m.mrt_f[0], m.mrt_f[1], m.mrt_f[2], m.mrt_f[3], m.mrt_f[4], m.mrt_f[5]};
+}
+template <> __device__ __forceinline__ MrtRates<double> mrt_of<double>(const Member& m) {
+  return {m.mrt[0], m.mrt[1], m.mrt[2], m.mrt[3], m.mrt[4], m.mrt[5]};
+}
 
 // Programmatic dependent launch: a step kernel lets the next one be
 // scheduled early (it then does its set-up while this one drains) and waits
@@ -267,7 +274,7 @@ __device__ __forceinline__ void fluid_node(S* __restrict__ B, const Member& m,
   if (COLL == 0 || (COLL == 2 && m.coll == LBM_BGK))
     collide_bgk<R>(h, sc.omega, drho, ux, uy);
   else
-    collide_mrt<R>(h, sc.mrt, drho, ux, uy);
+    collide_mrt<R>(h, mrt_of<R>(m), drho, ux, uy);
   bad |= nonfinite(drho);
 #pragma unroll
   for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[i]);
@@ -512,26 +519,38 @@ __device__ __noinline__ void nn_block(const StepParams& p, const Member& m, int 
   }
   R drho, ux, uy;
   if (m.coll == LBM_BGK) collide_bgk<R>(h, sc.omega, drho, ux, uy);
-  else collide_mrt<R>(h, sc.mrt, drho, ux, uy);
+  else collide_mrt<R>(h, mrt_of<R>(m), drho, ux, uy);
   if (nonfinite(drho)) atomicOr(m.status, DEV_NONFINITE);
   const int o = rc + L;
 #pragma unroll
   for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[i]);
 }
 
+// row index y wrapped into [0, ny) (y may lie any number of lattices away)
+__device__ __forceinline__ int wrap_row(int y, int ny) {
+  y %= ny;
+  return y < 0 ? y + ny : y;
+}
+
 // ---- characteristic outflow blocks (Sec. 4, Eqs. 17-28) ----------------------
-// One thread per east node (L, y), L = nx - 1.  From the post-collision state
-// at t (the source buffer): rho, u, v at (L, y), (L-1, y), (L-2, y),
-// (L, y -+ 1); p = c_s^2 rho; d/dx second-order one-sided backward, d/dy
-// central (periodic) or first-order towards the fluid next to a solid row.
-// Optional tuner: the six derivatives (p_x, u_x, v_x, p_y, u_y, v_y),
-// z-scored, through a small MLP; sigma = sigma_max sigmoid(s_0), and with a
-// second output kappa2 = kappa2_max sigmoid(s_1).  Wave amplitudes L5, L3
-// (Eqs. 20-22), transverse terms T1, T3, T5 (Eqs. 23-25), incoming L1 of
-// Eq. 26 with kappa1 of Eq. 27, time derivatives (Eqs. 17-19) and one Euler
-// step give the prescribed (rho, u, v) at t+1; the unknowns 3, 6, 7 of the
-// post-stream node follow by Zou & He with that state and f_0 takes the
-// correction of Eq. 28; then the node collides like any fluid node.
+// One thread per east node (L, y), L = nx - 1; a block takes blockDim.x
+// consecutive rows.  From the post-collision state at t (the source buffer):
+// rho, u, v at (L, y), (L-1, y), (L-2, y), (L, y -+ 1); p = c_s^2 rho; d/dx
+// second-order one-sided backward, d/dy central (periodic) or first-order
+// towards the fluid next to a solid row.  The block first stages the moments of
+// columns L-2 .. L for its rows and one row on each side in shared memory, each
+// node computed once from loads of three adjacent columns (instead of every
+// thread gathering 45 scattered populations).  Optional tuner: the six
+// derivatives (p_x, u_x, v_x, p_y, u_y, v_y), z-scored, through a small MLP;
+// sigma = sigma_max sigmoid(s_0), and with a second output kappa2 = kappa2_max
+// sigmoid(s_1).  With FP32 or FP16 storage each warp evaluates the tuner for
+// its 32 nodes on the tensor cores (BF16 operands, FP32 accumulation); with
+// FP64 storage every thread evaluates it in FP64.  Wave amplitudes L5, L3
+// (Eqs. 20-22), transverse terms T1, T3, T5 (Eqs. 23-25), incoming L1 of Eq. 26
+// with kappa1 of Eq. 27, time derivatives (Eqs. 17-19) and one Euler step give
+// the prescribed (rho, u, v) at t+1; the unknowns 3, 6, 7 of the post-stream
+// node follow by Zou & He with that state and f_0 takes the correction of
+// Eq. 28; then the node collides like any fluid node.
 constexpr int kTunerMaxW = 32;    // widest hidden layer of the CBC tuner
 
 // rho - 1, u, v of the stored (post-collision) populations of node (x, y);
@@ -552,7 +571,8 @@ __device__ __forceinline__ void node_macros(const S* __restrict__ A, const Membe
 template <typename R>
 __device__ __forceinline__ R sigmoid_r(R s) { return R(1) / (R(1) + exp(-s)); }
 
-// tuner outputs s[0..1] (s[1] = 0 with one output) for six inputs
+// tuner outputs s[0..1] (s[1] = 0 with one output) for six inputs, one node
+// per thread in the compute precision (the FP64 path)
 template <typename R>
 __device__ void tuner_eval(const Member& m, const R x_in[6], R s_out[2]) {
   const R* __restrict__ net = static_cast<const R*>(m.nn_net);
@@ -580,50 +600,223 @@ __device__ void tuner_eval(const Member& m, const R x_in[6], R s_out[2]) {
   s_out[1] = m.nn_sizes[m.nn_layers] > 1 ? a[1] : R(0);
 }
 
+// ---- the tuner on the tensor cores (FP32 and FP16 storage) -------------------
+// The 32 nodes of a warp form the rows of a [32 x K] activation tile; each
+// layer is one warp-level GEMM with mma.sync m16n8k16 (BF16 operands, FP32
+// accumulators initialised with the bias), two m-tiles of 16 nodes.  Layer
+// widths are padded: the six inputs to K = 16, hidden widths to 16 or 32 (at
+// most 32, so at most 4 n-tiles and 2 k-steps), the last layer to N = 8.  The
+// accumulator fragment of two neighbouring n-tiles is exactly the A fragment of
+// the next layer's k-step, so activations stay in registers between layers
+// (padded columns hold 0: zero weights and bias, and act(0) = 0).  The weights
+// come from the library's padded BF16 copy ([N_pad][K_pad] per layer, K
+// fastest), biases from the FP32 copy.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // lo in the low half
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], uint32_t b0,
+                                               uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__host__ __device__ constexpr int tuner_pad16(int n) { return (n + 15) / 16 * 16; }
+
+// per-warp shared scratch of the tensor-core tuner: [32][8] BF16 inputs, [32][2] outputs
+constexpr int kTunerWarpBytes = 32 * 8 * 2 + 32 * 2 * 4;
+
+// z: this thread's six z-scored inputs; every lane of the warp must call it.
+__device__ inline void tuner_mma_warp(const Member& m, const float z[6], float s_out[2],
+                               unsigned char* wscratch) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+  uint32_t* feat = reinterpret_cast<uint32_t*>(wscratch);          // [32][4] bf16 pairs
+  float* outs = reinterpret_cast<float*>(wscratch + 32 * 8 * 2);   // [32][2]
+  feat[lane * 4 + 0] = pack_bf16x2(z[0], z[1]);
+  feat[lane * 4 + 1] = pack_bf16x2(z[2], z[3]);
+  feat[lane * 4 + 2] = pack_bf16x2(z[4], z[5]);
+  feat[lane * 4 + 3] = 0u;
+  __syncwarp();
+  const uint16_t* __restrict__ W = static_cast<const uint16_t*>(m.nn_bf16);
+  const float* __restrict__ net = static_cast<const float*>(m.nn_net);
+  const int L = m.nn_layers;
+#pragma unroll 1
+  for (int mt = 0; mt < 2; ++mt) {
+    const int ra = mt * 16 + g, rb = ra + 8;
+    uint32_t a[2][4];
+    a[0][0] = feat[ra * 4 + t4];
+    a[0][1] = feat[rb * 4 + t4];
+    a[0][2] = a[0][3] = 0u;
+    a[1][0] = a[1][1] = a[1][2] = a[1][3] = 0u;
+    int ksteps = 1, woff = 0, foff = 0;
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+      const int n_in = m.nn_sizes[l], n_out = m.nn_sizes[l + 1];
+      const bool last = l == L - 1;
+      const int Kp = l == 0 ? 16 : tuner_pad16(n_in);
+      const int Np = last ? 8 : tuner_pad16(n_out);
+      const int nt = Np / 8;
+      const float* bias = net + foff + n_in * n_out;
+      float c[4][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+        if (j < nt) {
+          const int n0 = j * 8 + 2 * t4;
+          const float b0 = n0 < n_out ? __ldg(bias + n0) : 0.f;
+          const float b1 = n0 + 1 < n_out ? __ldg(bias + n0 + 1) : 0.f;
+          c[j][0] = b0;
+          c[j][1] = b1;
+          c[j][2] = b0;
+          c[j][3] = b1;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            if (kk < ksteps) {
+              const uint16_t* wr = W + woff + (j * 8 + g) * Kp + kk * 16 + 2 * t4;
+              const uint32_t b0r = __ldg(reinterpret_cast<const unsigned int*>(wr));
+              const uint32_t b1r = __ldg(reinterpret_cast<const unsigned int*>(wr + 8));
+              mma_bf16_16816(c[j], a[kk], b0r, b1r);
+            }
+          }
+        }
+      }
+      if (!last) {
+        ksteps = Np / 16;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          if (kk < ksteps) {
+            const int j0 = 2 * kk, j1 = 2 * kk + 1;
+            a[kk][0] = pack_bf16x2(act_hidden<float>(c[j0][0], m.nn_act),
+                                   act_hidden<float>(c[j0][1], m.nn_act));
+            a[kk][1] = pack_bf16x2(act_hidden<float>(c[j0][2], m.nn_act),
+                                   act_hidden<float>(c[j0][3], m.nn_act));
+            a[kk][2] = pack_bf16x2(act_hidden<float>(c[j1][0], m.nn_act),
+                                   act_hidden<float>(c[j1][1], m.nn_act));
+            a[kk][3] = pack_bf16x2(act_hidden<float>(c[j1][2], m.nn_act),
+                                   act_hidden<float>(c[j1][3], m.nn_act));
+          }
+        }
+      } else if (t4 == 0) {
+        // columns 0 and 1 of n-tile 0: s_0, s_1 of rows ra and rb
+        outs[ra * 2] = c[0][0];
+        outs[ra * 2 + 1] = c[0][1];
+        outs[rb * 2] = c[0][2];
+        outs[rb * 2 + 1] = c[0][3];
+      }
+      woff += Np * Kp;
+      foff += n_in * n_out + n_out;
+    }
+  }
+  __syncwarp();
+  s_out[0] = outs[lane * 2];
+  s_out[1] = m.nn_sizes[L] > 1 ? outs[lane * 2 + 1] : 0.f;
+}
+
+// shared memory of a CBC block of `threads` threads: the staged moments
+// [(threads + 2) rows][3 columns][rho - 1, u, v], then (FP32 compute) the
+// per-warp scratch of the tensor-core tuner
+template <typename R>
+__host__ __device__ constexpr size_t cbc_mac_bytes(int threads) {
+  return ((size_t)(threads + 2) * 9 * sizeof(R) + 15) / 16 * 16;
+}
+template <typename R>
+__host__ __device__ constexpr size_t cbc_smem_bytes(int threads) {
+  return cbc_mac_bytes<R>(threads) + (sizeof(R) == 4 ? (size_t)(threads / 32) * kTunerWarpBytes : 0);
+}
+
 template <typename S>
-__device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int local_block) {
+__device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int local_block,
+                                       unsigned char* smem) {
   using R = typename Compute<S>::R;
-  const int y = local_block * (int)blockDim.x + (int)threadIdx.x;
-  if (y >= m.ny) return;
+  const int T = (int)blockDim.x;
+  const int y0 = local_block * T;
+  const int y = y0 + (int)threadIdx.x;
   const int L = m.nx - 1;
   auto solid = [&](int x, int yy) -> bool {
     return (__ldg(m.solid_bits + yy * m.words_per_row + (x >> 5)) >> (x & 31)) & 1u;
   };
-  if (solid(L, y)) return;   // the stream-and-collide blocks handle solid nodes
   const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
   S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
-  const int ym = y == 0 ? m.ny - 1 : y - 1;
-  const int yp = y == m.ny - 1 ? 0 : y + 1;
+  // moments of columns L-2, L-1, L at the rows y0-1 .. y0+T (wrapped): item k is
+  // row k / 3 of the window, column L - 2 + k % 3
+  R* mac = reinterpret_cast<R*>(smem);
+  for (int k = (int)threadIdx.x; k < (T + 2) * 3; k += T) {
+    const int r = k / 3, c = k - 3 * r;
+    R d, u, v;
+    node_macros<S, R>(A, m, L - 2 + c, wrap_row(y0 - 1 + r, m.ny), d, u, v);
+    mac[3 * k] = d;
+    mac[3 * k + 1] = u;
+    mac[3 * k + 2] = v;
+  }
+  __syncthreads();
+  // threads past the last row compute on a wrapped row and write nothing (every
+  // lane of a warp takes part in the tensor-core tuner)
+  const bool active = y < m.ny && !solid(L, y < m.ny ? y : 0);
+  const int yy = y < m.ny ? y : m.ny - 1;
+  const int ym = yy == 0 ? m.ny - 1 : yy - 1;
+  const int yp = yy == m.ny - 1 ? 0 : yy + 1;
+  const R* w0 = mac + 9 * ((int)threadIdx.x + 1);   // this node's window row
+  const bool s_dn = solid(L, ym), s_up = solid(L, yp);
   const R cs2 = R(1) / R(3);
   const R cs = sqrt(cs2);
-  R r0, u0, v0, r1, u1, v1, r2, u2, v2, rm, um, vm, rp, up, vp;
-  node_macros<S, R>(A, m, L, y, r0, u0, v0);
-  node_macros<S, R>(A, m, L - 1, y, r1, u1, v1);
-  node_macros<S, R>(A, m, L - 2, y, r2, u2, v2);
-  node_macros<S, R>(A, m, L, ym, rm, um, vm);
-  node_macros<S, R>(A, m, L, yp, rp, up, vp);
-  // r* hold rho - 1 here; p - 1/3 = c_s^2 (rho - 1)
-  const R px = cs2 * (R(0.5) * (R(3) * r0 - R(4) * r1 + r2));
-  const R ux = R(0.5) * (R(3) * u0 - R(4) * u1 + u2);
-  const R vx = R(0.5) * (R(3) * v0 - R(4) * v1 + v2);
-  const bool s_dn = solid(L, ym), s_up = solid(L, yp);
-  auto ddy = [&](R qm, R q0, R qp) -> R {
-    if (!s_up && !s_dn) return R(0.5) * (qp - qm);
-    if (!s_up) return qp - q0;
-    if (!s_dn) return q0 - qm;
-    return R(0);
+  // the stencil's values and derivatives from the staged window (row y - 1 at
+  // w0 - 9, row y + 1 at w0 + 9); r* hold rho - 1 and p - 1/3 = c_s^2 (rho - 1).
+  // Evaluated before the tuner for its features and again after it, so the
+  // tuner's fragments do not compete with them for registers.
+  struct Stencil { R r0, u0, v0, px, ux, vx, py, uy, vy; };
+  auto stencil = [&]() {
+    Stencil st;
+    const R* wm = w0 - 9;
+    const R* wp = w0 + 9;
+    st.r0 = w0[6];
+    st.u0 = w0[7];
+    st.v0 = w0[8];
+    st.px = cs2 * (R(0.5) * (R(3) * st.r0 - R(4) * w0[3] + w0[0]));
+    st.ux = R(0.5) * (R(3) * st.u0 - R(4) * w0[4] + w0[1]);
+    st.vx = R(0.5) * (R(3) * st.v0 - R(4) * w0[5] + w0[2]);
+    auto ddy = [&](R qm, R q0, R qp) -> R {
+      if (!s_up && !s_dn) return R(0.5) * (qp - qm);
+      if (!s_up) return qp - q0;
+      if (!s_dn) return q0 - qm;
+      return R(0);
+    };
+    st.py = cs2 * ddy(wm[6], st.r0, wp[6]);
+    st.uy = ddy(wm[7], st.u0, wp[7]);
+    st.vy = ddy(wm[8], st.v0, wp[8]);
+    return st;
   };
-  const R py = cs2 * ddy(rm, r0, rp);
-  const R uy = ddy(um, u0, up);
-  const R vy = ddy(vm, v0, vp);
   R sigma = (R)m.cbc_sigma, kappa2 = (R)m.cbc_kappa2;
-  if (m.nn_layers > 0) {
-    const R feats[6] = {px, ux, vx, py, uy, vy};
+  if (m.nn_layers > 0) {   // block-uniform
     R s[2];
-    tuner_eval<R>(m, feats, s);
+    {
+      const Stencil f = stencil();
+      const R feats[6] = {f.px, f.ux, f.vx, f.py, f.uy, f.vy};
+      if constexpr (sizeof(R) == 4) {
+        const float* net = static_cast<const float*>(m.nn_net);
+        int n_params = 0;
+        for (int l = 0; l < m.nn_layers; ++l)
+          n_params += m.nn_sizes[l] * m.nn_sizes[l + 1] + m.nn_sizes[l + 1];
+        float z[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          z[k] = (feats[k] - __ldg(net + n_params + k)) / __ldg(net + n_params + 6 + k);
+        tuner_mma_warp(m, z, s,
+                       smem + cbc_mac_bytes<R>(T) + (threadIdx.x >> 5) * kTunerWarpBytes);
+      } else {
+        tuner_eval<R>(m, feats, s);
+      }
+    }
     sigma = sigma * sigmoid_r(s[0]);
     if (m.nn_sizes[m.nn_layers] > 1) kappa2 = kappa2 * sigmoid_r(s[1]);
   }
+  const Stencil st = stencil();
+  const R r0 = st.r0, u0 = st.u0, v0 = st.v0, px = st.px, ux = st.ux, vx = st.vx;
+  const R py = st.py, vy = st.vy;
+  if (!active) return;   // the stream-and-collide blocks handle solid nodes
   // Eqs. 20-27 and the Euler step of Eqs. 17-19
   const R rho = R(1) + r0;
   const R pL = cs2 * rho;
@@ -659,7 +852,7 @@ __device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int
   const Scalars<R> sc(m);
   R drho, uxo, uyo;
   if (m.coll == LBM_BGK) collide_bgk<R>(h, sc.omega, drho, uxo, uyo);
-  else collide_mrt<R>(h, sc.mrt, drho, uxo, uyo);
+  else collide_mrt<R>(h, mrt_of<R>(m), drho, uxo, uyo);
   if (nonfinite(drho)) atomicOr(m.status, DEV_NONFINITE);
   const int o = rc + L;
 #pragma unroll
@@ -671,7 +864,7 @@ __device__ __forceinline__ void ext_dispatch(const StepParams& p, int blk, unsig
   const Member& m = p.n_members == 1 ? p.m0 : p.members[p.nn_block_member[blk]];
   const int local = p.n_members == 1 ? blk : blk - m.nn_first;
   if (m.ext_kind == 1) nn_block<S>(p, m, local, smem);
-  else cbc_block<S>(p, m, local);
+  else cbc_block<S>(p, m, local, smem);
 }
 
 template <typename S, int COLL, int MINB, bool EXT>
@@ -792,10 +985,6 @@ constexpr int kBulkThreads = 32 * (kConsumerWarps + 1);
 // tile (one that holds a column in L-4 .. L) also waits for the boundary
 // blocks of step t-1 that meet its rows +- 2 (they wrote its column L, and read
 // what it overwrites).
-__device__ __forceinline__ int wrap_row(int y, int ny) {
-  y %= ny;
-  return y < 0 ? y + ny : y;
-}
 
 // Calls fn(s, e) for the wrapped row segments [s, e] covering rows a..b.
 template <typename F>
@@ -1373,6 +1562,20 @@ inline void launch_pdl(Kernel kernel, int grid, int threads, size_t smem, cudaSt
   cudaLaunchKernelEx(&cfg, kernel, p);
 }
 
+// dynamic shared memory of launches with boundary blocks: the larger of the
+// stream-and-collide need (ring), the network block's and the CBC block's
+template <typename R>
+inline size_t ext_bulk_smem(size_t ring) {
+  size_t v = ring;
+  v = v > nn_smem_bytes<R>(kBulkThreads / 32) ? v : nn_smem_bytes<R>(kBulkThreads / 32);
+  return v > cbc_smem_bytes<R>(kBulkThreads) ? v : cbc_smem_bytes<R>(kBulkThreads);
+}
+template <typename R>
+inline size_t ext_reg_smem() {
+  return nn_smem_bytes<R>(4) > cbc_smem_bytes<R>(128) ? nn_smem_bytes<R>(4)
+                                                      : cbc_smem_bytes<R>(128);
+}
+
 template <typename S, int COLL, int MINB, bool EXT, bool DYN>
 void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
   // the dynamic shared memory attribute is set by the occupancy query that
@@ -1380,7 +1583,7 @@ void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
   // their first launch
   using R = typename Compute<S>::R;
   size_t smem = step_bulk_smem(prec_of<S>(), kBulkSlots);
-  if (EXT) smem = smem > nn_smem_bytes<R>(kBulkThreads / 32) ? smem : nn_smem_bytes<R>(kBulkThreads / 32);
+  if (EXT) smem = ext_bulk_smem<R>(smem);
   launch_pdl(step_bulk_kernel<S, COLL, kBulkSlots, MINB, EXT, DYN>, p.nn_blocks + blocks + p.n_members,
              kBulkThreads, smem, s, p);
 }
@@ -1389,7 +1592,7 @@ template <typename S, int COLL, bool EXT>
 void launch_v(const StepParams& p, int variant, int blocks, cudaStream_t s) {
   using R = typename Compute<S>::R;
   const int g = p.nn_blocks + blocks + p.n_members;
-  const size_t dyn = EXT ? nn_smem_bytes<R>(4) : 0;
+  const size_t dyn = EXT ? ext_reg_smem<R>() : 0;
   switch (variant) {
     case 0: launch_pdl(step_kernel<S, COLL, 6, EXT>, g, 128, dyn, s, p); break;
     case 1: launch_pdl(step_kernel<S, COLL, 8, EXT>, g, 128, dyn, s, p); break;

@@ -3,7 +3,8 @@ does once the tuner is trained: members with the characteristic outflow and a
 tuner (Sec. 4.2; one of odd size), a member with the fixed characteristic
 outflow and a Zou & He member with channel walls, advanced together by one launch
 per step, each equal node by node to its own FP64 oracle run (1e-12), and in
-FP32 within the solver's FP32 bounds."""
+FP32 (the tuner then a BF16 tensor-core GEMM, which the oracle emulates) within
+the solver's FP32 bounds."""
 import math
 
 import numpy as np
@@ -60,7 +61,9 @@ def _member_setup(m):
     return kind, (rho, u, v), tau
 
 
-def _oracle(m, steps):
+def _oracle(m, steps, bf16=False):
+    """FP64 oracle run of a member; bf16: the tuner with BF16 operands, as the
+    FP32 path evaluates it on the tensor cores."""
     nx, ny, strength, out, walls = m
     kind, init, tau = _member_setup(m)
     extra = {}
@@ -69,7 +72,7 @@ def _oracle(m, steps):
             layers, mean, std = _tuner(out[1])
             net = mlp.MLP([(W.astype(np.float64), b.astype(np.float64)) for W, b in layers],
                           "leaky", mean.astype(np.float64), std.astype(np.float64), 1.0)
-            cb = cbc.CBCOutflow(sigma=SMAX, kappa2=KMAX, mach=MACH, tuner=net)
+            cb = cbc.CBCOutflow(sigma=SMAX, kappa2=KMAX, mach=MACH, tuner=net, tuner_bf16=bf16)
         else:
             cb = cbc.CBCOutflow(sigma=out[1], kappa2=out[2], mach=MACH)
         extra = dict(outflow="cbc", cbc=cb)
@@ -118,6 +121,11 @@ def oracle_runs():
     return [_oracle(m, STEPS) for m in MEMBERS]
 
 
+@pytest.fixture(scope="module")
+def oracle_runs_bf16():
+    return [_oracle(m, STEPS, bf16=True) for m in MEMBERS]
+
+
 @pytest.mark.parametrize("tiling", [(16, 6), (8, 3), (12, 1)])
 def test_mixed_batch_matches_oracle_fp64(L, oracle_runs, tiling):
     fs = _gpu_batch(L, "fp64", STEPS, tiling)
@@ -126,9 +134,9 @@ def test_mixed_batch_matches_oracle_fp64(L, oracle_runs, tiling):
         assert err < 1e-12, (m, err)
 
 
-def test_mixed_batch_fp32_within_bounds(L, oracle_runs):
+def test_mixed_batch_fp32_within_bounds(L, oracle_runs_bf16):
     fs = _gpu_batch(L, "fp32", STEPS, (16, 6))
-    for m, f, (fo, kind) in zip(MEMBERS, fs, oracle_runs):
+    for m, f, (fo, kind) in zip(MEMBERS, fs, oracle_runs_bf16):
         r, u, v = lbm.moments(f)
         ro, uo, vo = lbm.moments(fo)
         fl = kind == 0

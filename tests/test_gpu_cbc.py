@@ -32,11 +32,16 @@ def _tuner(sizes, seed, scale=0.3):
 
 
 def _run(L, precision, nx, ny, steps, walls, sigma, kappa2, mach, exact, tuner=None, seed=3,
-         length=0.0):
+         length=0.0, bf16=None, amp_rho=0.005):
+    """GPU run and oracle run of the same case.  With FP32 or FP16 storage the
+    GPU evaluates the tuner on the tensor cores with BF16 operands, which the
+    oracle emulates (bf16 None: follow the storage precision)."""
+    if bf16 is None:
+        bf16 = precision != "fp64"
     kind = np.zeros((ny, nx), np.uint8)
     if walls:
         kind = add_walls(kind)
-    rho, ux, uy = random_smooth_state(nx, ny, seed=seed, amp_u=0.02, amp_rho=0.005)
+    rho, ux, uy = random_smooth_state(nx, ny, seed=seed, amp_u=0.02, amp_rho=amp_rho)
     ux = np.where(kind == 0, 0.04 + ux, 0.0)
     cfg = L.lbm_config_default(nx=nx, ny=ny, tau=0.62, precision=precision, u_in=0.04,
                                v_pert_amp=1e-3, seed=seed)
@@ -57,7 +62,7 @@ def _run(L, precision, nx, ny, steps, walls, sigma, kappa2, mach, exact, tuner=N
         net = mlp.MLP([(W.astype(np.float64), b.astype(np.float64)) for W, b in layers], "leaky",
                       mean.astype(np.float64), std.astype(np.float64), 1.0)
     cb = cbc.CBCOutflow(sigma=sigma, kappa2=kappa2, mach=mach, length=length or None,
-                        tuner=net, exact_mass=exact)
+                        tuner=net, exact_mass=exact, tuner_bf16=bf16)
     o = lbm.Solver(lbm.Config(nx=nx, ny=ny, tau=0.62, u_in=0.04, v_pert_amp=1e-3, seed=seed,
                               outflow="cbc", cbc=cb), kind)
     o.init_equilibrium(rho, ux, uy)
@@ -82,6 +87,28 @@ def test_tuner_matches_oracle_fp64(L, sizes):
     f, fo, kind = _run(L, "fp64", 70, 33, 50, False, 0.8, 0.3, 0.07, False,
                        tuner=_tuner(sizes, 4), length=50.0)
     assert np.abs(f - fo)[:, kind == 0].max() < 1e-12
+
+
+def test_tensor_core_tuner_is_the_bf16_network(L):
+    """FP32 storage evaluates the tuner as a BF16 GEMM with FP32 accumulation
+    (mma.sync on the tensor cores).  With a tuner to which the boundary is
+    sensitive (sigma up to 2, kappa1 of a short length, a 6-20-20-2 network),
+    the GPU run follows the oracle that rounds the network's operands to BF16
+    within FP32 bounds, and stays measurably farther from the oracle whose
+    network is FP64 throughout."""
+    U = 0.04
+    layers, mean, std = _tuner([6, 20, 20, 2], 8, scale=1.0)
+    args = (L, "fp32", 60, 41, 40, False, 2.0, 0.3, U / CS, False)
+    kw = dict(tuner=(layers, mean, std), length=8.0, amp_rho=0.01)
+    f, fo_bf16, kind = _run(*args, bf16=True, **kw)
+    _, fo_64, _ = _run(*args, bf16=False, **kw)
+    r, u, v = lbm.moments(f)
+    rb, ub, vb = lbm.moments(fo_bf16)
+    r6, u6, v6 = lbm.moments(fo_64)
+    e_bf16 = np.abs(r - rb).max()
+    e_64 = np.abs(r - r6).max()
+    assert e_bf16 < 1e-5, e_bf16
+    assert e_64 > 5 * e_bf16, (e_64, e_bf16)
 
 
 def test_fp32_matches_oracle(L):

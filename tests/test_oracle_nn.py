@@ -240,3 +240,44 @@ def test_snapshot_rows_follow_the_streaming_definition_and_equal_the_plane_captu
         p.step(1)
         c = x - 4
         assert np.array_equal(p.dataset(), rows[c * ny:(c + 1) * ny])
+
+
+def test_bf16_rounding_known_values():
+    """round_bf16 keeps 8 significand bits and rounds to nearest, ties to even
+    (IEEE 754 round-to-nearest-even on the bfloat16 format)."""
+    r = mlp.round_bf16
+    one = 1.0
+    assert r(one) == one and r(-2.5) == -2.5 and r(0.0) == 0.0
+    assert r(one + 2.0 ** -7) == one + 2.0 ** -7          # representable
+    assert r(one + 2.0 ** -8) == one                       # tie, to the even 1.0
+    assert r(one + 3 * 2.0 ** -8) == one + 2.0 ** -6       # tie, to the even neighbour
+    assert r(one + 2.0 ** -8 + 2.0 ** -20) == one + 2.0 ** -7   # above the tie
+    assert r(-(one + 2.0 ** -8 + 2.0 ** -20)) == -(one + 2.0 ** -7)
+    big = r(3.0e38)                                        # near the top of the range
+    assert np.isfinite(big) and abs(big / 3.0e38 - 1) <= 2.0 ** -8
+    x = rng.uniform(-10, 10, 1000)
+    y = r(x)
+    # |x - y| <= half a bf16 spacing of x, and y has 8 significand bits
+    spacing = 2.0 ** (np.floor(np.log2(np.abs(x))) - 7)
+    assert np.all(np.abs(x - y) <= 0.5 * spacing * (1 + 1e-12))
+    m, _ = np.frexp(y)
+    assert np.all(np.abs(m * 2 ** 8 - np.round(m * 2 ** 8)) == 0)
+
+
+def test_bf16_network_equals_fp64_when_operands_are_representable():
+    """Weights, biases and inputs with at most 8 significand bits, and hidden
+    activations that stay so (positive pre-activations of few bits): the BF16
+    evaluation equals the FP64 one exactly; a weight that is not representable
+    changes the output by exactly its rounding error times its input."""
+    W1 = np.array([[0.5, -0.25, 1.0, 0.0, 2.0, -1.0], [0.125, 0.75, -0.5, 1.5, 0.0, 0.25]])
+    W2 = np.array([[1.0, -0.5], [0.25, 0.75]])
+    net = mlp.MLP([(W1, np.array([0.5, -0.25])), (W2, np.array([0.0, 1.0]))], "leaky")
+    x = np.array([[1.0, 2.0, -0.5, 0.25, 1.5, -2.0], [0.0, 0.5, 0.5, 1.0, 2.0, 4.0]])
+    assert np.array_equal(net.predict_bf16(x), net.predict(x))
+    W2b = W2.copy()
+    W2b[0, 0] = 1.0 + 2.0 ** -9           # rounds to 1.0 in BF16
+    net2 = mlp.MLP([(W1, np.array([0.5, -0.25])), (W2b, np.array([0.0, 1.0]))], "leaky")
+    h = net2.forward(x)[0][1]              # hidden activations (exact here)
+    d = net2.predict(x) - net2.predict_bf16(x)
+    assert np.allclose(d[:, 0], 2.0 ** -9 * h[:, 0], rtol=0, atol=1e-15)
+    assert np.array_equal(d[:, 1], np.zeros(2))
