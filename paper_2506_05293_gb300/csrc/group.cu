@@ -118,6 +118,75 @@ std::vector<int32_t> strip_force_slots(const Group& g, std::vector<Member>& ms, 
   return slot;
 }
 
+// Launch order of the stream-and-collide and boundary blocks (see
+// block_role): boundary blocks first when the whole grid is resident at once
+// or the grid is resident-sized; otherwise each boundary block right before
+// the stream-and-collide block of its lattice's east-tile strip that holds
+// the middle row of the block's rows, so both touch the east columns within
+// microseconds of each other and share them in L2.  ms holds the members'
+// strip ranges; force is the strip -> force-slot table (its order puts strips
+// with solids first, as the stream-and-collide blocks take them).
+void build_launch_order(Group& g, const std::vector<Member>& ms, const std::vector<int32_t>& force) {
+  const int n = (int)g.sims.size();
+  const int room = std::max(1, g.max_blocks_v[g.variant]);
+  const bool one_per_strip = !g.persistent && !step_variant_streams(g.variant) &&
+                             !step_variant_dynamic(g.variant);
+  std::vector<int32_t> lo;
+  lo.reserve((size_t)(g.blocks + g.nn_blocks));
+  if (!one_per_strip || n + g.blocks + g.nn_blocks <= room) {
+    for (int j = 0; j < g.nn_blocks; ++j) lo.push_back(-j - 1);
+    for (int b = 0; b < g.blocks; ++b) lo.push_back(b);
+  } else {
+    // the strip each stream-and-collide block takes (strips with solids first)
+    std::vector<int32_t> strip_of((size_t)g.blocks);
+    if (!force.empty()) {
+      int w = 0;
+      for (size_t k = 0; k < force.size(); ++k)
+        if (force[k] >= 0) strip_of[(size_t)w++] = (int32_t)k;
+      for (size_t k = 0; k < force.size(); ++k)
+        if (force[k] < 0) strip_of[(size_t)w++] = (int32_t)k;
+    } else {
+      for (int b = 0; b < g.blocks; ++b) strip_of[(size_t)b] = b;
+    }
+    // boundary blocks anchored at each strip
+    std::vector<std::vector<int32_t>> at((size_t)g.blocks);
+    std::vector<int32_t> block_of_strip((size_t)g.blocks, -1);
+    for (int b = 0; b < g.blocks; ++b) block_of_strip[(size_t)strip_of[(size_t)b]] = b;
+    int nb = 0;
+    for (int k = 0; k < n; ++k) {
+      const int kind = ext_kind(g.sims[k]);
+      if (!kind) continue;
+      const Member& m = ms[(size_t)k];
+      const int per = step_ext_rows(g.variant, kind);
+      const int blocks_k = step_ext_blocks(m.ny, g.variant, kind);
+      for (int j = 0; j < blocks_k; ++j, ++nb) {
+        const int y_mid = std::min(m.ny - 1, j * per + per / 2);
+        const int ls = (y_mid / g.rows) * m.tiles_x + (m.tiles_x - 1);
+        const int b = block_of_strip[(size_t)(m.strip_first + ls)];
+        at[(size_t)(b >= 0 ? b : 0)].push_back(-nb - 1);
+      }
+    }
+    for (int b = 0; b < g.blocks; ++b) {
+      for (int32_t v : at[(size_t)b]) lo.push_back(v);
+      lo.push_back(b);
+    }
+  }
+  if ((int)lo.size() > g.launch_cap) {
+    const lbm_allocator* a = g.sims[0]->have_alloc ? &g.sims[0]->alloc : nullptr;
+    if (g.d_launch_order) {
+      ck(cudaStreamSynchronize(g.stream), "table sync");
+      dev_free_raw(a, g.d_launch_order);
+      g.owned.erase(std::remove(g.owned.begin(), g.owned.end(), (void*)g.d_launch_order),
+                    g.owned.end());
+    }
+    g.d_launch_order = (int32_t*)dev_alloc_raw(a, lo.size() * sizeof(int32_t));
+    g.owned.push_back(g.d_launch_order);
+    g.launch_cap = (int)lo.size();
+  }
+  ck(cudaMemcpyAsync(g.d_launch_order, lo.data(), lo.size() * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, g.stream), "launch order copy");
+}
+
 // (Re)build the launch table for the current tiling and member state.
 void build_table(Group& g) {
   const int n = (int)g.sims.size();
@@ -271,6 +340,7 @@ void build_table(Group& g) {
     ck(cudaMemcpyAsync(g.d_strip_order, order.data(), order.size() * sizeof(int32_t),
                        cudaMemcpyHostToDevice, g.stream), "order table copy");
   }
+  if (g.nn_blocks > 0) build_launch_order(g, ms, force);
   int parts = g.blocks;
   for (int k = 0; k < n; ++k)
     parts = std::max(parts, ms[(size_t)k].part_first + ms[(size_t)k].part_count);
@@ -297,6 +367,7 @@ StepParams params(const Group& g, int q) {
   p.partial_stride = g.partial_stride;
   p.nn_blocks = g.nn_blocks;
   p.nn_block_member = g.d_nn_block_member;
+  p.launch_order = g.nn_blocks > 0 ? g.d_launch_order : nullptr;
   p.dyn_ctr = g.dyn_ctr;
   p.strip_force = g.use_strip_force ? g.d_strip_force : nullptr;
   p.strip_order = g.use_strip_force ? g.d_strip_order : nullptr;

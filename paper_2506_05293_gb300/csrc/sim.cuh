@@ -85,7 +85,10 @@ struct StepParams {
                                  // solids first; null: the natural order
   unsigned long long* dyn_ctr;   // variant 5: [next strip, finished blocks], zero between launches
   int32_t dyn_strips;            // variant 5: strips of the whole table
-  int32_t nn_blocks;             // boundary blocks (the first blocks of the grid)
+  int32_t nn_blocks;             // boundary blocks of the grid
+  const int32_t* launch_order;   // with boundary blocks: the role of each block after the
+                                 // force-reduction blocks (>= 0 stream-and-collide block,
+                                 // < 0 boundary block -v - 1); null: all stream-and-collide
   const int32_t* nn_block_member;  // member of each boundary block (multi-member)
   int64_t* strip_done;           // variant 6: per strip of the table, the number of steps it
                                  // has completed; null: wait for the whole previous launch
@@ -122,6 +125,7 @@ void launch_step_ext(int prec, int coll, const StepParams& p, int variant, int b
                      cudaStream_t s);   // launches with boundary blocks (step_ext.cu)
 int step_strips(int nx, int ny, int rows);
 int step_ext_blocks(int ny, int variant, int ext_kind);  // boundary blocks of one member
+int step_ext_rows(int variant, int ext_kind);             // east nodes of one boundary block
 bool step_variant_is_bulk(int variant);
 bool step_variant_streams(int variant);   // staged variant with a fixed share per block
 bool step_variant_dynamic(int variant);   // staged variant taking strips from a counter
@@ -275,6 +279,8 @@ struct Group {
   unsigned long long* dyn_ctr = nullptr;   // counters of the dynamic staged variant
   int32_t* d_strip_force = nullptr;        // force-partial slot of each strip
   int32_t* d_strip_order = nullptr;        // launch order of the strips
+  int32_t* d_launch_order = nullptr;       // roles of the blocks with boundary blocks
+  int launch_cap = 0;                      // entries of d_launch_order
   int force_cap = 0;
   bool use_strip_force = false;
   int nn_blocks = 0;             // network blocks of the current table

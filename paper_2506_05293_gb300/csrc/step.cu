@@ -74,9 +74,14 @@ int step_strips(int nx, int ny, int rows) {
   return ((nx + 127) / 128) * ((ny + rows - 1) / rows);
 }
 
+int step_ext_rows(int variant, int ext_kind) {
+  // NN: kNnNodes nodes per block; CBC: one node per thread but the first and last
+  return ext_kind == 1 ? kNnNodes
+                       : cbc_block_rows(step_variant_is_bulk(variant) ? kBulkThreads : 128);
+}
+
 int step_ext_blocks(int ny, int variant, int ext_kind) {
-  // NN: kNnNodes nodes per block; CBC: one node per thread
-  const int per = ext_kind == 1 ? kNnNodes : (step_variant_is_bulk(variant) ? kBulkThreads : 128);
+  const int per = step_ext_rows(variant, ext_kind);
   return (ny + per - 1) / per;
 }
 

@@ -553,21 +553,6 @@ __device__ __forceinline__ int wrap_row(int y, int ny) {
 // Eq. 28; then the node collides like any fluid node.
 constexpr int kTunerMaxW = 32;    // widest hidden layer of the CBC tuner
 
-// rho - 1, u, v of the stored (post-collision) populations of node (x, y);
-// differences are taken on rho - 1, which FP32 holds to full relative precision
-template <typename S, typename R>
-__device__ __forceinline__ void node_macros(const S* __restrict__ A, const Member& m, int x, int y,
-                                            R& drho, R& u, R& v) {
-  R h[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) h[i] = to_r<R>(__ldcg(A + i * m.plane + y * m.pitch + x));
-  R jx, jy;
-  moments_shifted(h, drho, jx, jy);
-  const R rho = R(1) + drho;
-  u = jx / rho;
-  v = jy / rho;
-}
-
 template <typename R>
 __device__ __forceinline__ R sigmoid_r(R s) { return R(1) / (R(1) + exp(-s)); }
 
@@ -716,16 +701,22 @@ __device__ inline void tuner_mma_warp(const Member& m, const float z[6], float s
   s_out[1] = m.nn_sizes[L] > 1 ? outs[lane * 2 + 1] : 0.f;
 }
 
-// shared memory of a CBC block of `threads` threads: the staged moments
-// [(threads + 2) rows][3 columns][rho - 1, u, v], then (FP32 compute) the
-// per-warp scratch of the tensor-core tuner
+// Rows (east nodes) of one CBC block of `threads` threads: every thread
+// stages one row of the window, which reaches one row beyond the block's
+// nodes on each side.
+__host__ __device__ constexpr int cbc_block_rows(int threads) { return threads - 2; }
+
+// shared memory of a CBC block of `threads` threads: per window row the
+// moments of columns L-2, L-1, L ([3][rho - 1, u, v]) and six stored
+// populations (A_0, A_2, A_4 at L; A_1, A_5, A_8 at L-1: the known pulls of the
+// east node), then (FP32 compute) the per-warp scratch of the tensor-core tuner
 template <typename R>
-__host__ __device__ constexpr size_t cbc_mac_bytes(int threads) {
-  return ((size_t)(threads + 2) * 9 * sizeof(R) + 15) / 16 * 16;
+__host__ __device__ constexpr size_t cbc_win_bytes(int threads) {
+  return ((size_t)threads * 15 * sizeof(R) + 15) / 16 * 16;
 }
 template <typename R>
 __host__ __device__ constexpr size_t cbc_smem_bytes(int threads) {
-  return cbc_mac_bytes<R>(threads) + (sizeof(R) == 4 ? (size_t)(threads / 32) * kTunerWarpBytes : 0);
+  return cbc_win_bytes<R>(threads) + (sizeof(R) == 4 ? (size_t)(threads / 32) * kTunerWarpBytes : 0);
 }
 
 template <typename S>
@@ -733,33 +724,55 @@ __device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int
                                        unsigned char* smem) {
   using R = typename Compute<S>::R;
   const int T = (int)blockDim.x;
-  const int y0 = local_block * T;
-  const int y = y0 + (int)threadIdx.x;
+  const int E = cbc_block_rows(T);
+  const int t = (int)threadIdx.x;
+  const int y0 = local_block * E;   // nodes y0 .. y0 + E - 1 on threads 1 .. E
   const int L = m.nx - 1;
   auto solid = [&](int x, int yy) -> bool {
     return (__ldg(m.solid_bits + yy * m.words_per_row + (x >> 5)) >> (x & 31)) & 1u;
   };
   const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
   S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
-  // moments of columns L-2, L-1, L at the rows y0-1 .. y0+T (wrapped): item k is
-  // row k / 3 of the window, column L - 2 + k % 3
-  R* mac = reinterpret_cast<R*>(smem);
-  for (int k = (int)threadIdx.x; k < (T + 2) * 3; k += T) {
-    const int r = k / 3, c = k - 3 * r;
-    R d, u, v;
-    node_macros<S, R>(A, m, L - 2 + c, wrap_row(y0 - 1 + r, m.ny), d, u, v);
-    mac[3 * k] = d;
-    mac[3 * k + 1] = u;
-    mac[3 * k + 2] = v;
+  R* mac = reinterpret_cast<R*>(smem);   // [T][3 columns][rho - 1, u, v]
+  R* raw = mac + 9 * T;                  // [T][A_0, A_2, A_4 at L; A_1, A_5, A_8 at L-1]
+  {
+    // window row t is lattice row y0 - 1 + t (wrapped): its 27 stored
+    // populations of columns L-2 .. L, all loads issued before any is used
+    const S* src = A + wrap_row(y0 - 1 + t, m.ny) * m.pitch + (L - 2);
+    R v[9][3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[i][c] = to_r<R>(__ldcg(src + i * m.plane + c));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R h[9] = {v[0][c], v[1][c], v[2][c], v[3][c], v[4][c],
+                      v[5][c], v[6][c], v[7][c], v[8][c]};
+      R d, jx, jy;
+      moments_shifted(h, d, jx, jy);
+      const R rho = R(1) + d;
+      mac[9 * t + 3 * c] = d;
+      mac[9 * t + 3 * c + 1] = jx / rho;
+      mac[9 * t + 3 * c + 2] = jy / rho;
+    }
+    raw[6 * t] = v[0][2];
+    raw[6 * t + 1] = v[2][2];
+    raw[6 * t + 2] = v[4][2];
+    raw[6 * t + 3] = v[1][1];
+    raw[6 * t + 4] = v[5][1];
+    raw[6 * t + 5] = v[8][1];
   }
   __syncthreads();
-  // threads past the last row compute on a wrapped row and write nothing (every
-  // lane of a warp takes part in the tensor-core tuner)
-  const bool active = y < m.ny && !solid(L, y < m.ny ? y : 0);
+  // threads 0 and T-1 (halo rows) and nodes past the last row compute on a
+  // neighbouring row and write nothing: every lane of a warp takes part in the
+  // tensor-core tuner
+  const int tc = t < 1 ? 1 : (t > E ? E : t);   // window row of the node this thread evaluates
+  const int y = y0 + tc - 1;
   const int yy = y < m.ny ? y : m.ny - 1;
+  const bool active = t == tc && y < m.ny && !solid(L, yy);
   const int ym = yy == 0 ? m.ny - 1 : yy - 1;
   const int yp = yy == m.ny - 1 ? 0 : yy + 1;
-  const R* w0 = mac + 9 * ((int)threadIdx.x + 1);   // this node's window row
+  const R* w0 = mac + 9 * tc;
   const bool s_dn = solid(L, ym), s_up = solid(L, yp);
   const R cs2 = R(1) / R(3);
   const R cs = sqrt(cs2);
@@ -804,8 +817,7 @@ __device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int
 #pragma unroll
         for (int k = 0; k < 6; ++k)
           z[k] = (feats[k] - __ldg(net + n_params + k)) / __ldg(net + n_params + 6 + k);
-        tuner_mma_warp(m, z, s,
-                       smem + cbc_mac_bytes<R>(T) + (threadIdx.x >> 5) * kTunerWarpBytes);
+        tuner_mma_warp(m, z, s, smem + cbc_win_bytes<R>(T) + (t >> 5) * kTunerWarpBytes);
       } else {
         tuner_eval<R>(m, feats, s);
       }
@@ -813,10 +825,10 @@ __device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int
     sigma = sigma * sigmoid_r(s[0]);
     if (m.nn_sizes[m.nn_layers] > 1) kappa2 = kappa2 * sigmoid_r(s[1]);
   }
+  if (!active) return;   // the stream-and-collide blocks handle solid nodes
   const Stencil st = stencil();
   const R r0 = st.r0, u0 = st.u0, v0 = st.v0, px = st.px, ux = st.ux, vx = st.vx;
   const R py = st.py, vy = st.vy;
-  if (!active) return;   // the stream-and-collide blocks handle solid nodes
   // Eqs. 20-27 and the Euler step of Eqs. 17-19
   const R rho = R(1) + r0;
   const R pL = cs2 * rho;
@@ -830,15 +842,15 @@ __device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int
   const R dr = r0 + (-(L5 + L1) / (R(2) * cs2) + (T5 + T1) / (R(2) * cs2));   // rho - 1 at t+1
   const R un = u0 + (-(L5 - L1) / (R(2) * rho * cs) + (T5 - T1) / (R(2) * rho * cs));
   const R vn = v0 + (-L3 + T3);
-  // post-stream node (the pulls from x = L + 1 are rebuilt below)
-  const int rc = y * m.pitch, rmo = ym * m.pitch, rpo = yp * m.pitch;
+  // post-stream node: the known pulls from the window (those from x = L + 1
+  // are rebuilt below)
   R h[9];
-  h[0] = to_r<R>(__ldcg(A + 0 * m.plane + rc + L));
-  h[1] = to_r<R>(__ldcg(A + 1 * m.plane + rc + L - 1));
-  h[2] = to_r<R>(__ldcg(A + 2 * m.plane + rmo + L));
-  h[4] = to_r<R>(__ldcg(A + 4 * m.plane + rpo + L));
-  h[5] = to_r<R>(__ldcg(A + 5 * m.plane + rmo + L - 1));
-  h[8] = to_r<R>(__ldcg(A + 8 * m.plane + rpo + L - 1));
+  h[0] = raw[6 * tc];
+  h[2] = raw[6 * (tc - 1) + 1];
+  h[4] = raw[6 * (tc + 1) + 2];
+  h[1] = raw[6 * tc + 3];
+  h[5] = raw[6 * (tc - 1) + 4];
+  h[8] = raw[6 * (tc + 1) + 5];
   // Zou & He with the prescribed state, then Eq. 28 on f_0
   const R sknown = (h[0] + h[2] + h[4]) + R(2) * (h[1] + h[5] + h[8]);   // rho0 + 2 rho+ - 1
   R heq[9];
@@ -854,17 +866,55 @@ __device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int
   if (m.coll == LBM_BGK) collide_bgk<R>(h, sc.omega, drho, uxo, uyo);
   else collide_mrt<R>(h, mrt_of<R>(m), drho, uxo, uyo);
   if (nonfinite(drho)) atomicOr(m.status, DEV_NONFINITE);
-  const int o = rc + L;
+  const int o = y * m.pitch + L;
 #pragma unroll
   for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[i]);
 }
 
 template <typename S>
 __device__ __forceinline__ void ext_dispatch(const StepParams& p, int blk, unsigned char* smem) {
-  const Member& m = p.n_members == 1 ? p.m0 : p.members[p.nn_block_member[blk]];
-  const int local = p.n_members == 1 ? blk : blk - m.nn_first;
-  if (m.ext_kind == 1) nn_block<S>(p, m, local, smem);
-  else cbc_block<S>(p, m, local, smem);
+  if (p.n_members == 1) {
+    if (p.m0.ext_kind == 1) nn_block<S>(p, p.m0, blk, smem);
+    else cbc_block<S>(p, p.m0, blk, smem);
+    return;
+  }
+  // the block's member record staged in shared memory once (coalesced), so
+  // the boundary code reads its fields without global round trips
+  __shared__ __align__(16) Member s_ext;
+  constexpr int kWords = (int)(sizeof(Member) / sizeof(uint64_t));
+  if (threadIdx.x < 32) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(p.members + p.nn_block_member[blk]);
+    uint64_t* dst = reinterpret_cast<uint64_t*>(&s_ext);
+    for (int w = threadIdx.x; w < kWords; w += 32) dst[w] = src[w];
+  }
+  __syncthreads();
+  const int local = blk - s_ext.nn_first;
+  if (s_ext.ext_kind == 1) nn_block<S>(p, s_ext, local, smem);
+  else cbc_block<S>(p, s_ext, local, smem);
+}
+
+// Block roles of a step launch: first one force-reduction block per member
+// (they sum the previous step's partials and finish within microseconds),
+// then the stream-and-collide and boundary blocks in the order of the launch
+// table p.launch_order (entry v >= 0: stream-and-collide block v; v < 0:
+// boundary block -v - 1), or, without boundary blocks, the stream-and-collide
+// blocks in order.  The host places each boundary block next to the strips of
+// its lattice's east tile that cover its rows, so the two read (and write)
+// the same sectors of the east columns while they are in L2, instead of each
+// fetching them from DRAM; when the whole grid is resident at once (or on the
+// resident-sized grids, whose blocks live for the whole step) the boundary
+// blocks come first, where their longer dependent chains start at once.
+enum : int { ROLE_REDUCE = 0, ROLE_BOUNDARY = 1, ROLE_BULK = 2 };
+struct BlockRole {
+  int kind, idx;
+};
+__device__ __forceinline__ BlockRole block_role(const StepParams& p) {
+  const int g = (int)blockIdx.x;
+  if (g < p.n_members) return {ROLE_REDUCE, g};
+  const int r = g - p.n_members;
+  if (!p.launch_order) return {ROLE_BULK, r};
+  const int v = __ldg(p.launch_order + r);
+  return v >= 0 ? BlockRole{ROLE_BULK, v} : BlockRole{ROLE_BOUNDARY, -v - 1};
 }
 
 template <typename S, int COLL, int MINB, bool EXT>
@@ -873,18 +923,17 @@ __global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
   extern __shared__ __align__(16) unsigned char nn_smem[];   // boundary blocks only
   pdl_launch_dependents();
   pdl_wait();
-  if (EXT && (int)blockIdx.x < p.nn_blocks) {
-    ext_dispatch<S>(p, (int)blockIdx.x, nn_smem);
+  const BlockRole role = block_role(p);
+  if (EXT && role.kind == ROLE_BOUNDARY) {
+    ext_dispatch<S>(p, role.idx, nn_smem);
     return;
   }
-  // force-reduction blocks of the previous step come next, ahead of the
-  // stream-and-collide blocks, so they finish early
   const int64_t t = step_index(p);
-  if ((int)blockIdx.x < p.nn_blocks + p.n_members) {
-    if (p.reduce_prev && t >= 1) reduce_force(p, (int)blockIdx.x - p.nn_blocks, t - 1);
+  if (role.kind == ROLE_REDUCE) {
+    if (p.reduce_prev && t >= 1) reduce_force(p, role.idx, t - 1);
     return;
   }
-  const int b = (int)blockIdx.x - p.nn_blocks - p.n_members;   // stream-and-collide block
+  const int b = role.idx;   // stream-and-collide block
   const int nblocks = (int)gridDim.x - p.nn_blocks - p.n_members;
   double fx = 0.0, fy = 0.0;
   bool touched = false, bad = false;
@@ -1004,7 +1053,7 @@ __device__ __forceinline__ void row_segments(int a, int b, int ny, F fn) {
 
 // rows of one boundary block of member m
 __device__ __forceinline__ int ext_rows(const Member& m) {
-  return m.ext_kind == 1 ? kNnNodes : kBulkThreads;
+  return m.ext_kind == 1 ? kNnNodes : cbc_block_rows(kBulkThreads);
 }
 
 // One poll: have the east-tile strips (if `strips`) and the boundary blocks (if
@@ -1227,7 +1276,7 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
   }
   // the block's force partial: its strip's slot when partials go per strip
   // (recomputed here rather than kept live through the loop)
-  const int bb = (int)blockIdx.x - p.nn_blocks - p.n_members;
+  const int bb = block_role(p).idx;
   const int sgb = p.strip_order ? p.strip_order[bb] : bb;
   const int slot = p.strip_force ? p.strip_force[sgb] : sgb;
   // dataflow (one strip per block: sgb is the strip's index in the table):
@@ -1460,8 +1509,9 @@ template <typename S, int COLL, int NS, int MINB, bool EXT, bool DYN>
 __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const StepParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   pdl_launch_dependents();
-  if (EXT && (int)blockIdx.x < p.nn_blocks) {
-    const int blk = (int)blockIdx.x;
+  const BlockRole role = block_role(p);
+  if (EXT && role.kind == ROLE_BOUNDARY) {
+    const int blk = role.idx;
     if (p.strip_done) {
       // dataflow: wait for the east strips and boundary blocks of step t-1
       // that meet this block's rows +- 2
@@ -1488,18 +1538,16 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
     }
     return;
   }
-  // force-reduction blocks of the previous step come next, ahead of the
-  // stream-and-collide blocks, so they finish early
-  if ((int)blockIdx.x < p.nn_blocks + p.n_members) {
+  if (role.kind == ROLE_REDUCE) {
     pdl_wait();
     const int64_t t = step_index(p);
     if (p.reduce_prev && t >= 1) {
-      reduce_force(p, (int)blockIdx.x - p.nn_blocks, t - 1);
-      publish_reduced(p, (int)blockIdx.x - p.nn_blocks, t - 1);
+      reduce_force(p, role.idx, t - 1);
+      publish_reduced(p, role.idx, t - 1);
     }
     return;
   }
-  const int b = (int)blockIdx.x - p.nn_blocks - p.n_members;   // stream-and-collide block
+  const int b = role.idx;   // stream-and-collide block
   const int nblocks = (int)gridDim.x - p.nn_blocks - p.n_members;
   // one block per strip: the strip order puts strips holding solid nodes first,
   // so their extra work overlaps the rest instead of trailing it

@@ -177,7 +177,7 @@ def test_waits_cover_every_dependency(seed):
         nx = rng.choice([1, 2, 3, 5, 127, 128, 129, 131, 132, 133, 200, 255, 256, 260, 390])
         ny = rng.randint(1, 30)
         rows = rng.randint(2, 9)
-        per = 8 if ext == "nn" else rng.choice([3, 5, 160])   # CBC: the block size
+        per = 8 if ext == "nn" else rng.choice([3, 5, 126, 158])   # CBC: block size - 2
         if nx * ny > 6000:
             continue
         lat = Lattice(nx, ny, rows, ext, per, periodic, random_solid(nx, ny, rng, 0.1))
@@ -186,9 +186,10 @@ def test_waits_cover_every_dependency(seed):
 
 
 def test_waits_cover_tall_cbc_blocks():
-    """Characteristic-outflow blocks of 160 rows over several strip rows."""
+    """Characteristic-outflow blocks of 158 rows (160 threads, one halo row on
+    each side) over several strip rows."""
     for nx, ny, rows in [(131, 400, 40), (5, 333, 16), (260, 170, 24)]:
-        check(Lattice(nx, ny, rows, "cbc", 160, False, set()))
+        check(Lattice(nx, ny, rows, "cbc", 158, False, set()))
 
 
 def test_a_narrower_rule_misses_dependencies():
