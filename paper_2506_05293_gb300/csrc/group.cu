@@ -157,8 +157,8 @@ void build_launch_order(Group& g, const std::vector<Member>& ms, const std::vect
       const int kind = ext_kind(g.sims[k]);
       if (!kind) continue;
       const Member& m = ms[(size_t)k];
-      const int per = step_ext_rows(g.variant, kind);
-      const int blocks_k = step_ext_blocks(m.ny, g.variant, kind);
+      const int per = step_ext_rows(g.variant, kind, g.prec);
+      const int blocks_k = step_ext_blocks(m.ny, g.variant, kind, g.prec);
       for (int j = 0; j < blocks_k; ++j, ++nb) {
         const int y_mid = std::min(m.ny - 1, j * per + per / 2);
         const int ls = (y_mid / g.rows) * m.tiles_x + (m.tiles_x - 1);
@@ -206,7 +206,8 @@ void build_table(Group& g) {
     const int kind = ext_kind(g.sims[k]);
     if (!kind) continue;
     ms[(size_t)k].nn_first = (int32_t)nb.size();
-    const int c = step_ext_blocks(g.sims[k]->ny, g.variant, kind);
+    ms[(size_t)k].ext_rows = step_ext_rows(g.variant, kind, g.prec);
+    const int c = step_ext_blocks(g.sims[k]->ny, g.variant, kind, g.prec);
     for (int j = 0; j < c; ++j) nb.push_back(k);
   }
   g.nn_blocks = (int)nb.size();

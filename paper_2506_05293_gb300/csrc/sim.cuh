@@ -63,6 +63,7 @@ struct Member {
   int32_t nn_act;
   int32_t nn_sizes[LBM_MLP_MAX_LAYERS + 1];
   int32_t nn_first;       // first boundary block of this member in the launch
+  int32_t ext_rows;       // east nodes (rows) of one boundary block
 };
 
 // Parameters of one launch of a step kernel.
@@ -124,8 +125,8 @@ void launch_set_t(int64_t* t_base, int64_t value, cudaStream_t s);
 void launch_step_ext(int prec, int coll, const StepParams& p, int variant, int blocks,
                      cudaStream_t s);   // launches with boundary blocks (step_ext.cu)
 int step_strips(int nx, int ny, int rows);
-int step_ext_blocks(int ny, int variant, int ext_kind);  // boundary blocks of one member
-int step_ext_rows(int variant, int ext_kind);             // east nodes of one boundary block
+int step_ext_blocks(int ny, int variant, int ext_kind, int prec);  // boundary blocks of a member
+int step_ext_rows(int variant, int ext_kind, int prec);             // east nodes of one of them
 bool step_variant_is_bulk(int variant);
 bool step_variant_streams(int variant);   // staged variant with a fixed share per block
 bool step_variant_dynamic(int variant);   // staged variant taking strips from a counter

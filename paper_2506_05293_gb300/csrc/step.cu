@@ -74,14 +74,15 @@ int step_strips(int nx, int ny, int rows) {
   return ((nx + 127) / 128) * ((ny + rows - 1) / rows);
 }
 
-int step_ext_rows(int variant, int ext_kind) {
-  // NN: kNnNodes nodes per block; CBC: one node per thread but the first and last
-  return ext_kind == 1 ? kNnNodes
-                       : cbc_block_rows(step_variant_is_bulk(variant) ? kBulkThreads : 128);
+int step_ext_rows(int variant, int ext_kind, int prec) {
+  // NN: kNnTcNodes nodes per block on the tensor cores (FP32 / FP16 storage),
+  // kNnNodes with FP64; CBC: one node per thread but the first and last
+  if (ext_kind == 1) return prec == LBM_FP64 ? kNnNodes : kNnTcNodes;
+  return cbc_block_rows(step_variant_is_bulk(variant) ? kBulkThreads : 128);
 }
 
-int step_ext_blocks(int ny, int variant, int ext_kind) {
-  const int per = step_ext_rows(variant, ext_kind);
+int step_ext_blocks(int ny, int variant, int ext_kind, int prec) {
+  const int per = step_ext_rows(variant, ext_kind, prec);
   return (ny + per - 1) / per;
 }
 

@@ -367,12 +367,20 @@ __device__ __forceinline__ void reg_strip(const StepParams& p, const Member& m,
   }
 }
 
+// row index y wrapped into [0, ny) (y may lie any number of lattices away)
+__device__ __forceinline__ int wrap_row(int y, int ny) {
+  y %= ny;
+  return y < 0 ? y + ny : y;
+}
+
 // ---- fused network blocks of the NN direct-reconstruction outflow -----------
-// (Sec. 3.1, Eq. 15.)  The first p.nn_blocks blocks of a step launch rebuild
-// the east fluid nodes of the members with a network outflow, concurrently
-// with the stream-and-collide blocks: they read only the source buffer and
-// write only the east column, which the other blocks leave to them.  A block
-// takes kNnNodes consecutive east nodes.  For each layer its warps split the
+// (Sec. 3.1, Eq. 15.)  Boundary blocks of the step launch rebuild the east
+// fluid nodes of the members with a network outflow, concurrently with the
+// stream-and-collide blocks: they read only the source buffer and write only
+// the east column, which the other blocks leave to them.  With FP32 or FP16
+// storage a block takes kNnTcNodes east nodes and runs the network on the
+// tensor cores (nn_block_tc below).  With FP64 storage a block takes
+// kNnNodes consecutive east nodes.  For each layer its warps split the
 // inputs k: warp w sums its slice of k for every node and unit (lane j holds
 // units j and j + 32; inputs are broadcast from shared memory; the transposed
 // weights, row k = input k's weights to every unit, stream through L1 with
@@ -397,6 +405,217 @@ __device__ __forceinline__ R post_stream_h(const S* __restrict__ A, const Member
   sy = sy < 0 ? sy + m.ny : (sy >= m.ny ? sy - m.ny : sy);
   const int sx = x - cx(k);
   return to_r<R>(__ldcg(A + k * m.plane + sy * m.pitch + sx));
+}
+
+// ---- the network on the tensor cores (FP32 and FP16 storage) -----------------
+// A block takes kNnTcNodes = 16 east nodes, the m-dimension of one mma tile.
+// (1) One round of loads stages the window the block needs: the nine stored
+// populations of columns L-4 .. L at rows y0-2 .. y0+17 (every pull of the
+// 81 inputs of its nodes and of the nodes themselves) and the solid bits of
+// those rows.  (2) The 81 inputs of every node are formed in shared memory
+// (post-stream values: pulls, reversed at solid nodes; z-scored), zero-padded
+// to K = 88.  (3) Each layer is one GEMM [16 x K] x [K x N] with
+// mma.sync m16n8k8 on TF32 operands split into high and low parts (3xTF32:
+// hi*hi + hi*lo + lo*hi, FP32 accumulators initialised with the bias), which
+// keeps the products to FP32 accuracy; the warps take the layer's 8-column
+// n-tiles in turn, the transposed weights come through L1.  (4) One thread
+// per node applies Eq. 15 with the Zou & He fallback and collides.
+constexpr int kNnTcNodes = 16;                 // east nodes per tensor-core network block
+constexpr int kNnTcWin = kNnTcNodes + 4;       // window rows y0-2 .. y0+17
+constexpr int kNnTcLdIn = 92;                  // row stride of the input tile (88 used; 92 = 28
+                                               // mod 32 keeps the fragment loads conflict-free)
+constexpr int kNnTcLdAct = 68;                 // row stride of hidden activations (64 used)
+
+__host__ __device__ constexpr size_t nn_tc_smem_bytes() {
+  return (size_t)9 * kNnTcWin * 5 * 4 + 32 + (size_t)kNnTcNodes * kNnTcLdIn * 4 +
+         (size_t)kNnTcNodes * kNnTcLdAct * 4;
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x = hi + lo (approximately), both TF32
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32_1688(float c[4], const uint32_t a[4], uint32_t b0,
+                                              uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// out[16][n_out] = act(in[16][n_in] W^T + b) for the block's 16 nodes; in is
+// zero-padded to a multiple of 8 columns (row stride ldi), out gets the padded
+// columns too (zero weights and bias: act(0) = 0).  Wt is the transposed
+// weight matrix [n_in][n_out] (global, read through L1), bias [n_out].
+__device__ inline void nn_layer_tc(const float* in, int ldi, int n_in, float* out, int ldo,
+                                   int n_out, const float* __restrict__ Wt,
+                                   const float* __restrict__ bias, bool hidden, int act) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  const int g = lane >> 2, t4 = lane & 3;
+  const int K8 = (n_in + 7) / 8, N8 = (n_out + 7) / 8;
+  for (int j = warp; j < N8; j += nw) {
+    const int n = j * 8 + g;            // this lane's column of B
+    const int nc = j * 8 + 2 * t4;      // this lane's columns of C
+    float c[4];
+    c[0] = nc < n_out ? __ldg(bias + nc) : 0.f;
+    c[1] = nc + 1 < n_out ? __ldg(bias + nc + 1) : 0.f;
+    c[2] = c[0];
+    c[3] = c[1];
+#pragma unroll 2
+    for (int kk = 0; kk < K8; ++kk) {
+      const int k0 = kk * 8 + t4;
+      uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
+      tf32_split(in[g * ldi + k0], ah[0], al[0]);
+      tf32_split(in[(g + 8) * ldi + k0], ah[1], al[1]);
+      tf32_split(in[g * ldi + k0 + 4], ah[2], al[2]);
+      tf32_split(in[(g + 8) * ldi + k0 + 4], ah[3], al[3]);
+      const float w0 = (n < n_out && k0 < n_in) ? __ldg(Wt + k0 * n_out + n) : 0.f;
+      const float w1 = (n < n_out && k0 + 4 < n_in) ? __ldg(Wt + (k0 + 4) * n_out + n) : 0.f;
+      tf32_split(w0, bh0, bl0);
+      tf32_split(w1, bh1, bl1);
+      mma_tf32_1688(c, al, bh0, bh1);   // the small terms first
+      mma_tf32_1688(c, ah, bl0, bl1);
+      mma_tf32_1688(c, ah, bh0, bh1);
+    }
+    if (hidden) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[q] = act_hidden<float>(c[q], act);
+    }
+    out[g * ldo + nc] = c[0];
+    out[g * ldo + nc + 1] = c[1];
+    out[(g + 8) * ldo + nc] = c[2];
+    out[(g + 8) * ldo + nc + 1] = c[3];
+  }
+}
+
+template <typename S>
+__device__ __noinline__ void nn_block_tc(const StepParams& p, const Member& m, int local_block,
+                                         unsigned char* smem) {
+  constexpr int G = kNnTcNodes, WR = kNnTcWin;
+  constexpr int NWIN = 9 * WR * 5;
+  const int T = (int)blockDim.x;
+  const int y0 = local_block * G;
+  const int L = m.nx - 1;
+  const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
+  S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
+  const float* __restrict__ net = static_cast<const float*>(m.nn_net);
+  float* win = reinterpret_cast<float*>(smem);                      // [9][WR][5]
+  uint8_t* sol = reinterpret_cast<uint8_t*>(win + NWIN);            // [WR] solid bits of L-4 .. L
+  float* buf0 = reinterpret_cast<float*>(sol + 32);                 // [G][kNnTcLdIn]
+  float* buf1 = buf0 + G * kNnTcLdIn;                               // [G][kNnTcLdAct]
+  // (1) the window: A_i at rows y0-2+r, columns L-4+c; every load of a thread
+  // issued before any is used
+#pragma unroll
+  for (int q = 0; q < (NWIN + 127) / 128; ++q) {
+    const int e = (int)threadIdx.x + q * T;
+    if (e < NWIN) {
+      const int i = e / (WR * 5), r = (e / 5) % WR, c = e % 5;
+      const int yy = wrap_row(y0 - 2 + r, m.ny);
+      win[e] = to_r<float>(__ldcg(A + i * m.plane + yy * m.pitch + (L - 4 + c)));
+    }
+  }
+  if ((int)threadIdx.x < WR) {
+    const int yy = wrap_row(y0 - 2 + (int)threadIdx.x, m.ny);
+    const uint32_t* row = m.solid_bits + yy * m.words_per_row;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const int x = L - 4 + c;
+      bits |= ((__ldg(row + (x >> 5)) >> (x & 31)) & 1u) << c;
+    }
+    sol[threadIdx.x] = (uint8_t)bits;
+  }
+  __syncthreads();
+  // post-stream h_i at window row r, column c (bounce-back at solid nodes)
+  auto post = [&](int r, int c, int i) -> float {
+    const bool solid = (sol[r] >> c) & 1u;
+    const int k = solid ? opp(i) : i;
+    return win[(k * WR + r - cy(k)) * 5 + c - cx(k)];
+  };
+  int n_params = 0;
+  for (int l = 0; l < m.nn_layers; ++l)
+    n_params += m.nn_sizes[l] * m.nn_sizes[l + 1] + m.nn_sizes[l + 1];
+  const float* in_mean = net + n_params;
+  const float* in_std = in_mean + 81;
+  // (2) inputs, index k*27 + j*9 + i: column L-1-k, row y-1+j, population i
+  for (int e = threadIdx.x; e < G * 88; e += T) {
+    const int n = e / 88, kx = e - 88 * n;
+    float v = 0.f;
+    if (kx < 81) {
+      const int col = kx / 27, j = (kx / 9) % 3, i = kx % 9;
+      v = (post(n + j + 1, 3 - col, i) + wgt<float>(i) - __ldg(in_mean + kx)) / __ldg(in_std + kx);
+    }
+    buf0[n * kNnTcLdIn + kx] = v;
+  }
+  __syncthreads();
+  // (3) the layers, alternating between the two buffers
+  int off = 0;
+  float* cur = buf0;
+  int ld = kNnTcLdIn;
+  for (int l = 0; l < m.nn_layers; ++l) {
+    const int n_in = m.nn_sizes[l], n_out = m.nn_sizes[l + 1];
+    const bool last = l == m.nn_layers - 1;
+    float* nxt = cur == buf0 ? buf1 : buf0;
+    nn_layer_tc(cur, ld, n_in, nxt, kNnTcLdAct, n_out, net + off, net + off + n_in * n_out,
+                !last, m.nn_act);
+    __syncthreads();
+    off += n_in * n_out + n_out;
+    cur = nxt;
+    ld = kNnTcLdAct;
+  }
+  // (4) Eq. 15 with the Zou & He fallback, then collision; one thread per node
+  const int n = threadIdx.x;
+  const int y = y0 + n;
+  if (n >= G || y >= m.ny) return;
+  if ((sol[n + 2] >> 4) & 1u) return;   // a solid east node: the stream-and-collide blocks
+  const Scalars<float> sc(m);
+  // pulled populations of (L, y) from the window (those from x = L + 1 are rebuilt)
+  float h[9];
+  h[0] = win[(0 * WR + n + 2) * 5 + 4];
+  h[1] = win[(1 * WR + n + 2) * 5 + 3];
+  h[2] = win[(2 * WR + n + 1) * 5 + 4];
+  h[4] = win[(4 * WR + n + 3) * 5 + 4];
+  h[5] = win[(5 * WR + n + 1) * 5 + 3];
+  h[8] = win[(8 * WR + n + 3) * 5 + 3];
+  h[3] = h[6] = h[7] = 0.f;
+  const float scale = (float)m.nn_out_scale;
+  const float s3 = scale * cur[n * kNnTcLdAct + 0];
+  const float s6 = scale * cur[n * kNnTcLdAct + 1];
+  const float s7 = scale * cur[n * kNnTcLdAct + 2];
+  float hn[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) hn[i] = h[i];
+  // g_i(L) = f_i(L-1) + s_i, the bases taken post-stream at (L-1, y)
+  hn[3] = post(n + 2, 3, 3) + s3;
+  hn[6] = post(n + 2, 3, 6) + s6;
+  hn[7] = post(n + 2, 3, 7) + s7;
+  float drho_n, jx_n, jy_n;
+  moments_shifted(hn, drho_n, jx_n, jy_n);
+  bool ok = !nonfinite(s3) && !nonfinite(s6) && !nonfinite(s7);
+  ok = ok && (hn[3] + wgt<float>(3) >= 0.f) && (hn[6] + wgt<float>(6) >= 0.f) &&
+       (hn[7] + wgt<float>(7) >= 0.f);
+  ok = ok && (fabsf((1.f + drho_n) - sc.rho_out) <= (float)m.nn_drho);
+  if (ok) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = hn[i];
+  } else {
+    zouhe_east<float>(h, sc.rho_out);
+    atomicAdd(m.nn_fallbacks, 1ull);
+  }
+  float drho, ux, uy;
+  if (m.coll == LBM_BGK) collide_bgk<float>(h, sc.omega, drho, ux, uy);
+  else collide_mrt<float>(h, mrt_of<float>(m), drho, ux, uy);
+  if (nonfinite(drho)) atomicOr(m.status, DEV_NONFINITE);
+  const int o = y * m.pitch + L;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[i]);
 }
 
 template <typename S>
@@ -524,12 +743,6 @@ __device__ __noinline__ void nn_block(const StepParams& p, const Member& m, int 
   const int o = rc + L;
 #pragma unroll
   for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[i]);
-}
-
-// row index y wrapped into [0, ny) (y may lie any number of lattices away)
-__device__ __forceinline__ int wrap_row(int y, int ny) {
-  y %= ny;
-  return y < 0 ? y + ny : y;
 }
 
 // ---- characteristic outflow blocks (Sec. 4, Eqs. 17-28) ----------------------
@@ -871,10 +1084,19 @@ __device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int
   for (int i = 0; i < 9; ++i) B[i * m.plane + o] = from_r<S>(h[i]);
 }
 
+// the network block of the storage precision: tensor cores for FP32 / FP16,
+// FP64 on the FP64 pipe
+template <typename S>
+__device__ __forceinline__ void nn_dispatch(const StepParams& p, const Member& m, int blk,
+                                            unsigned char* smem) {
+  if constexpr (sizeof(typename Compute<S>::R) == 4) nn_block_tc<S>(p, m, blk, smem);
+  else nn_block<S>(p, m, blk, smem);
+}
+
 template <typename S>
 __device__ __forceinline__ void ext_dispatch(const StepParams& p, int blk, unsigned char* smem) {
   if (p.n_members == 1) {
-    if (p.m0.ext_kind == 1) nn_block<S>(p, p.m0, blk, smem);
+    if (p.m0.ext_kind == 1) nn_dispatch<S>(p, p.m0, blk, smem);
     else cbc_block<S>(p, p.m0, blk, smem);
     return;
   }
@@ -889,7 +1111,7 @@ __device__ __forceinline__ void ext_dispatch(const StepParams& p, int blk, unsig
   }
   __syncthreads();
   const int local = blk - s_ext.nn_first;
-  if (s_ext.ext_kind == 1) nn_block<S>(p, s_ext, local, smem);
+  if (s_ext.ext_kind == 1) nn_dispatch<S>(p, s_ext, local, smem);
   else cbc_block<S>(p, s_ext, local, smem);
 }
 
@@ -1052,9 +1274,7 @@ __device__ __forceinline__ void row_segments(int a, int b, int ny, F fn) {
 }
 
 // rows of one boundary block of member m
-__device__ __forceinline__ int ext_rows(const Member& m) {
-  return m.ext_kind == 1 ? kNnNodes : cbc_block_rows(kBulkThreads);
-}
+__device__ __forceinline__ int ext_rows(const Member& m) { return m.ext_rows; }
 
 // One poll: have the east-tile strips (if `strips`) and the boundary blocks (if
 // `exts`) of member m whose rows meet a..b completed t steps?
@@ -1615,13 +1835,14 @@ inline void launch_pdl(Kernel kernel, int grid, int threads, size_t smem, cudaSt
 template <typename R>
 inline size_t ext_bulk_smem(size_t ring) {
   size_t v = ring;
-  v = v > nn_smem_bytes<R>(kBulkThreads / 32) ? v : nn_smem_bytes<R>(kBulkThreads / 32);
+  const size_t nn = sizeof(R) == 4 ? nn_tc_smem_bytes() : nn_smem_bytes<R>(kBulkThreads / 32);
+  v = v > nn ? v : nn;
   return v > cbc_smem_bytes<R>(kBulkThreads) ? v : cbc_smem_bytes<R>(kBulkThreads);
 }
 template <typename R>
 inline size_t ext_reg_smem() {
-  return nn_smem_bytes<R>(4) > cbc_smem_bytes<R>(128) ? nn_smem_bytes<R>(4)
-                                                      : cbc_smem_bytes<R>(128);
+  const size_t nn = sizeof(R) == 4 ? nn_tc_smem_bytes() : nn_smem_bytes<R>(4);
+  return nn > cbc_smem_bytes<R>(128) ? nn : cbc_smem_bytes<R>(128);
 }
 
 template <typename S, int COLL, int MINB, bool EXT, bool DYN>

@@ -177,7 +177,7 @@ def test_waits_cover_every_dependency(seed):
         nx = rng.choice([1, 2, 3, 5, 127, 128, 129, 131, 132, 133, 200, 255, 256, 260, 390])
         ny = rng.randint(1, 30)
         rows = rng.randint(2, 9)
-        per = 8 if ext == "nn" else rng.choice([3, 5, 126, 158])   # CBC: block size - 2
+        per = rng.choice([8, 16]) if ext == "nn" else rng.choice([3, 5, 126, 158])
         if nx * ny > 6000:
             continue
         lat = Lattice(nx, ny, rows, ext, per, periodic, random_solid(nx, ny, rng, 0.1))
