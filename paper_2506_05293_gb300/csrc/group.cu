@@ -62,6 +62,7 @@ void fill_member(const lbm_sim* s, Member& m) {
     if (s->nn.n_layers > 0) {
       m.nn_net = s->prec == LBM_FP64 ? (const void*)s->nn.params_d : (const void*)s->nn.params_f;
       m.nn_bf16 = s->nn.params_bf16;
+      m.nn_blob_elems = s->nn.blob_elems;
       m.nn_layers = s->nn.n_layers;
       m.nn_act = s->nn.act;
       for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) m.nn_sizes[l] = s->nn.sizes[l];
@@ -369,6 +370,13 @@ StepParams params(const Group& g, int q) {
   p.nn_blocks = g.nn_blocks;
   p.nn_block_member = g.d_nn_block_member;
   p.launch_order = g.nn_blocks > 0 ? g.d_launch_order : nullptr;
+  p.nn_blob_max = 0;
+  p.has_cbc = 0;
+  for (const lbm_sim* s : g.sims) {
+    const int kind = ext_kind(s);
+    if (kind == 1) p.nn_blob_max = std::max(p.nn_blob_max, (int32_t)s->nn.blob_elems);
+    if (kind == 2) p.has_cbc = 1;
+  }
   p.dyn_ctr = g.dyn_ctr;
   p.strip_force = g.use_strip_force ? g.d_strip_force : nullptr;
   p.strip_order = g.use_strip_force ? g.d_strip_order : nullptr;

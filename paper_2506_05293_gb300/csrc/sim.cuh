@@ -64,6 +64,7 @@ struct Member {
   int32_t nn_sizes[LBM_MLP_MAX_LAYERS + 1];
   int32_t nn_first;       // first boundary block of this member in the launch
   int32_t ext_rows;       // east nodes (rows) of one boundary block
+  int32_t nn_blob_elems;  // floats of the network blob (copied whole into shared memory)
 };
 
 // Parameters of one launch of a step kernel.
@@ -87,6 +88,8 @@ struct StepParams {
   unsigned long long* dyn_ctr;   // variant 5: [next strip, finished blocks], zero between launches
   int32_t dyn_strips;            // variant 5: strips of the whole table
   int32_t nn_blocks;             // boundary blocks of the grid
+  int32_t nn_blob_max;           // largest network blob (floats) of the launch's NN members
+  int32_t has_cbc;               // the launch has characteristic-outflow members
   const int32_t* launch_order;   // with boundary blocks: the role of each block after the
                                  // force-reduction blocks (>= 0 stream-and-collide block,
                                  // < 0 boundary block -v - 1); null: all stream-and-collide

@@ -11,14 +11,20 @@ namespace {
 
 template <typename S, int COLL>
 void set_bulk_smem_attr() {
-  using R = typename Compute<S>::R;
   static bool done = false;
   if (done) return;
-  const size_t smem = ext_bulk_smem<R>(step_bulk_smem(prec_of<S>(), kBulkSlots));
+  // a cap: each launch passes what its members need (ext_need)
+  const int cap = kExtSmemCap;
   cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true, false>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true, true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(step_kernel<S, COLL, 6, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(step_kernel<S, COLL, 8, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(step_kernel<S, COLL, 10, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   done = true;
 }
 

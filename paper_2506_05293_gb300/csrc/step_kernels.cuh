@@ -367,6 +367,50 @@ __device__ __forceinline__ void reg_strip(const StepParams& p, const Member& m,
   }
 }
 
+// ---- shared-memory barriers and bulk copies (bounded waits) -----------------
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or the hint (ns) elapses, instead of spinning
+constexpr uint32_t kSuspendHintNs = 1000000;   // 1 ms per attempt
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr uint32_t kWaitLimit = 2000;   // attempts (x the 1 ms hint) before a wait gives up
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t k = 0; k < kWaitLimit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // row index y wrapped into [0, ny) (y may lie any number of lattices away)
 __device__ __forceinline__ int wrap_row(int y, int ny) {
   y %= ny;
@@ -412,13 +456,15 @@ __device__ __forceinline__ R post_stream_h(const S* __restrict__ A, const Member
 // (1) One round of loads stages the window the block needs: the nine stored
 // populations of columns L-4 .. L at rows y0-2 .. y0+17 (every pull of the
 // 81 inputs of its nodes and of the nodes themselves) and the solid bits of
-// those rows.  (2) The 81 inputs of every node are formed in shared memory
+// those rows, while one thread copies the whole network (weights and input
+// statistics, about 39 KB for 81-64-64-3) into shared memory with a single
+// cp.async.bulk.  (2) The 81 inputs of every node are formed in shared memory
 // (post-stream values: pulls, reversed at solid nodes; z-scored), zero-padded
 // to K = 88.  (3) Each layer is one GEMM [16 x K] x [K x N] with
 // mma.sync m16n8k8 on TF32 operands split into high and low parts (3xTF32:
 // hi*hi + hi*lo + lo*hi, FP32 accumulators initialised with the bias), which
 // keeps the products to FP32 accuracy; the warps take the layer's 8-column
-// n-tiles in turn, the transposed weights come through L1.  (4) One thread
+// n-tiles in turn, reading the weights from shared memory.  (4) One thread
 // per node applies Eq. 15 with the Zou & He fallback and collides.
 constexpr int kNnTcNodes = 16;                 // east nodes per tensor-core network block
 constexpr int kNnTcWin = kNnTcNodes + 4;       // window rows y0-2 .. y0+17
@@ -426,9 +472,15 @@ constexpr int kNnTcLdIn = 92;                  // row stride of the input tile (
                                                // mod 32 keeps the fragment loads conflict-free)
 constexpr int kNnTcLdAct = 68;                 // row stride of hidden activations (64 used)
 
-__host__ __device__ constexpr size_t nn_tc_smem_bytes() {
+// shared memory of a tensor-core network block: the network blob (per layer
+// W^T then b, in_mean, in_std; blob_elems floats, a multiple of 4), then the
+// window, solid bits, the two activation tiles and the copy's mbarrier
+__host__ __device__ constexpr size_t nn_tc_fixed_bytes() {
   return (size_t)9 * kNnTcWin * 5 * 4 + 32 + (size_t)kNnTcNodes * kNnTcLdIn * 4 +
-         (size_t)kNnTcNodes * kNnTcLdAct * 4;
+         (size_t)kNnTcNodes * kNnTcLdAct * 4 + 16;
+}
+__host__ __device__ constexpr size_t nn_tc_smem_bytes(int blob_elems) {
+  return (size_t)blob_elems * 4 + nn_tc_fixed_bytes();
 }
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
@@ -453,51 +505,81 @@ __device__ __forceinline__ void mma_tf32_1688(float c[4], const uint32_t a[4], u
 // out[16][n_out] = act(in[16][n_in] W^T + b) for the block's 16 nodes; in is
 // zero-padded to a multiple of 8 columns (row stride ldi), out gets the padded
 // columns too (zero weights and bias: act(0) = 0).  Wt is the transposed
-// weight matrix [n_in][n_out] (global, read through L1), bias [n_out].
+// weight matrix [n_in][n_out], bias [n_out], both in shared memory.
 __device__ inline void nn_layer_tc(const float* in, int ldi, int n_in, float* out, int ldo,
-                                   int n_out, const float* __restrict__ Wt,
-                                   const float* __restrict__ bias, bool hidden, int act) {
+                                   int n_out, const float* Wt, const float* bias, bool hidden,
+                                   int act) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
   const int g = lane >> 2, t4 = lane & 3;
   const int K8 = (n_in + 7) / 8, N8 = (n_out + 7) / 8;
-  for (int j = warp; j < N8; j += nw) {
-    const int n = j * 8 + g;            // this lane's column of B
-    const int nc = j * 8 + 2 * t4;      // this lane's columns of C
-    float c[4];
-    c[0] = nc < n_out ? __ldg(bias + nc) : 0.f;
-    c[1] = nc + 1 < n_out ? __ldg(bias + nc + 1) : 0.f;
-    c[2] = c[0];
-    c[3] = c[1];
+  // this warp's n-tiles: warp and warp + nw (N8 <= 8 <= 2 nw: at most two)
+  const int j0 = warp, j1 = warp + nw;
+  const bool has0 = j0 < N8, has1 = j1 < N8;
+  if (!has0) return;
+  float c0[4], c1[4];
+  {
+    const int nc0 = j0 * 8 + 2 * t4, nc1 = j1 * 8 + 2 * t4;
+    c0[0] = nc0 < n_out ? bias[nc0] : 0.f;
+    c0[1] = nc0 + 1 < n_out ? bias[nc0 + 1] : 0.f;
+    c1[0] = has1 && nc1 < n_out ? bias[nc1] : 0.f;
+    c1[1] = has1 && nc1 + 1 < n_out ? bias[nc1 + 1] : 0.f;
+    c0[2] = c0[0];
+    c0[3] = c0[1];
+    c1[2] = c1[0];
+    c1[3] = c1[1];
+  }
+  const int n0 = j0 * 8 + g, n1 = j1 * 8 + g;   // this lane's columns of B
 #pragma unroll 2
-    for (int kk = 0; kk < K8; ++kk) {
-      const int k0 = kk * 8 + t4;
-      uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
-      tf32_split(in[g * ldi + k0], ah[0], al[0]);
-      tf32_split(in[(g + 8) * ldi + k0], ah[1], al[1]);
-      tf32_split(in[g * ldi + k0 + 4], ah[2], al[2]);
-      tf32_split(in[(g + 8) * ldi + k0 + 4], ah[3], al[3]);
-      const float w0 = (n < n_out && k0 < n_in) ? __ldg(Wt + k0 * n_out + n) : 0.f;
-      const float w1 = (n < n_out && k0 + 4 < n_in) ? __ldg(Wt + (k0 + 4) * n_out + n) : 0.f;
-      tf32_split(w0, bh0, bl0);
-      tf32_split(w1, bh1, bl1);
-      mma_tf32_1688(c, al, bh0, bh1);   // the small terms first
-      mma_tf32_1688(c, ah, bl0, bl1);
-      mma_tf32_1688(c, ah, bh0, bh1);
+  for (int kk = 0; kk < K8; ++kk) {
+    const int k0 = kk * 8 + t4;
+    uint32_t ah[4], al[4];
+    tf32_split(in[g * ldi + k0], ah[0], al[0]);
+    tf32_split(in[(g + 8) * ldi + k0], ah[1], al[1]);
+    tf32_split(in[g * ldi + k0 + 4], ah[2], al[2]);
+    tf32_split(in[(g + 8) * ldi + k0 + 4], ah[3], al[3]);
+    const bool ka = k0 < n_in, kb = k0 + 4 < n_in;
+    {
+      uint32_t bh0, bl0, bh1, bl1;
+      tf32_split(n0 < n_out && ka ? Wt[k0 * n_out + n0] : 0.f, bh0, bl0);
+      tf32_split(n0 < n_out && kb ? Wt[(k0 + 4) * n_out + n0] : 0.f, bh1, bl1);
+      mma_tf32_1688(c0, al, bh0, bh1);   // the small terms first
+      mma_tf32_1688(c0, ah, bl0, bl1);
+      mma_tf32_1688(c0, ah, bh0, bh1);
     }
+    if (has1) {
+      uint32_t bh0, bl0, bh1, bl1;
+      tf32_split(n1 < n_out && ka ? Wt[k0 * n_out + n1] : 0.f, bh0, bl0);
+      tf32_split(n1 < n_out && kb ? Wt[(k0 + 4) * n_out + n1] : 0.f, bh1, bl1);
+      mma_tf32_1688(c1, al, bh0, bh1);
+      mma_tf32_1688(c1, ah, bl0, bl1);
+      mma_tf32_1688(c1, ah, bh0, bh1);
+    }
+  }
+  auto store = [&](const float c[4], int j) {
+    float v[4] = {c[0], c[1], c[2], c[3]};
     if (hidden) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) c[q] = act_hidden<float>(c[q], act);
+      for (int q = 0; q < 4; ++q) v[q] = act_hidden<float>(v[q], act);
     }
-    out[g * ldo + nc] = c[0];
-    out[g * ldo + nc + 1] = c[1];
-    out[(g + 8) * ldo + nc] = c[2];
-    out[(g + 8) * ldo + nc + 1] = c[3];
-  }
+    const int nc = j * 8 + 2 * t4;
+    out[g * ldo + nc] = v[0];
+    out[g * ldo + nc + 1] = v[1];
+    out[(g + 8) * ldo + nc] = v[2];
+    out[(g + 8) * ldo + nc + 1] = v[3];
+  };
+  store(c0, j0);
+  if (has1) store(c1, j1);
 }
+
+// The launch's dynamic shared memory seen from the boundary blocks: the same
+// bytes as the kernels' own extern arrays, named here so that the compiler
+// addresses them as shared memory (not through generic pointers).
+extern __shared__ __align__(16) unsigned char ext_dyn_smem[];
 
 template <typename S>
 __device__ __noinline__ void nn_block_tc(const StepParams& p, const Member& m, int local_block,
-                                         unsigned char* smem) {
+                                         unsigned char*) {
+  unsigned char* smem = ext_dyn_smem;
   constexpr int G = kNnTcNodes, WR = kNnTcWin;
   constexpr int NWIN = 9 * WR * 5;
   const int T = (int)blockDim.x;
@@ -505,32 +587,59 @@ __device__ __noinline__ void nn_block_tc(const StepParams& p, const Member& m, i
   const int L = m.nx - 1;
   const S* __restrict__ A = static_cast<const S*>(m.buf[p.q]);
   S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
-  const float* __restrict__ net = static_cast<const float*>(m.nn_net);
-  float* win = reinterpret_cast<float*>(smem);                      // [9][WR][5]
+  float* net = reinterpret_cast<float*>(smem);                      // the network blob
+  float* win = net + m.nn_blob_elems;                               // [9][WR][5]
   uint8_t* sol = reinterpret_cast<uint8_t*>(win + NWIN);            // [WR] solid bits of L-4 .. L
   float* buf0 = reinterpret_cast<float*>(sol + 32);                 // [G][kNnTcLdIn]
   float* buf1 = buf0 + G * kNnTcLdIn;                               // [G][kNnTcLdAct]
-  // (1) the window: A_i at rows y0-2+r, columns L-4+c; every load of a thread
+  uint64_t* bar = reinterpret_cast<uint64_t*>(buf1 + G * kNnTcLdAct);
+  // (1) the network blob by one bulk copy, overlapping the window loads
+  const uint32_t blob_bytes = (uint32_t)m.nn_blob_elems * 4u;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(bar, blob_bytes);
+    bulk_copy_g2s(net, m.nn_net, blob_bytes, bar);
+  }
+  // the window: A_i at rows y0-2+r, columns L-4+c; every load of a thread
   // issued before any is used
+  {
+    constexpr int Q = (NWIN + 127) / 128;
+    float v[Q];
 #pragma unroll
-  for (int q = 0; q < (NWIN + 127) / 128; ++q) {
-    const int e = (int)threadIdx.x + q * T;
-    if (e < NWIN) {
-      const int i = e / (WR * 5), r = (e / 5) % WR, c = e % 5;
-      const int yy = wrap_row(y0 - 2 + r, m.ny);
-      win[e] = to_r<float>(__ldcg(A + i * m.plane + yy * m.pitch + (L - 4 + c)));
+    for (int q = 0; q < Q; ++q) {
+      const int e = (int)threadIdx.x + q * T;
+      v[q] = 0.f;
+      if (e < NWIN) {
+        const int i = e / (WR * 5), r = (e / 5) % WR, c = e % 5;
+        const int yy = wrap_row(y0 - 2 + r, m.ny);
+        v[q] = to_r<float>(__ldcg(A + i * m.plane + yy * m.pitch + (L - 4 + c)));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int e = (int)threadIdx.x + q * T;
+      if (e < NWIN) win[e] = v[q];
     }
   }
   if ((int)threadIdx.x < WR) {
     const int yy = wrap_row(y0 - 2 + (int)threadIdx.x, m.ny);
     const uint32_t* row = m.solid_bits + yy * m.words_per_row;
+    const uint32_t lo = __ldg(row + ((L - 4) >> 5)), hi = __ldg(row + (L >> 5));
     uint32_t bits = 0;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const int x = L - 4 + c;
-      bits |= ((__ldg(row + (x >> 5)) >> (x & 31)) & 1u) << c;
+      bits |= ((((x >> 5) == ((L - 4) >> 5) ? lo : hi) >> (x & 31)) & 1u) << c;
     }
     sol[threadIdx.x] = (uint8_t)bits;
+  }
+  // the copy must land before the weights are read (and before the block may
+  // exit): a bounded wait, which on giving up latches DEV_TIMEOUT and waits once
+  // more so that no copy is left in flight
+  if (threadIdx.x == 0 && !mbar_wait_bounded(bar, 0)) {
+    atomicOr(m.status, DEV_TIMEOUT);
+    mbar_wait_bounded(bar, 0);
   }
   __syncthreads();
   // post-stream h_i at window row r, column c (bounce-back at solid nodes)
@@ -544,15 +653,27 @@ __device__ __noinline__ void nn_block_tc(const StepParams& p, const Member& m, i
     n_params += m.nn_sizes[l] * m.nn_sizes[l + 1] + m.nn_sizes[l + 1];
   const float* in_mean = net + n_params;
   const float* in_std = in_mean + 81;
-  // (2) inputs, index k*27 + j*9 + i: column L-1-k, row y-1+j, population i
-  for (int e = threadIdx.x; e < G * 88; e += T) {
-    const int n = e / 88, kx = e - 88 * n;
-    float v = 0.f;
+  // (2) inputs, index k*27 + j*9 + i: column L-1-k, row y-1+j, population i;
+  // a thread takes one input index for a quarter of the nodes (window offsets
+  // of the pull and of the reversed pull at a solid node computed once)
+  constexpr int NQ = G / 4;
+  for (int e = threadIdx.x; e < 88 * 4; e += T) {
+    const int kx = e % 88, n0 = (e / 88) * NQ;
     if (kx < 81) {
-      const int col = kx / 27, j = (kx / 9) % 3, i = kx % 9;
-      v = (post(n + j + 1, 3 - col, i) + wgt<float>(i) - __ldg(in_mean + kx)) / __ldg(in_std + kx);
+      const int col = kx / 27, j = (kx / 9) % 3, i = kx % 9, o = opp(i);
+      const int c = 3 - col;
+      const float mean = in_mean[kx] - wgt<float>(i), inv = 1.f / in_std[kx];
+      const int off_f = (i * WR + j + 1 - cy(i)) * 5 + c - cx(i);   // node fluid
+      const int off_s = (o * WR + j + 1 - cy(o)) * 5 + c - cx(o);   // node solid
+#pragma unroll
+      for (int n = n0; n < n0 + NQ; ++n) {
+        const bool solid = (sol[n + j + 1] >> c) & 1u;
+        buf0[n * kNnTcLdIn + kx] = (win[(solid ? off_s : off_f) + 5 * n] - mean) * inv;
+      }
+    } else {
+#pragma unroll
+      for (int n = n0; n < n0 + NQ; ++n) buf0[n * kNnTcLdIn + kx] = 0.f;
     }
-    buf0[n * kNnTcLdIn + kx] = v;
   }
   __syncthreads();
   // (3) the layers, alternating between the two buffers
@@ -934,8 +1055,9 @@ __host__ __device__ constexpr size_t cbc_smem_bytes(int threads) {
 
 template <typename S>
 __device__ __noinline__ void cbc_block(const StepParams& p, const Member& m, int local_block,
-                                       unsigned char* smem) {
+                                       unsigned char*) {
   using R = typename Compute<S>::R;
+  unsigned char* smem = ext_dyn_smem;
   const int T = (int)blockDim.x;
   const int E = cbc_block_rows(T);
   const int t = (int)threadIdx.x;
@@ -1185,49 +1307,6 @@ __global__ void __launch_bounds__(128, MINB) step_kernel(const StepParams p) {
 // elements (16 bytes) before the tile, so every copy is 16-byte aligned and
 // the x shifts become fixed offsets.  Waits are bounded: a wait that gives up
 // latches DEV_TIMEOUT and the block drains its copies before it exits.
-
-__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-// try_wait with a suspend-time hint: the thread sleeps in hardware until the
-// phase completes or the hint (ns) elapses, instead of spinning
-constexpr uint32_t kSuspendHintNs = 1000000;   // 1 ms per attempt
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
-                                              uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-constexpr uint32_t kWaitLimit = 2000;   // attempts (x the 1 ms hint) before a wait gives up
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t k = 0; k < kWaitLimit; ++k)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 
 size_t step_bulk_smem(int prec, int stages);   // dynamic shared memory of the staged kernel
 
@@ -1832,18 +1911,28 @@ inline void launch_pdl(Kernel kernel, int grid, int threads, size_t smem, cudaSt
 
 // dynamic shared memory of launches with boundary blocks: the larger of the
 // stream-and-collide need (ring), the network block's and the CBC block's
+// The network blocks need the blob of the largest network of the launch
+// (p.nn_blob_max floats) on top of their window; a launch without network or
+// CBC members asks for no more than its stream-and-collide blocks need, so
+// those keep their occupancy.
 template <typename R>
-inline size_t ext_bulk_smem(size_t ring) {
-  size_t v = ring;
-  const size_t nn = sizeof(R) == 4 ? nn_tc_smem_bytes() : nn_smem_bytes<R>(kBulkThreads / 32);
-  v = v > nn ? v : nn;
-  return v > cbc_smem_bytes<R>(kBulkThreads) ? v : cbc_smem_bytes<R>(kBulkThreads);
+inline size_t ext_need(const StepParams& p, int threads) {
+  size_t v = 0;
+  if (p.nn_blob_max > 0) {
+    const size_t nn = sizeof(R) == 4 ? nn_tc_smem_bytes(p.nn_blob_max)
+                                     : nn_smem_bytes<R>(threads / 32);
+    v = v > nn ? v : nn;
+  }
+  if (p.has_cbc) v = v > cbc_smem_bytes<R>(threads) ? v : cbc_smem_bytes<R>(threads);
+  return v;
 }
 template <typename R>
-inline size_t ext_reg_smem() {
-  const size_t nn = sizeof(R) == 4 ? nn_tc_smem_bytes() : nn_smem_bytes<R>(4);
-  return nn > cbc_smem_bytes<R>(128) ? nn : cbc_smem_bytes<R>(128);
+inline size_t ext_bulk_smem(const StepParams& p, size_t ring) {
+  const size_t e = ext_need<R>(p, kBulkThreads);
+  return ring > e ? ring : e;
 }
+// cap of the dynamic shared memory attribute of the kernels with boundary blocks
+constexpr int kExtSmemCap = 160 * 1024;
 
 template <typename S, int COLL, int MINB, bool EXT, bool DYN>
 void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
@@ -1852,7 +1941,7 @@ void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
   // their first launch
   using R = typename Compute<S>::R;
   size_t smem = step_bulk_smem(prec_of<S>(), kBulkSlots);
-  if (EXT) smem = ext_bulk_smem<R>(smem);
+  if (EXT) smem = ext_bulk_smem<R>(p, smem);
   launch_pdl(step_bulk_kernel<S, COLL, kBulkSlots, MINB, EXT, DYN>, p.nn_blocks + blocks + p.n_members,
              kBulkThreads, smem, s, p);
 }
@@ -1861,7 +1950,7 @@ template <typename S, int COLL, bool EXT>
 void launch_v(const StepParams& p, int variant, int blocks, cudaStream_t s) {
   using R = typename Compute<S>::R;
   const int g = p.nn_blocks + blocks + p.n_members;
-  const size_t dyn = EXT ? ext_reg_smem<R>() : 0;
+  const size_t dyn = EXT ? ext_need<R>(p, 128) : 0;
   switch (variant) {
     case 0: launch_pdl(step_kernel<S, COLL, 6, EXT>, g, 128, dyn, s, p); break;
     case 1: launch_pdl(step_kernel<S, COLL, 8, EXT>, g, 128, dyn, s, p); break;
