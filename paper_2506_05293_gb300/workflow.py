@@ -41,6 +41,7 @@ class Study:
     seed: int = 1
     v_pert_amp: float = 1e-3
     fallback_drho: float = 0.05
+    input_noise: float = 0.0         # training inputs perturbed by N(0, (input_noise std_k)^2)
     precision: str = "fp32"
     autotune: bool = True            # tune every lattice's tiling before it runs
     stream: int = 0
@@ -130,19 +131,42 @@ def capture_rows_needed(st: Study):
     return ((st.t_trans + st.t_stat - st.capture_from) // st.every + 1) * st.ny
 
 
+def perturb_inputs(rows, n_rows, std, level, seed):
+    """A copy of the rows whose 81 inputs carry seeded Gaussian noise of
+    standard deviation level * std_k per input k; the targets (f_3, f_6, f_7 at
+    the plane) are unchanged, so the network learns to rebuild them from a
+    perturbed neighbourhood (the residual it is trained on, target minus the
+    perturbed f(L-1) inputs, then absorbs the perturbation).  Torch tensor
+    operations on the device."""
+    import torch
+    g = torch.Generator(device=rows.device)
+    g.manual_seed(int(seed))
+    out = rows[:n_rows].clone()
+    sd = torch.as_tensor(np.asarray(std, np.float32) * level, device=rows.device)
+    for a in range(0, n_rows, 1 << 20):
+        b = min(n_rows, a + (1 << 20))
+        out[a:b, :81] += torch.randn((b - a, 81), generator=g, device=rows.device) * sd
+    return out
+
+
 def train(st: Study, rows, n_rows, init_layers):
     """Normalisation from the training batches, then Adam over seeded
-    shuffled epochs.  Returns (layers, mean, std, scale, train/val losses)."""
+    shuffled epochs (inputs perturbed when st.input_noise > 0).  Returns
+    (layers, mean, std, scale, train/val losses; validation on clean rows)."""
     ny = st.ny
     n_b = n_rows // ny
     n_train = max(1, int(n_b * st.train_frac))
     mean, std, scale = L.lbm_nn_dataset_stats(rows, n_rows=n_train * ny)
+    train_rows = rows
+    if st.input_noise > 0:
+        train_rows = perturb_inputs(rows, n_rows, std, st.input_noise, st.seed + 29)
     rng = np.random.default_rng(st.seed + 17)
     order = np.concatenate([rng.permutation(n_train) for _ in range(st.epochs)]).astype(np.int32)
     t0 = time.perf_counter()
-    layers, _, _, losses = L.lbm_nn_train(rows, order, init_layers, "tanh", mean, std, scale,
-                                          n_rows=n_rows, batch_rows=ny, lr=st.lr,
+    layers, _, _, losses = L.lbm_nn_train(train_rows, order, init_layers, "tanh", mean, std,
+                                          scale, n_rows=n_rows, batch_rows=ny, lr=st.lr,
                                           stream=st.stream)
+    del train_rows
     st.timings["train_s"] = time.perf_counter() - t0
     st.timings["train_steps"] = int(order.size)
     val_b = np.arange(n_train, n_b) if n_b > n_train else np.arange(n_train)
