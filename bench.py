@@ -224,14 +224,15 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def max_over_ranks(x, device):
+def max_over_ranks(x):
     """The largest value of x over the ranks of the process group (the slowest
-    replica's time); x itself when there is no group."""
+    replica's time); x itself when there is no group.  A host scalar over the
+    host (gloo) group: the replicas exchange nothing on the device."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
         return float(x)
-    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(x)], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -636,7 +637,8 @@ def run_ours(args):
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        # replicas share nothing but the start barrier and the slowest time
+        dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     import __graft_entry__ as ge
     ge.build()
@@ -738,7 +740,7 @@ def run_ours(args):
             diverged.append(member_label(m))
 
     if world > 1:
-        total_ms = max_over_ranks(total_ms, "cuda")
+        total_ms = max_over_ranks(total_ms)
     value = job_glups(world, nodes, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
     batch.destroy()

@@ -17,7 +17,7 @@ def _rank(rank, world, port, out):
     import bench
     dist.init_process_group("gloo", rank=rank, world_size=world)
     ms = [120.0, 180.0][rank]                  # rank 1 is the slower replica
-    m = bench.max_over_ranks(ms, "cpu")
+    m = bench.max_over_ranks(ms)
     v = bench.job_glups(world, 1_000_000, 100, m)
     r, w, lr = bench.dist_env()
     out.put((rank, m, v, r, w, lr))
@@ -44,5 +44,5 @@ def test_two_gloo_ranks_take_the_slowest_time():
 def test_single_process_needs_no_group():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.max_over_ranks(3.5, "cpu") == 3.5
+    assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_glups(1, 10, 10, 1.0) == pytest.approx(1e-4)
