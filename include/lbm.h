@@ -404,8 +404,10 @@ lbm_status lbm_device_state(lbm_sim* sim, void** base, int64_t* pitch, int64_t* 
 /* Tiling of the step kernel: rows per strip (1..4096; a strip is 128 columns)
  * and variant: 0..2 = the register-pipelined kernel on a persistent grid with
  * at least 6, 8 or 10 resident blocks of 128 threads per SM; 3 = the staged
- * kernel (a producer warp copies rows into a 4-slot shared-memory ring with
- * cp.async.bulk, four consumer warps collide from it; one block per strip);
+ * kernel (a producer warp copies rows into a shared-memory ring with
+ * cp.async.bulk -- with FP16 storage whole input rows of all nine populations,
+ * one tensor copy each -- and four consumer warps collide from it; one block
+ * per strip);
  * 4 = the staged kernel on a resident-sized grid, each block streaming a
  * fixed share of the strips through its ring; 5 = the staged kernel on a
  * resident-sized grid whose blocks take strips from a global counter (dynamic

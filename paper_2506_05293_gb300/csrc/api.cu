@@ -1,6 +1,8 @@
 // C ABI of the library (include/lbm.h): argument checking, device memory,
 // streams, CUDA-graph replay of chunks of steps, and host post-processing.
 // Every numerical step of the method runs in the kernels of step.cu and train.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -51,6 +53,53 @@ void* dev_alloc(lbm_sim* s, size_t bytes) {
   void* p = lbm::dev_alloc_raw(s->have_alloc ? &s->alloc : nullptr, bytes);
   s->owned.push_back(p);
   return p;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the library
+// does not link the driver library itself)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// The tensor maps of the two population buffers (FP16 storage) for the staged
+// kernel's row-window copies: a 3-D view (x: pitch elements, y: ny rows, population: 9 planes)
+// with a box of 128 + 2 A columns, one row and nine populations, A = 16 bytes
+// in elements (the kernel's row window).  Stored in 256 bytes of device
+// memory, each map 64-byte aligned.
+void make_tensor_maps(lbm_sim* s) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) throw lbm::CudaError{cudaErrorNotSupported, "cuTensorMapEncodeTiled unavailable"};
+  unsigned char* d = static_cast<unsigned char*>(dev_alloc(s, 256 + 64));
+  d += (64 - (reinterpret_cast<uintptr_t>(d) & 63)) & 63;
+  const CUtensorMapDataType dt = s->prec == LBM_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                               : s->prec == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const cuuint64_t dims[3] = {(cuuint64_t)s->pitch, (cuuint64_t)s->ny, 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)s->pitch * s->elem, (cuuint64_t)s->plane * s->elem};
+  const cuuint32_t box[3] = {(cuuint32_t)(128 + 2 * (16 / s->elem)), 1, 9};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUtensorMap maps[2];
+  for (int b = 0; b < 2; ++b) {
+    const CUresult r = enc(&maps[b], dt, 3, s->buf[b], dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw lbm::CudaError{cudaErrorInvalidValue, "tensor map encoding"};
+  }
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  ck(cudaMemcpyAsync(d, maps, sizeof(maps), cudaMemcpyHostToDevice, s->stream),
+     "tensor map copy");
+  ck(cudaStreamSynchronize(s->stream), "tensor map copy");
+  s->tmap[0] = d;
+  s->tmap[1] = d + 128;
 }
 
 // Scratch for row chunks of per_node doubles per node: allocated at the first
@@ -490,6 +539,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_sim** out) {
   } else {
     s->buf[0] = dev_alloc(s, bytes);
     s->buf[1] = dev_alloc(s, bytes);
+    if (s->prec == LBM_FP16DEV) make_tensor_maps(s);   // row windows of the staged kernel
   }
   const int64_t cells = (int64_t)s->nx * s->ny;
   s->kind = (uint8_t*)dev_alloc(s, cells);

@@ -30,6 +30,8 @@ void fill_member(const lbm_sim* s, Member& m) {
   memset(&m, 0, sizeof(m));
   m.buf[0] = s->buf[0];
   m.buf[1] = s->buf[1];
+  m.tmap[0] = s->tmap[0];
+  m.tmap[1] = s->tmap[1];
   m.nx = s->nx;
   m.ny = s->ny;
   m.pitch = (int32_t)s->pitch;

@@ -61,63 +61,105 @@ __device__ __forceinline__ void heq_all(R drho, R ux, R uy, R heq[9]) {
   }
 }
 
+// ---- lane arithmetic --------------------------------------------------------
+// The collision is written once over a lane type V: one node (float, double)
+// or two nodes side by side (float2, the packed FP32x2 instructions of sm_100
+// and later, one instruction for both nodes).  Every operation rounds once and
+// none is contracted by the compiler, so a pair of nodes collided as a float2
+// gets the bits of the same two nodes collided one at a time, whichever
+// kernel takes them.
+template <typename V> struct Ar;
+template <> struct Ar<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  using T = float;                                  // component type
+  static __device__ __forceinline__ float lit(double v) { return (float)v; }   // exact constants
+  static __device__ __forceinline__ float splat(float v) { return v; }
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }   // correctly rounded
+  static __device__ __forceinline__ bool bad(float x) { return !(fabsf(x) < 1e30f); }
+};
+template <> struct Ar<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  using T = double;
+  static __device__ __forceinline__ double lit(double v) { return v; }
+  static __device__ __forceinline__ double splat(double v) { return v; }
+  static __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+  static __device__ __forceinline__ bool bad(double x) { return !(fabs(x) < 1e30); }
+};
+template <> struct Ar<float2> {
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  // a - b as b * (-1) + a: the product is exact, so this is RN(a - b)
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+  }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+  using T = float;
+  static __device__ __forceinline__ float2 lit(double v) { return make_float2((float)v, (float)v); }
+  static __device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+  static __device__ __forceinline__ float2 rcp(float2 x) {
+    return make_float2(__frcp_rn(x.x), __frcp_rn(x.y));
+  }
+  static __device__ __forceinline__ bool bad(float2 x) {
+    return !(fabsf(x.x) < 1e30f) || !(fabsf(x.y) < 1e30f);
+  }
+};
+
 // The same equilibrium evaluated pairwise: for a direction i and its opposite
 // ibar, c.u changes sign, so h^eq_i,ibar = s_i +- a_i with
 // s_i = w_i (drho - 3/2 rho u.u + 9/2 rho (c_i.u)^2) and a_i = 3 w_i rho c_i.u.
-template <typename R>
-__device__ __forceinline__ void heq_sym(R drho, R ux, R uy, R heq[9]) {
-  const R rho = R(1) + drho;
-  const R base = drho - R(1.5) * rho * (ux * ux + uy * uy);
-  const R r45 = R(4.5) * rho, r3 = R(3) * rho;
-  heq[0] = wgt<R>(0) * base;
-  {
-    const R s = wgt<R>(1) * (base + r45 * ux * ux), a = wgt<R>(1) * r3 * ux;
-    heq[1] = s + a;
-    heq[3] = s - a;
-  }
-  {
-    const R s = wgt<R>(2) * (base + r45 * uy * uy), a = wgt<R>(2) * r3 * uy;
-    heq[2] = s + a;
-    heq[4] = s - a;
-  }
-  const R up = ux + uy;   // c5 = (1, 1); c7 = -c5
-  const R um = uy - ux;   // c6 = (-1, 1); c8 = -c6
-  {
-    const R s = wgt<R>(5) * (base + r45 * up * up), a = wgt<R>(5) * r3 * up;
-    heq[5] = s + a;
-    heq[7] = s - a;
-  }
-  {
-    const R s = wgt<R>(6) * (base + r45 * um * um), a = wgt<R>(6) * r3 * um;
-    heq[6] = s + a;
-    heq[8] = s - a;
-  }
+template <typename V>
+__device__ __forceinline__ void heq_sym(V drho, V ux, V uy, V heq[9]) {
+  using A = Ar<V>;
+  const V rho = A::add(A::lit(1), drho);
+  const V usq = A::fma(ux, ux, A::mul(uy, uy));
+  const V base = A::fma(A::mul(A::lit(-1.5), rho), usq, drho);        // drho - 3/2 rho u.u
+  const V r45 = A::mul(A::lit(4.5), rho), r3 = A::mul(A::lit(3), rho);
+  heq[0] = A::mul(A::splat(wgt<typename A::T>(0)), base);
+  // direction pair (i, ibar) along the component cu = c_i.u
+  auto pair = [&](int i, int ib, V cu) {
+    const V w = A::splat(wgt<typename A::T>(i));
+    const V s = A::mul(w, A::fma(A::mul(r45, cu), cu, base));
+    const V a = A::mul(A::mul(w, r3), cu);
+    heq[i] = A::add(s, a);
+    heq[ib] = A::sub(s, a);
+  };
+  pair(1, 3, ux);
+  pair(2, 4, uy);
+  pair(5, 7, A::add(ux, uy));   // c5 = (1, 1); c7 = -c5
+  pair(6, 8, A::sub(uy, ux));   // c6 = (-1, 1); c8 = -c6
 }
 
-// correctly rounded reciprocal
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-
 // rho - 1 and momentum of shifted populations (sum w_i = 1, sum w_i c_i = 0)
-template <typename R>
-__device__ __forceinline__ void moments_shifted(const R h[9], R& drho, R& jx, R& jy) {
-  drho = ((h[0] + h[2]) + (h[4] + h[1])) + ((h[3] + h[5]) + (h[6] + h[7])) + h[8];
-  jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-  jy = (h[2] - h[4]) + (h[5] + h[6]) - (h[7] + h[8]);
+template <typename V>
+__device__ __forceinline__ void moments_shifted(const V h[9], V& drho, V& jx, V& jy) {
+  using A = Ar<V>;
+  drho = A::add(A::add(A::add(A::add(h[0], h[2]), A::add(h[4], h[1])),
+                       A::add(A::add(h[3], h[5]), A::add(h[6], h[7]))),
+                h[8]);
+  jx = A::add(A::add(A::sub(h[1], h[3]), A::sub(h[5], h[6])), A::sub(h[8], h[7]));
+  jy = A::sub(A::add(A::sub(h[2], h[4]), A::add(h[5], h[6])), A::add(h[7], h[8]));
 }
 
 // ---- collision operators -------------------------------------------------
 // BGK (Eq. 2): h* = h - omega (h - h^eq), omega = 1 / tau.
-template <typename R>
-__device__ __forceinline__ void collide_bgk(R h[9], R omega, R& drho_out, R& ux_out, R& uy_out) {
-  R drho, jx, jy;
+template <typename V>
+__device__ __forceinline__ void collide_bgk(V h[9], V omega, V& drho_out, V& ux_out, V& uy_out) {
+  using A = Ar<V>;
+  V drho, jx, jy;
   moments_shifted(h, drho, jx, jy);
-  const R inv_rho = recip(R(1) + drho);
-  const R ux = jx * inv_rho, uy = jy * inv_rho;
-  R heq[9];
+  const V inv_rho = A::rcp(A::add(A::lit(1), drho));
+  const V ux = A::mul(jx, inv_rho), uy = A::mul(jy, inv_rho);
+  V heq[9];
   heq_sym(drho, ux, uy, heq);
+  const V nomega = A::mul(A::lit(-1), omega);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) h[i] = h[i] - omega * (h[i] - heq[i]);
+  for (int i = 0; i < 9; ++i) h[i] = A::fma(nomega, A::sub(h[i], heq[i]), h[i]);
   drho_out = drho; ux_out = ux; uy_out = uy;
 }
 
@@ -128,43 +170,52 @@ __device__ __forceinline__ void collide_bgk(R h[9], R omega, R& drho_out, R& ux_
 template <typename R>
 struct MrtRates { R se, seps, sqx, sqy, snxx, snxy; };
 
-template <typename R>
-__device__ __forceinline__ void collide_mrt(R h[9], const MrtRates<R>& s, R& drho_out, R& ux_out,
-                                            R& uy_out) {
-  R drho, jx, jy;
+template <typename V, typename R>
+__device__ __forceinline__ void collide_mrt(V h[9], const MrtRates<R>& s, V& drho_out, V& ux_out,
+                                            V& uy_out) {
+  using A = Ar<V>;
+  V drho, jx, jy;
   moments_shifted(h, drho, jx, jy);
-  const R inv_rho = recip(R(1) + drho);
-  const R ux = jx * inv_rho, uy = jy * inv_rho;
-  R n[9];
+  const V inv_rho = A::rcp(A::add(A::lit(1), drho));
+  const V ux = A::mul(jx, inv_rho), uy = A::mul(jy, inv_rho);
+  V n[9];
   heq_sym(drho, ux, uy, n);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) n[i] = h[i] - n[i];
+  for (int i = 0; i < 9; ++i) n[i] = A::sub(h[i], n[i]);
   // moments of n (rows of M written out; integer coefficients)
-  const R axis = (n[1] + n[2]) + (n[3] + n[4]);
-  const R diag = (n[5] + n[6]) + (n[7] + n[8]);
-  const R m_e = R(-4) * n[0] - axis + R(2) * diag;
-  const R m_eps = R(4) * n[0] - R(2) * axis + diag;
-  const R m_qx = R(-2) * (n[1] - n[3]) + (n[5] - n[6] - n[7] + n[8]);
-  const R m_qy = R(-2) * (n[2] - n[4]) + (n[5] + n[6] - n[7] - n[8]);
-  const R m_pxx = (n[1] + n[3]) - (n[2] + n[4]);
-  const R m_pxy = (n[5] - n[6]) + (n[7] - n[8]);
+  const V axis = A::add(A::add(n[1], n[2]), A::add(n[3], n[4]));
+  const V diag = A::add(A::add(n[5], n[6]), A::add(n[7], n[8]));
+  const V two = A::lit(2);
+  const V m_e = A::fma(two, diag, A::sub(A::mul(A::lit(-4), n[0]), axis));
+  const V m_eps = A::add(A::fma(A::lit(-2), axis, A::mul(A::lit(4), n[0])), diag);
+  const V m_qx = A::fma(A::lit(-2), A::sub(n[1], n[3]),
+                        A::add(A::sub(n[5], n[6]), A::sub(n[8], n[7])));
+  const V m_qy = A::fma(A::lit(-2), A::sub(n[2], n[4]),
+                        A::sub(A::add(n[5], n[6]), A::add(n[7], n[8])));
+  const V m_pxx = A::sub(A::add(n[1], n[3]), A::add(n[2], n[4]));
+  const V m_pxy = A::add(A::sub(n[5], n[6]), A::sub(n[7], n[8]));
   // relaxed amounts divided by the row norms
-  const R de = s.se * m_e * (R(1) / R(36));
-  const R deps = s.seps * m_eps * (R(1) / R(36));
-  const R dqx = s.sqx * m_qx * (R(1) / R(12));
-  const R dqy = s.sqy * m_qy * (R(1) / R(12));
-  const R dpxx = s.snxx * m_pxx * R(0.25);
-  const R dpxy = s.snxy * m_pxy * R(0.25);
+  using T = typename A::T;
+  const V de = A::mul(A::splat((T)s.se * T(1.0 / 36.0)), m_e);
+  const V deps = A::mul(A::splat((T)s.seps * T(1.0 / 36.0)), m_eps);
+  const V dqx = A::mul(A::splat((T)s.sqx * T(1.0 / 12.0)), m_qx);
+  const V dqy = A::mul(A::splat((T)s.sqy * T(1.0 / 12.0)), m_qy);
+  const V dpxx = A::mul(A::splat((T)s.snxx * T(0.25)), m_pxx);
+  const V dpxy = A::mul(A::splat((T)s.snxy * T(0.25)), m_pxy);
   // h* = h - M^T d (columns of M)
-  h[0] -= R(-4) * de + R(4) * deps;
-  h[1] -= -de - R(2) * deps - R(2) * dqx + dpxx;
-  h[2] -= -de - R(2) * deps - R(2) * dqy - dpxx;
-  h[3] -= -de - R(2) * deps + R(2) * dqx + dpxx;
-  h[4] -= -de - R(2) * deps + R(2) * dqy - dpxx;
-  h[5] -= R(2) * de + deps + dqx + dqy + dpxy;
-  h[6] -= R(2) * de + deps - dqx + dqy - dpxy;
-  h[7] -= R(2) * de + deps - dqx - dqy + dpxy;
-  h[8] -= R(2) * de + deps + dqx - dqy - dpxy;
+  const V e2 = A::fma(two, deps, de);            // de + 2 deps
+  const V e5 = A::fma(two, de, deps);            // 2 de + deps
+  h[0] = A::sub(h[0], A::mul(A::lit(4), A::sub(deps, de)));
+  // axis directions: -(de + 2 deps) -+ 2 dq +- dpxx
+  h[1] = A::sub(h[1], A::add(A::fma(A::lit(-2), dqx, dpxx), A::mul(A::lit(-1), e2)));
+  h[3] = A::sub(h[3], A::add(A::fma(two, dqx, dpxx), A::mul(A::lit(-1), e2)));
+  h[2] = A::sub(h[2], A::sub(A::fma(A::lit(-2), dqy, A::mul(A::lit(-1), e2)), dpxx));
+  h[4] = A::sub(h[4], A::sub(A::fma(two, dqy, A::mul(A::lit(-1), e2)), dpxx));
+  // diagonals: 2 de + deps +- dqx +- dqy +- dpxy
+  h[5] = A::sub(h[5], A::add(A::add(e5, A::add(dqx, dqy)), dpxy));
+  h[6] = A::sub(h[6], A::sub(A::add(e5, A::sub(dqy, dqx)), dpxy));
+  h[7] = A::sub(h[7], A::add(A::sub(e5, A::add(dqx, dqy)), dpxy));
+  h[8] = A::sub(h[8], A::sub(A::add(e5, A::sub(dqx, dqy)), dpxy));
   drho_out = drho; ux_out = ux; uy_out = uy;
 }
 

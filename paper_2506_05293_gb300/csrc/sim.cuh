@@ -23,6 +23,8 @@ enum : int { DEV_NONFINITE = 1, DEV_TIMEOUT = 2 };
 // Built on the host and kept in device memory; the kernels read it per block.
 struct Member {
   void* buf[2];           // population buffers (storage type S); source = buf[q]
+  const void* tmap[2];    // FP16 storage: tensor maps of buf[0] and buf[1] (x, y, population;
+                          // 64-byte aligned, in device memory) for the row-window copies
   int32_t nx, ny, pitch, plane;   // elements; 9 * plane < 2^31
   const uint32_t* solid_bits;
   int32_t words_per_row;
@@ -320,6 +322,8 @@ struct lbm_sim {
   size_t elem = 0;
   int prec = LBM_FP32;
   void* buf[2] = {nullptr, nullptr};
+  const void* tmap[2] = {nullptr, nullptr};   // device tensor maps of buf[0], buf[1] (two-buffer
+                                              // layout, FP16 storage)
   int cur = 0;
   uint8_t* kind = nullptr;
   uint32_t* solid_bits = nullptr;

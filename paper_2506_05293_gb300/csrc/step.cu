@@ -63,10 +63,14 @@ void launch_dataflow_reset(int64_t* strip_done, int n_strips, int64_t t, int64_t
 }
 
 size_t step_bulk_smem(int prec, int stages) {
-  const int sb = prec == LBM_FP64 ? BulkLayout<double>::STAGE_BYTES
-               : prec == LBM_FP32 ? BulkLayout<float>::STAGE_BYTES
-                                  : BulkLayout<__half>::STAGE_BYTES;
-  return (size_t)stages * sb + (size_t)stages * 16 + 16;   // ring + full/empty barriers
+  // the ring (per-row stages; with FP16 storage the larger of those and the
+  // row windows of variants 3, 4, 6), the full/empty barriers and the
+  // alignment of the ring to 128 bytes
+  int sb = prec == LBM_FP64 ? BulkLayout<double>::STAGE_BYTES
+         : prec == LBM_FP32 ? BulkLayout<float>::STAGE_BYTES
+                            : BulkLayout<__half>::STAGE_BYTES;
+  if (prec == LBM_FP16DEV && WinLayout<__half>::SLOT_BYTES > sb) sb = WinLayout<__half>::SLOT_BYTES;
+  return (size_t)stages * sb + (size_t)stages * 16 + 16 + 128;
 }
 
 // ---- variants and launch ------------------------------------------------------
@@ -96,8 +100,8 @@ int step_variants() { return kVariants; }
 
 template <typename S, int COLL, int MINB, bool DYN>
 static cudaError_t occ_bulk(int* per_sm) {
-  const size_t smem = step_bulk_smem(prec_of<S>(), kBulkSlots);
-  auto k = step_bulk_kernel<S, COLL, kBulkSlots, MINB, false, DYN>;
+  const size_t smem = step_bulk_smem(prec_of<S>(), bulk_slots<S>());
+  auto k = step_bulk_kernel<S, COLL, bulk_slots<S>(), MINB, false, DYN>;
   const cudaError_t e =
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -15,9 +15,9 @@ void set_bulk_smem_attr() {
   if (done) return;
   // a cap: each launch passes what its members need (ext_need)
   const int cap = kExtSmemCap;
-  cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true, false>,
+  cudaFuncSetAttribute(step_bulk_kernel<S, COLL, bulk_slots<S>(), 6, true, false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(step_bulk_kernel<S, COLL, kBulkSlots, 6, true, true>,
+  cudaFuncSetAttribute(step_bulk_kernel<S, COLL, bulk_slots<S>(), 6, true, true>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(step_kernel<S, COLL, 6, true>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, cap);

@@ -1395,6 +1395,286 @@ __device__ inline bool wait_east(const StepParams& p, const Member& m, int a, in
   return false;
 }
 
+// ---- row-window staging (variants 3, 4, 6) -----------------------------------
+// A slot of the ring holds one input row of all nine populations: columns
+// x0 - A .. x0 + 127 + A of the strip's tile (A = 16 bytes in elements, so the
+// copy starts on a 16-byte boundary; columns outside the lattice read zeros
+// and are never used), fetched by one 3-D tensor copy (x, y, population) of a
+// W x 1 x 9 box, plus the row's 16 bytes of solid-mask words.  Output row y
+// pulls population i from input row y - c_iy at column x - c_ix, so it reads
+// three consecutive slots; each input row is copied once per strip.
+template <typename S>
+struct WinLayout {
+  static constexpr int A = 16 / (int)sizeof(S);
+  static constexpr int W = 128 + 2 * A;                    // staged columns
+  static constexpr int ROW_BYTES = 9 * W * (int)sizeof(S);
+  static constexpr int SLOT_BYTES = (ROW_BYTES + 16 + 127) / 128 * 128;
+  static constexpr uint32_t TX_BYTES = (uint32_t)ROW_BYTES + 16u;
+};
+
+// One W x 1 x 9 box of a population buffer (its tensor map: x, y,
+// population) into shared memory, completing on bar.  x * sizeof(S) must be a
+// multiple of 16 (x may be negative: those columns read zeros).
+__device__ __forceinline__ void tma_row_g2s(void* dst, const void* tmap, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(0), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// One node after its nine pulled values are loaded: the periodic wrap of the
+// x +- 1 neighbours at the lattice edges, then bounce-back with momentum
+// exchange, or the boundary condition and the collision.
+template <typename S, int COLL>
+__device__ __forceinline__ void finish_node(const Member& m, const Scalars<typename Compute<S>::R>& sc,
+                                            const S* A, S* B, int x, int y, bool solid,
+                                            int64_t t, typename Compute<S>::R h[9], double& fx,
+                                            double& fy, bool& touched, bool& bad) {
+  using R = typename Compute<S>::R;
+  const int nx = m.nx, ny = m.ny, plane = m.plane, pitch = m.pitch;
+  if (x == 0 || x == nx - 1) {
+    const int ym = y == 0 ? ny - 1 : y - 1;
+    const int yp = y == ny - 1 ? 0 : y + 1;
+    // (A is not __restrict__: these plain loads must not take the
+    // non-coherent path, the previous launch may still be writing A)
+    if (x == 0) {
+      h[1] = to_r<R>(A[1 * plane + y * pitch + nx - 1]);
+      h[5] = to_r<R>(A[5 * plane + ym * pitch + nx - 1]);
+      h[8] = to_r<R>(A[8 * plane + yp * pitch + nx - 1]);
+    }
+    if (x == nx - 1) {
+      h[3] = to_r<R>(A[3 * plane + y * pitch]);
+      h[6] = to_r<R>(A[6 * plane + ym * pitch]);
+      h[7] = to_r<R>(A[7 * plane + yp * pitch]);
+    }
+  }
+  const bool west = !m.x_periodic && x == 0;
+  const bool east = !m.x_periodic && x == nx - 1;
+  const int o = y * pitch + x;
+  // the network blocks rebuild external east fluid nodes; solid ones stay here
+  if (solid)
+    solid_node<S, R>(A, B, m, x, y, o, h, fx, fy, touched);
+  else if (!(east && m.east_mode == EAST_EXTERNAL))
+    fluid_node<S, R, COLL>(B, m, sc, t, west, east, y, o, h, bad);
+}
+
+// One block streams the rows of its strips (local strips lb, lb + gk, ... of
+// member m) through an NS-slot ring of input rows with warp specialisation:
+// warp 4 is the producer -- its lane 0 waits until a slot is released
+// ("empty" barrier, one arrival per consumer warp), then fetches the next
+// input row (rows y0 - 1 .. y0 + nrows of each strip, wrapped) with one tensor
+// copy and one bulk copy completing on the slot's "full" barrier -- and warps
+// 0-3 are consumers: for output row y each waits for input row y + 1, collides
+// its 32 columns from input rows y - 1, y, y + 1 and releases row y - 1.  No
+// block-wide barrier per row: warps run ahead independently.
+template <typename S, int COLL, int NS>
+__device__ __forceinline__ void bulk_run_window(const StepParams& p, const Member& m, int lb,
+                                                int gk, unsigned char* smem_base) {
+  static_assert(NS >= 3, "an output row needs three input rows in the ring");
+  using R = typename Compute<S>::R;
+  using Lay = WinLayout<S>;
+  // the ring is 128-byte aligned (tensor copies); barriers after the slots
+  unsigned char* smem = smem_base + ((128u - (smem_u32(smem_base) & 127u)) & 127u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * Lay::SLOT_BYTES);
+  uint64_t* empty = full + NS;
+  __shared__ int s_abort;
+  const S* A = static_cast<const S*>(m.buf[p.q]);
+  S* __restrict__ B = static_cast<S*>(m.buf[1 - p.q]);
+  const void* tmap = m.tmap[p.q];
+  const int nx = m.nx, ny = m.ny, tiles_x = m.tiles_x, rows = p.rows;
+  const int strips = m.strip_count;
+  const int warp = threadIdx.x >> 5;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const int64_t t = step_index(p);
+  const bool flow = p.strip_done != nullptr;   // one strip per block (variant 6)
+  if (p.strip_done && threadIdx.x == kConsumerWarps * 32) {
+    // the producer lane: wait for the strips around this one (and, in an east
+    // tile, the boundary blocks next to it) to complete step t-1; the fence
+    // orders those acquires before its copies (async proxy)
+    bool ok = wait_strip_neighbours(p, m, lb, t);
+    const int c = lb % m.tiles_x, L = m.nx - 1;
+    if (ok && m.ext_kind != 0 && (c << 7) + 127 >= L - 4) {
+      const int y0 = (lb / m.tiles_x) * p.rows;
+      ok = wait_east(p, m, y0 - 2, min(y0 + p.rows, m.ny) + 1, t, false, true);
+    }
+    if (!ok) atomicOr(m.status, DEV_TIMEOUT);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+  __syncthreads();
+  // set-up done: wait for the previous step to complete before touching the
+  // populations (it may still be reading the buffer this step writes)
+  if (!flow) pdl_wait();
+
+  // strip geometry
+  struct Strip {
+    int y0, x0, nrows;
+  };
+  auto strip_at = [&](int ls) {
+    Strip st;
+    st.y0 = (ls / tiles_x) * rows;
+    st.x0 = (ls % tiles_x) << 7;
+    st.nrows = min(rows, ny - st.y0);
+    return st;
+  };
+
+  double fx = 0.0, fy = 0.0;
+  bool touched = false, bad = false;
+
+  if (warp == kConsumerWarps) {
+    // ---------------- producer ----------------
+    if ((threadIdx.x & 31) == 0) {
+      // input row k goes to slot k mod NS; its "empty" wait is for the
+      // slot's previous use (phase of round k / NS - 1)
+      int ps = lb, pr = -1, k = 0, slot = 0;
+      uint32_t round = 0;
+      Strip pst = strip_at(lb);
+      while (ps < strips) {
+        if (k >= NS && !mbar_wait_bounded(&empty[slot], (round - 1) & 1u)) {
+          atomicOr(m.status, DEV_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        if (s_abort) break;
+        int y = pst.y0 + pr;                    // input rows y0 - 1 .. y0 + nrows, wrapped
+        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+        unsigned char* st = smem + slot * Lay::SLOT_BYTES;
+        if (pr >= 0 && pr < pst.nrows) {
+          // a row of the strip: all nine populations and its solid-mask words
+          mbar_expect_tx(&full[slot], Lay::TX_BYTES);
+          tma_row_g2s(st, tmap, pst.x0 - Lay::A, y, &full[slot]);
+          bulk_copy_g2s(st + Lay::ROW_BYTES,
+                        m.solid_bits + y * m.words_per_row + (pst.x0 >> 5), 16u, &full[slot]);
+        } else {
+          // a halo row: only the three populations pulled across the strip's
+          // edge (c_iy = 1 from the row above it, c_iy = -1 from the row
+          // below); at x0 = 0 the copy starts at the lattice's first column
+          const int lead = pst.x0 == 0 ? 0 : Lay::A;
+          const uint32_t bytes = (uint32_t)((Lay::W - Lay::A + lead) * (int)sizeof(S));
+          mbar_expect_tx(&full[slot], 3u * bytes);
+          const int i0 = pr < 0 ? 2 : 4;       // 2, 5, 6 or 4, 7, 8
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const int i = j == 0 ? i0 : i0 + 3 + (j - 1);
+            bulk_copy_g2s(st + (i * Lay::W + Lay::A - lead) * (int)sizeof(S),
+                          A + i * m.plane + y * m.pitch + pst.x0 - lead, bytes, &full[slot]);
+          }
+        }
+        ++k;
+        if (++slot == NS) {
+          slot = 0;
+          ++round;
+        }
+        if (++pr == pst.nrows + 1) {
+          pr = -1;
+          ps += gk;
+          if (ps < strips) pst = strip_at(ps);
+        }
+      }
+      // no copy may land after the block exits: wait (bounded) for the last
+      // item staged into each slot
+      for (int kk = k > NS ? k - NS : 0; kk < k; ++kk)
+        mbar_wait_bounded(&full[kk % NS], (uint32_t)((kk / NS) & 1));
+    }
+  } else {
+    // ---------------- consumers ----------------
+    const Scalars<R> sc(m);
+    const int lx = threadIdx.x;     // column within the 128-wide tile
+    const int lane = threadIdx.x & 31;
+    // ring position of input row k as (slot, phase), advanced one row at a time
+    struct Pos {
+      int slot;
+      uint32_t phase;
+    };
+    auto next = [](Pos q) {
+      return ++q.slot == NS ? Pos{0, q.phase ^ 1u} : q;
+    };
+    auto wait_full = [&](Pos q) {
+      // warp-uniform outcome, so the warp never diverges around __syncwarp
+      return __all_sync(0xffffffffu, !s_abort && mbar_wait_bounded(&full[q.slot], q.phase));
+    };
+    auto release = [&](Pos q) {
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[q.slot]))
+                     : "memory");
+    };
+    auto row_at = [&](Pos q) {
+      return reinterpret_cast<const S*>(smem + q.slot * Lay::SLOT_BYTES);
+    };
+    bool ok = true;
+    Pos pm{0, 0u};                  // input row y - 1 of the next output row
+    for (int cs = lb; ok && cs < strips; cs += gk) {
+      const Strip cst = strip_at(cs);
+      const int x = cst.x0 + lx;
+      const bool skip = x >= nx;
+      Pos p0 = next(pm), pp = next(p0);
+      ok = wait_full(pm) && wait_full(p0);
+      for (int cr = 0; ok && cr < cst.nrows; ++cr) {
+        if (!wait_full(pp)) {
+          ok = false;
+          break;
+        }
+        if (!skip) {
+          const S* rows3[3] = {row_at(pm), row_at(p0), row_at(pp)};
+          R h[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i)
+            h[i] = to_r<R>(rows3[1 - cy(i)][i * Lay::W + lx + Lay::A - cx(i)]);
+          const uint32_t word = reinterpret_cast<const uint32_t*>(
+              reinterpret_cast<const unsigned char*>(rows3[1]) + Lay::ROW_BYTES)[lx >> 5];
+          finish_node<S, COLL>(m, sc, A, B, x, cst.y0 + cr, ((word >> (lx & 31)) & 1u) != 0, t,
+                               h, fx, fy, touched, bad);
+        }
+        release(pm);                // row y - 1 is not read again
+        pm = p0;
+        p0 = pp;
+        pp = next(pp);
+      }
+      if (ok) {
+        release(pm);
+        release(p0);
+        pm = pp;                    // the next strip's first input row
+      }
+    }
+    if (!ok) {
+      atomicOr(m.status, DEV_TIMEOUT);
+      s_abort = 1;
+    }
+  }
+  // the block's force partial: its strip's slot when partials go per strip
+  // (recomputed here rather than kept live through the loop)
+  const int bb = block_role(p).idx;
+  const int sgb = p.strip_order ? p.strip_order[bb] : bb;
+  const int slot = p.strip_force ? p.strip_force[sgb] : sgb;
+  // dataflow (one strip per block: sgb is the strip's index in the table):
+  // the partial slot of step t last held step t-2's partials; they must be
+  // reduced (by a block of launch t-1) before they are overwritten
+  if (p.strip_done && slot >= 0 && threadIdx.x == 0 &&
+      !wait_at_least(p.reduced + (p.n_members == 1 ? 0 : p.strip_member[sgb]), t - 1, m.status))
+    atomicOr(m.status, DEV_TIMEOUT);
+  write_partial(p, t, slot, fx, fy, touched, bad, m.status);
+  if (p.strip_done) {
+    // every thread's stores of this strip (ordered with the copies of the
+    // next step that read them), then its completion of step t
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(p.strip_done + sgb, t + 1);
+    }
+  }
+}
+
 // One block streams the rows of its strips (local strips lb, lb + gk, ... of
 // member m) through an NS-slot ring with warp specialisation: warp 4 is the
 // producer -- its lane 0 waits until a slot is released ("empty" barrier,
@@ -1403,8 +1683,8 @@ __device__ inline bool wait_east(const StepParams& p, const Member& m, int a, in
 // consumers, each waiting on "full", colliding its 32 columns and releasing
 // the slot.  No block-wide barrier per row: warps run ahead independently.
 template <typename S, int COLL, int NS>
-__device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, int lb, int gk,
-                                         unsigned char* smem) {
+__device__ __forceinline__ void bulk_run_rows(const StepParams& p, const Member& m, int lb,
+                                              int gk, unsigned char* smem) {
   using R = typename Compute<S>::R;
   using Lay = BulkLayout<S>;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * Lay::STAGE_BYTES);
@@ -1595,6 +1875,19 @@ __device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, i
       st_release(p.strip_done + sgb, t + 1);
     }
   }
+}
+
+// Variants 3, 4 and 6: FP16 storage streams row windows (one tensor copy per
+// input row); FP32 and FP64 storage stage each output row's nine source
+// segments (their consumers are bound by DRAM and the FP64 pipe, where the
+// windows' wider rows cost more than their fewer copies save).
+template <typename S, int COLL, int NS>
+__device__ __forceinline__ void bulk_run(const StepParams& p, const Member& m, int lb, int gk,
+                                         unsigned char* smem) {
+  if constexpr (sizeof(S) == 2)
+    bulk_run_window<S, COLL, NS>(p, m, lb, gk, smem);
+  else
+    bulk_run_rows<S, COLL, NS>(p, m, lb, gk, smem);
 }
 
 // Persistent staged kernel with dynamic strip assignment (variant 5): a
@@ -1878,14 +2171,21 @@ __global__ void __launch_bounds__(kBulkThreads, MINB) step_bulk_kernel(const Ste
 
 // Variants 0-2: the register-pipelined kernel with __launch_bounds__ minimum
 // resident blocks of 128 threads per SM of 6, 8, 10.  Variant 3: the
-// warp-specialised staged kernel (4-slot ring), one block per strip.
+// warp-specialised staged kernel (a ring of 4, 6 or 8 row slots for FP64, FP32
+// or FP16 storage), one block per strip.
 // Variant 4: the same on a resident-sized grid, each block streaming a fixed
 // share of the strips through its ring.  Variant 5: the resident-sized grid
 // taking strips from a global counter (dynamic balance).  Variant 6: variant 3
 // ordered by per-strip completion flags instead of whole launches (dataflow
 // between consecutive steps).
 constexpr int kVariants = 7;
-constexpr int kBulkSlots = 4;
+// ring slots of the staged kernel: with FP16 storage the consumers of
+// variants 3, 4 and 6 hold three input rows (y - 1, y, y + 1) of an 8-slot
+// ring; otherwise one staged output row of a 4-slot ring
+template <typename S>
+constexpr int bulk_slots() {
+  return sizeof(S) == 2 ? 8 : 4;
+}
 
 template <typename S>
 constexpr int prec_of() {
@@ -1940,9 +2240,9 @@ void launch_bulk(const StepParams& p, int blocks, cudaStream_t s) {
   // every group runs at creation (occ_bulk), or for the network kernels at
   // their first launch
   using R = typename Compute<S>::R;
-  size_t smem = step_bulk_smem(prec_of<S>(), kBulkSlots);
+  size_t smem = step_bulk_smem(prec_of<S>(), bulk_slots<S>());
   if (EXT) smem = ext_bulk_smem<R>(p, smem);
-  launch_pdl(step_bulk_kernel<S, COLL, kBulkSlots, MINB, EXT, DYN>, p.nn_blocks + blocks + p.n_members,
+  launch_pdl(step_bulk_kernel<S, COLL, bulk_slots<S>(), MINB, EXT, DYN>, p.nn_blocks + blocks + p.n_members,
              kBulkThreads, smem, s, p);
 }
 

@@ -181,6 +181,53 @@ def test_c1_mrt_re100_fp16dev(L, c1_mrt_re100_oracle):
     assert e["cd"] < 1e-3 and e["cl_rms"] < 5e-2
 
 
+# an off-centre cylinder at Re 20: no shedding, so FP16 rounding cannot shift a
+# shedding phase, and the wall asymmetry gives the lift a non-zero mean
+C2_KIND = add_walls(cylinder_mask(200, 80, 40, 33.5, 10))
+C2 = dict(u_in=0.05, v_pert_amp=0.0, seed=1)
+
+
+@pytest.fixture(scope="module")
+def c2_bgk_re20_oracle():
+    return _oracle_run(C2_KIND, 2000, tau=lbm.tau_from_re(0.05, 10, 20), **C2)
+
+
+def test_c2_offcentre_re20_fp16dev_pointwise(L, c2_bgk_re20_oracle):
+    """FP16-deviation storage on a non-shedding flow, pinned step by step: the
+    drag and lift coefficients of every one of the 2000 steps (impulsive start;
+    the forces carry the channel's acoustic standing wave on top of the steady
+    wake) against the FP64 oracle's, as a fraction of the oracle's RMS; the
+    mean lift of the second half, as a fraction of the lift's RMS; the final
+    fields node by node.  Measured on GB300 (two roundings of the FP32
+    collision): C_D 4.1e-3 - 5.1e-3 and C_L 3.5e-2 - 4.0e-2 of their RMS at the
+    worst step, mean C_L within 1e-5 - 9e-4 of the RMS, rho 1.5e-4 - 2.2e-4
+    relative, u 1.0e-3 - 1.1e-3 relative L2 and 4.6e-2 U at the worst node.
+    The per-step lift error is the FP16 rounding (2^-12 relative) of the
+    deviations that enter the momentum exchange in that step, about 40 links
+    of |h| up to 0.1: a few 1e-4 in lattice force units against a lift
+    amplitude of 7e-3; it averages out of the mean.  The bounds are about
+    twice the largest measured errors."""
+    o = c2_bgk_re20_oracle
+    g = _gpu_run(L, C2_KIND, 2000, "fp16dev", tau=lbm.tau_from_re(0.05, 10, 20), **C2)
+    cd_g, cl_g = post.coefficients(g["F"], 1.0, 0.05, 10)
+    cd_o, cl_o = post.coefficients(o["F"], 1.0, 0.05, 10)
+    assert len(cd_g) == len(cd_o) == 2000
+    assert abs(cl_o[1000:].mean()) > 0.05            # a lift with a non-zero mean
+    rms = lambda v: float(np.sqrt((v[1:] ** 2).mean()))
+    fl = C2_KIND == 0
+    drho = (np.abs(g["rho"] - o["rho"])[fl] / o["rho"][fl]).max()
+    du = np.hypot(g["ux"] - o["ux"], g["uy"] - o["uy"])[fl]
+    un = np.hypot(o["ux"], o["uy"])[fl]
+    e = dict(cd=float(np.abs(cd_g - cd_o).max() / rms(cd_o)),
+             cl=float(np.abs(cl_g - cl_o).max() / rms(cl_o)),
+             cl_mean=float(abs(cl_g[1000:].mean() - cl_o[1000:].mean()) / rms(cl_o)),
+             rho=float(drho), u_l2=float(np.linalg.norm(du) / np.linalg.norm(un)),
+             u_max=float(du.max() / 0.05))
+    print("fp16dev pointwise errors", e)
+    assert e["cd"] < 1e-2 and e["cl"] < 8e-2 and e["cl_mean"] < 2e-3
+    assert e["rho"] < 5e-4 and e["u_l2"] < 2.5e-3 and e["u_max"] < 9e-2
+
+
 # --------------------------------------------------------------------------- #
 # ragged sizes spanning several tiles, periodic boxes, edge cases
 # --------------------------------------------------------------------------- #
