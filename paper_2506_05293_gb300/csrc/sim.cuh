@@ -224,7 +224,7 @@ struct TrainParams {
   int32_t mode;                    // 0 Adam steps, 1 gradients, 2 losses only
   float* grad_out;                 // device [n_steps][n_params] (mode 1)
   double* loss_log;                // device [n_steps]
-  int32_t chunk;                   // samples per shared-memory chunk (multiple of 4)
+  int32_t chunk;                   // samples per shared-memory chunk (multiple of 16)
 };
 int train_smem_bytes(const int* sizes, int n_layers, int chunk);
 int train_max_chunk(const int* sizes, int n_layers, int batch_per_cta, int smem_limit);

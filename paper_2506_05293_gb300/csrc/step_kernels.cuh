@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "lattice.cuh"
+#include "mma_tf32.cuh"
 #include "sim.cuh"
 
 namespace lbm {
@@ -481,25 +482,6 @@ __host__ __device__ constexpr size_t nn_tc_fixed_bytes() {
 }
 __host__ __device__ constexpr size_t nn_tc_smem_bytes(int blob_elems) {
   return (size_t)blob_elems * 4 + nn_tc_fixed_bytes();
-}
-
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-// x = hi + lo (approximately), both TF32
-__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(x - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32_1688(float c[4], const uint32_t a[4], uint32_t b0,
-                                              uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
-      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // out[16][n_out] = act(in[16][n_in] W^T + b) for the block's 16 nodes; in is

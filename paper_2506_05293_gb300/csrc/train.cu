@@ -5,6 +5,9 @@
 //
 // Training runs as ONE thread-block cluster.  Every CTA keeps a full copy of
 // the network in shared memory and takes a contiguous slice of each batch;
+// the forward products, the backward deltas and the weight gradients of a
+// slice run on the tensor cores (mma.sync on TF32 operands split into high
+// and low parts, 3xTF32, FP32 accumulation: FP32-level products);
 // the per-CTA gradients are summed in a fixed CTA order through distributed
 // shared memory by the CTA that owns each parameter, which applies Adam and
 // writes the new value into every CTA's copy.  Two cluster barriers per Adam
@@ -20,6 +23,7 @@
 
 #include "../../include/lbm.h"
 #include "lattice.cuh"
+#include "mma_tf32.cuh"
 #include "sim.cuh"
 
 namespace cg = cooperative_groups;
@@ -153,18 +157,24 @@ int dataset_stats_scratch_doubles() { return kStatBlocks * kStatCols + 2 * 82; }
 // ---- training ---------------------------------------------------------------
 
 // Shared-memory layout of the training kernel, identical on host and device.
-// Weight rows and activation rows use odd strides, so a warp reading one
-// column across rows hits 32 different banks.
+// The layer products run on the tensor cores (3xTF32 mma.sync), so every
+// operand is zero-padded: a layer's inputs to a multiple of 8 columns (kp),
+// its outputs to a multiple of 8 (np8), samples of a chunk to a multiple of
+// 16.  Row strides are 4 more than a multiple of 8, which spreads the rows of
+// a fragment load over distinct banks.
 struct TrainLayout {
   int nl = 0;
   int sizes[LBM_MLP_MAX_LAYERS + 1] = {0};
-  int ws[LBM_MLP_MAX_LAYERS] = {0};      // weight row stride (odd)
-  int w_off[LBM_MLP_MAX_LAYERS] = {0};   // padded W; bias follows W
+  int kp[LBM_MLP_MAX_LAYERS] = {0};      // inputs of layer l padded to a multiple of 8
+  int np8[LBM_MLP_MAX_LAYERS] = {0};     // outputs of layer l padded to a multiple of 8
+  int ws[LBM_MLP_MAX_LAYERS] = {0};      // weight row stride (kp + 4)
+  int w_off[LBM_MLP_MAX_LAYERS] = {0};   // W [np8][ws]; bias [no] follows
   int g_off[LBM_MLP_MAX_LAYERS] = {0};   // flat (natural) parameter offsets
-  int hs[LBM_MLP_MAX_LAYERS] = {0};      // activation row stride of layer inputs
+  int hs[LBM_MLP_MAX_LAYERS] = {0};      // activation row stride of layer inputs (kp + 4)
   int h_off[LBM_MLP_MAX_LAYERS] = {0};
+  int os = 0;                            // output row stride (np8 of the last layer + 4)
   int ds = 0;                            // delta row stride
-  int chunk = 0;
+  int chunk = 0;                         // samples per chunk (a multiple of 16)
   int n_params = 0;
   int w_total = 0, g0 = 0, out0 = 0, base0 = 0, ref0 = 0, d0 = 0, d1 = 0, mean0 = 0, std0 = 0;
   int loss0 = 0;                         // double slots (in floats from the start)
@@ -173,32 +183,37 @@ struct TrainLayout {
   __host__ __device__ TrainLayout(const int* sz, int n_layers, int chunk_) {
     nl = n_layers;
     chunk = chunk_;
-    int off = 0, goff = 0, maxw = 3;
+    int off = 0, goff = 0, maxd = 8;
     for (int l = 0; l <= nl; ++l) sizes[l] = sz[l];
     for (int l = 0; l < nl; ++l) {
-      ws[l] = sizes[l] | 1;
+      kp[l] = (sizes[l] + 7) / 8 * 8;
+      np8[l] = (sizes[l + 1] + 7) / 8 * 8;
+      ws[l] = kp[l] + 4;
       w_off[l] = off;
-      off += sizes[l + 1] * ws[l] + sizes[l + 1];
+      off += np8[l] * ws[l] + sizes[l + 1];
       g_off[l] = goff;
       goff += sizes[l + 1] * sizes[l] + sizes[l + 1];
-      if (sizes[l + 1] > maxw) maxw = sizes[l + 1];
+      const int m16 = (sizes[l + 1] + 15) / 16 * 16;   // rows of a weight-gradient product
+      if (m16 > maxd) maxd = m16;
+      if (kp[l] > maxd) maxd = kp[l];
     }
     n_params = goff;
     w_total = off;
     g0 = off;
     off += goff;
     for (int l = 0; l < nl; ++l) {
-      hs[l] = sizes[l] | 1;
+      hs[l] = kp[l] + 4;
       h_off[l] = off;
       off += chunk * hs[l];
     }
+    os = np8[nl - 1] + 4;
     out0 = off;
-    off += chunk * 3;
+    off += chunk * os;
     base0 = off;
     off += chunk * 3;
     ref0 = off;
     off += chunk * 3;
-    ds = maxw | 1;
+    ds = maxd + 4;
     d0 = off;
     off += chunk * ds;
     d1 = off;
@@ -223,7 +238,7 @@ struct TrainLayout {
       const int j = idx / ni;
       return w_off[l] + j * ws[l] + (idx - j * ni);
     }
-    return w_off[l] + no * ws[l] + (idx - no * ni);
+    return w_off[l] + np8[l] * ws[l] + (idx - no * ni);
   }
 };
 
@@ -241,127 +256,96 @@ __device__ __forceinline__ float act_grad_out(float h, int act) {
   return h > 0.f ? 1.f : 0.01f;
 }
 
-// out[s][j] = b[j] + sum_k W[j][k] h[s][k] (then the activation), for s < S,
-// j < no; each thread a 4 x 4 tile (samples sg + a*nsg, units jg + b*njg).
-__device__ void layer_forward(const float* __restrict__ W, int ws, const float* __restrict__ bias,
-                              const float* __restrict__ h, int hs, int ni, float* out, int os,
-                              int no, int S, bool hidden, int act) {
-  const int njg = (no + 3) >> 2, nsg = (S + 3) >> 2;
-  for (int e = threadIdx.x; e < njg * nsg; e += blockDim.x) {
-    const int sg = e / njg, jg = e - sg * njg;
-    int sidx[4], jidx[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      sidx[a] = min(sg + a * nsg, S - 1);
-      jidx[a] = min(jg + a * njg, no - 1);
-    }
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = bias[jidx[b]];
-    for (int k = 0; k < ni; ++k) {
-      float hv[4], wv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) hv[a] = h[sidx[a] * hs + k];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) wv[b] = W[jidx[b] * ws + k];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(wv[b], hv[a], acc[a][b]);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int s = sg + a * nsg;
-      if (s >= S) continue;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int j = jg + b * njg;
-        if (j < no) out[s * os + j] = hidden ? act_fwd(acc[a][b], act) : acc[a][b];
-      }
-    }
+// One 16 x 8 tile (rows m0.., columns n0..) of sum_k A(m, k) B(k, n) over
+// k < K (a multiple of 8) into c, on the tensor cores with 3xTF32 (the two
+// small cross terms first).  a(m, k) and b(k, n) read shared memory.
+template <typename FA, typename FB>
+__device__ __forceinline__ void tile_3xtf32(float c[4], int m0, int n0, int K, FA a, FB b) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
+    tf32_split(a(m0 + g, k0 + t), ah[0], al[0]);
+    tf32_split(a(m0 + g + 8, k0 + t), ah[1], al[1]);
+    tf32_split(a(m0 + g, k0 + t + 4), ah[2], al[2]);
+    tf32_split(a(m0 + g + 8, k0 + t + 4), ah[3], al[3]);
+    tf32_split(b(k0 + t, n0 + g), bh0, bl0);
+    tf32_split(b(k0 + t + 4, n0 + g), bh1, bl1);
+    mma_tf32_1688(c, al, bh0, bh1);
+    mma_tf32_1688(c, ah, bl0, bl1);
+    mma_tf32_1688(c, ah, bh0, bh1);
   }
 }
 
-// G[j][k] += sum_s d[s][j] h[s][k]; Gb[j] += sum_s d[s][j].
-__device__ void layer_weight_grad(const float* __restrict__ d, int ds,
-                                  const float* __restrict__ h, int hs, int ni, int no, int S,
-                                  float* G, float* Gb) {
-  const int nkg = (ni + 3) >> 2, njg = (no + 3) >> 2;
-  for (int e = threadIdx.x; e < nkg * njg; e += blockDim.x) {
-    const int jg = e / nkg, kg = e - jg * nkg;
-    int kidx[4], jidx[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      kidx[a] = min(kg + a * nkg, ni - 1);
-      jidx[a] = min(jg + a * njg, no - 1);
+// out[s][j] = act(b[j] + sum_k W[j][k] h[s][k]) for s < M (a multiple of 16)
+// and j < no8 (the padded outputs come out zero: zero weights and bias, and
+// act(0) = 0).  The warps take the 16 x 8 tiles in turn.
+__device__ void layer_forward(const float* W, int ws, const float* bias, const float* h, int hs,
+                              int kp, float* out, int os, int no, int no8, int M, bool hidden,
+                              int act) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int nt = no8 / 8, tiles = (M / 16) * nt;
+  for (int e = warp; e < tiles; e += nw) {
+    const int m0 = (e / nt) * 16, n0 = (e % nt) * 8;
+    const int j0 = n0 + 2 * t, j1 = j0 + 1;
+    const float b0 = j0 < no ? bias[j0] : 0.f, b1 = j1 < no ? bias[j1] : 0.f;
+    float c[4] = {b0, b1, b0, b1};
+    tile_3xtf32(c, m0, n0, kp, [&](int m, int k) { return h[m * hs + k]; },
+                [&](int k, int n) { return W[n * ws + k]; });
+    float* o0 = out + (m0 + g) * os + j0;
+    float* o1 = out + (m0 + g + 8) * os + j0;
+    o0[0] = hidden ? act_fwd(c[0], act) : c[0];
+    o0[1] = hidden ? act_fwd(c[1], act) : c[1];
+    o1[0] = hidden ? act_fwd(c[2], act) : c[2];
+    o1[1] = hidden ? act_fwd(c[3], act) : c[3];
+  }
+}
+
+// G[j][k] += sum_{s < K} d[s][j] h[s][k] (j < no, k < ni; K a multiple of 8,
+// rows of d beyond the chunk's samples zero) and Gb[j] += sum_s d[s][j].
+__device__ void layer_weight_grad(const float* d, int ds, const float* h, int hs, int ni, int kp,
+                                  int no, int K, float* G, float* Gb) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int nt = kp / 8, tiles = ((no + 15) / 16) * nt;
+  for (int e = warp; e < tiles; e += nw) {
+    const int m0 = (e / nt) * 16, n0 = (e % nt) * 8;
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    tile_3xtf32(c, m0, n0, K, [&](int m, int k) { return d[k * ds + m]; },
+                [&](int k, int n) { return h[k * hs + n]; });
+    const int ja = m0 + g, jb = ja + 8, k0 = n0 + 2 * t;
+    if (ja < no) {
+      if (k0 < ni) G[ja * ni + k0] += c[0];
+      if (k0 + 1 < ni) G[ja * ni + k0 + 1] += c[1];
     }
-    float acc[4][4] = {};
-    for (int s = 0; s < S; ++s) {
-      float dv[4], hv[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) dv[b] = d[s * ds + jidx[b]];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) hv[a] = h[s * hs + kidx[a]];
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int a = 0; a < 4; ++a) acc[b][a] = fmaf(dv[b], hv[a], acc[b][a]);
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = jg + b * njg;
-      if (j >= no) continue;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int k = kg + a * nkg;
-        if (k < ni) G[j * ni + k] += acc[b][a];
-      }
+    if (jb < no) {
+      if (k0 < ni) G[jb * ni + k0] += c[2];
+      if (k0 + 1 < ni) G[jb * ni + k0 + 1] += c[3];
     }
   }
   for (int j = threadIdx.x; j < no; j += blockDim.x) {
     float acc = 0.f;
-    for (int s = 0; s < S; ++s) acc += d[s * ds + j];
+    for (int s = 0; s < K; ++s) acc += d[s * ds + j];
     Gb[j] += acc;
   }
 }
 
-// dn[s][k] = act'(h[s][k]) * sum_j d[s][j] W[j][k].
-__device__ void layer_delta(const float* __restrict__ d, int ds, const float* __restrict__ W,
-                            int ws, const float* __restrict__ h, int hs, int ni, int no, int S,
-                            float* dn, int act) {
-  const int nkg = (ni + 3) >> 2, nsg = (S + 3) >> 2;
-  for (int e = threadIdx.x; e < nkg * nsg; e += blockDim.x) {
-    const int sg = e / nkg, kg = e - sg * nkg;
-    int sidx[4], kidx[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      sidx[a] = min(sg + a * nsg, S - 1);
-      kidx[a] = min(kg + a * nkg, ni - 1);
-    }
-    float acc[4][4] = {};
-    for (int j = 0; j < no; ++j) {
-      float dv[4], wv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) dv[a] = d[sidx[a] * ds + j];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) wv[b] = W[j * ws + kidx[b]];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(dv[a], wv[b], acc[a][b]);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int s = sg + a * nsg;
-      if (s >= S) continue;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int k = kg + b * nkg;
-        if (k < ni) dn[s * ds + k] = acc[a][b] * act_grad_out(h[s * hs + k], act);
-      }
-    }
+// dn[s][k] = act'(h[s][k]) * sum_{j < no8} d[s][j] W[j][k] for s < M, k < kp.
+__device__ void layer_delta(const float* d, int ds, const float* W, int ws, const float* h,
+                            int hs, int kp, int no8, int M, float* dn, int act) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int nt = kp / 8, tiles = (M / 16) * nt;
+  for (int e = warp; e < tiles; e += nw) {
+    const int m0 = (e / nt) * 16, n0 = (e % nt) * 8;
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    tile_3xtf32(c, m0, n0, no8, [&](int m, int k) { return d[m * ds + k]; },
+                [&](int k, int n) { return W[k * ws + n]; });
+    const int sa = m0 + g, sb = sa + 8, k0 = n0 + 2 * t;
+    dn[sa * ds + k0] = c[0] * act_grad_out(h[sa * hs + k0], act);
+    dn[sa * ds + k0 + 1] = c[1] * act_grad_out(h[sa * hs + k0 + 1], act);
+    dn[sb * ds + k0] = c[2] * act_grad_out(h[sb * hs + k0], act);
+    dn[sb * ds + k0 + 1] = c[3] * act_grad_out(h[sb * hs + k0 + 1], act);
   }
 }
 
@@ -383,6 +367,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nn_train_kernel(const TrainP
   float* STD = sm + L.std0;
   double* LOSS = reinterpret_cast<double*>(sm + L.loss0);
 
+  // weights with zero padding (the padded rows and columns stay zero: Adam
+  // writes only real parameters)
+  for (int q = tid; q < L.w_total; q += nth) W[q] = 0.f;
+  __syncthreads();
   for (int q = tid; q < P; q += nth) W[L.padded(q)] = p.params[q];
   for (int c = tid; c < 81; c += nth) {
     MEAN[c] = p.in_mean[c];
@@ -394,6 +382,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nn_train_kernel(const TrainP
   const int pc = (P + C - 1) / C;
   const int q_begin = min(P, rank * pc), q_end = min(P, q_begin + pc);
   const float dscale = 2.f * p.out_scale / (3.f * (float)B);
+  // beta^t of the first step of this launch (t = adam_t0 + 1), then one
+  // multiplication per step
+  double b1t = pow((double)p.beta1, (double)(p.adam_t0 + 1));
+  double b2t = pow((double)p.beta2, (double)(p.adam_t0 + 1));
   // every CTA's copy initialised before any CTA touches another's memory
   cluster.sync();
 
@@ -404,8 +396,17 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nn_train_kernel(const TrainP
     __syncthreads();
     for (int c0 = s_begin; c0 < s_end; c0 += L.chunk) {
       const int S = min(L.chunk, s_end - c0);
-      // inputs (z-scored), the base values f_{3,6,7}(L-1) and the targets
+      const int M = (S + 15) / 16 * 16;     // rows of the forward and delta products
+      const int K8 = (S + 7) / 8 * 8;       // samples summed by the weight gradients
+      // inputs (z-scored; padding zero), the base values f_{3,6,7}(L-1), the
+      // targets, and a zero output delta (its padding is read as zero)
       float* H0 = sm + L.h_off[0];
+      for (int e = tid; e < M * L.kp[0]; e += nth) {
+        const int s = e / L.kp[0], c = e - s * L.kp[0];
+        H0[s * L.hs[0] + c] = 0.f;
+      }
+      for (int e = tid; e < M * L.ds; e += nth) Dbuf[0][e] = 0.f;
+      __syncthreads();
       for (int e = tid; e < S * kRowFloats; e += nth) {
         const int s = e / kRowFloats, c = e - s * kRowFloats;
         const float v = p.rows[(row0 + c0 + s) * kRowFloats + c];
@@ -419,15 +420,15 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nn_train_kernel(const TrainP
       for (int l = 0; l < nl; ++l) {
         const bool hidden = l < nl - 1;
         const float* Wl = W + L.w_off[l];
-        layer_forward(Wl, L.ws[l], Wl + L.sizes[l + 1] * L.ws[l], sm + L.h_off[l], L.hs[l],
-                      L.sizes[l], hidden ? sm + L.h_off[l + 1] : OUT,
-                      hidden ? L.hs[l + 1] : 3, L.sizes[l + 1], S, hidden, p.act);
+        layer_forward(Wl, L.ws[l], Wl + L.np8[l] * L.ws[l], sm + L.h_off[l], L.hs[l], L.kp[l],
+                      hidden ? sm + L.h_off[l + 1] : OUT, hidden ? L.hs[l + 1] : L.os,
+                      L.sizes[l + 1], L.np8[l], M, hidden, p.act);
         __syncthreads();
       }
       // Eq. 16: r = f_{3,6,7}(L-1) + out_scale * o - f_ref; dL/do = 2 out_scale r / (3B)
       for (int e = tid; e < S * 3; e += nth) {
         const int s = e / 3, n = e - s * 3;
-        const float r = BASE[e] + p.out_scale * OUT[e] - REF[e];
+        const float r = BASE[e] + p.out_scale * OUT[s * L.os + n] - REF[e];
         lacc += (double)r * (double)r;
         Dbuf[0][s * L.ds + n] = dscale * r;
       }
@@ -437,11 +438,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nn_train_kernel(const TrainP
         for (int l = nl - 1; l >= 0; --l) {
           const int ni = L.sizes[l], no = L.sizes[l + 1];
           float* Gw = G + L.g_off[l];
-          layer_weight_grad(Dbuf[cur], L.ds, sm + L.h_off[l], L.hs[l], ni, no, S, Gw,
+          layer_weight_grad(Dbuf[cur], L.ds, sm + L.h_off[l], L.hs[l], ni, L.kp[l], no, K8, Gw,
                             Gw + no * ni);
           if (l > 0)
-            layer_delta(Dbuf[cur], L.ds, W + L.w_off[l], L.ws[l], sm + L.h_off[l], L.hs[l], ni,
-                        no, S, Dbuf[1 - cur], p.act);
+            layer_delta(Dbuf[cur], L.ds, W + L.w_off[l], L.ws[l], sm + L.h_off[l], L.hs[l],
+                        L.kp[l], L.np8[l], M, Dbuf[1 - cur], p.act);
           __syncthreads();
           cur = 1 - cur;
         }
@@ -458,13 +459,23 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nn_train_kernel(const TrainP
     }
     cluster.sync();   // every CTA's G and loss are complete
 
+    // the cluster's gradient of parameter q: the CTAs' partial sums added in
+    // CTA order (all remote loads issued before the first addition)
+    auto cluster_grad = [&](int q) {
+      float gv[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) gv[r] = r < C ? cluster.map_shared_rank(G, r)[q] : 0.f;
+      float g = 0.f;
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        if (r < C) g += gv[r];
+      return g;
+    };
     if (p.mode == 0) {
-      const int64_t t = p.adam_t0 + k + 1;
-      const float bc1 = (float)(1.0 - pow((double)p.beta1, (double)t));
-      const float bc2 = (float)(1.0 - pow((double)p.beta2, (double)t));
+      // bias corrections 1 - beta^t, t = adam_t0 + k + 1, from the running powers
+      const float bc1 = (float)(1.0 - b1t), bc2 = (float)(1.0 - b2t);
       for (int q = q_begin + tid; q < q_end; q += nth) {
-        float g = 0.f;
-        for (int r = 0; r < C; ++r) g += cluster.map_shared_rank(G, r)[q];
+        const float g = cluster_grad(q);
         const float m = p.beta1 * p.adam_m[q] + (1.f - p.beta1) * g;
         const float v = p.beta2 * p.adam_v[q] + (1.f - p.beta2) * g * g;
         p.adam_m[q] = m;
@@ -473,12 +484,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1) nn_train_kernel(const TrainP
         const float w = W[pq] - p.lr * (m / bc1) / (sqrtf(v / bc2) + p.eps);
         for (int r = 0; r < C; ++r) cluster.map_shared_rank(W, r)[pq] = w;
       }
+      b1t *= (double)p.beta1;
+      b2t *= (double)p.beta2;
     } else if (p.mode == 1) {
-      for (int q = q_begin + tid; q < q_end; q += nth) {
-        float g = 0.f;
-        for (int r = 0; r < C; ++r) g += cluster.map_shared_rank(G, r)[q];
-        p.grad_out[k * P + q] = g;
-      }
+      for (int q = q_begin + tid; q < q_end; q += nth) p.grad_out[k * P + q] = cluster_grad(q);
     }
     if (rank == 0 && tid == 0) {
       double tot = 0.0;
@@ -496,9 +505,10 @@ int train_smem_bytes(const int* sizes, int n_layers, int chunk) {
 }
 
 int train_max_chunk(const int* sizes, int n_layers, int batch_per_cta, int smem_limit) {
-  int chunk = ((batch_per_cta + 3) / 4) * 4;
+  // a multiple of 16 samples (the rows of a tensor-core tile)
+  int chunk = ((batch_per_cta + 15) / 16) * 16;
   if (chunk > 128) chunk = 128;
-  while (chunk > 4 && train_smem_bytes(sizes, n_layers, chunk) > smem_limit) chunk -= 4;
+  while (chunk > 16 && train_smem_bytes(sizes, n_layers, chunk) > smem_limit) chunk -= 16;
   return train_smem_bytes(sizes, n_layers, chunk) <= smem_limit ? chunk : 0;
 }
 
