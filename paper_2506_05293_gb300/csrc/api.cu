@@ -350,6 +350,60 @@ uint16_t bf16_rn(float f) {
   return (uint16_t)(u >> 16);
 }
 
+// IEEE binary32 -> TF32 (10 mantissa bits), round to nearest with ties away
+// from zero, as the device's cvt.rna.tf32.f32 (finite inputs): the result is
+// a binary32 value whose 13 low mantissa bits are zero
+float tf32_rna_host(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+// The blob of the NN outflow's tensor-core blocks (layout at nn_tc_layer_floats
+// in sim.cuh): input constants, then per layer the TF32-split weights in mma
+// fragment order and the padded bias.
+std::vector<float> nn_tc_blob(const lbm_mlp* net) {
+  using namespace lbm;
+  int64_t n = 4 * kNnTcFeat;
+  for (int l = 0; l < net->n_layers; ++l) n += nn_tc_layer_floats(net->sizes[l], net->sizes[l + 1]);
+  std::vector<float> b((size_t)n, 0.f);
+  for (int kx = 0; kx < 81; ++kx) {
+    const int col = kx / 27, j = (kx / 9) % 3, i = kx % 9, o = opp(i), c = 3 - col;
+    const float mean = net->in_mean ? net->in_mean[kx] : 0.f;
+    const float sd = net->in_std ? net->in_std[kx] : 1.f;
+    b[(size_t)kx] = mean - wgt<float>(i);
+    b[(size_t)(kNnTcFeat + kx)] = 1.f / sd;
+    b[(size_t)(2 * kNnTcFeat + kx)] = (float)((i * kNnTcWin + j + 1 - cy(i)) * 5 + c - cx(i));
+    b[(size_t)(3 * kNnTcFeat + kx)] = (float)((o * kNnTcWin + j + 1 - cy(o)) * 5 + c - cx(o));
+  }
+  int64_t off = 4 * kNnTcFeat, poff = 0;
+  for (int l = 0; l < net->n_layers; ++l) {
+    const int ni = net->sizes[l], no = net->sizes[l + 1];
+    const int K8 = nn_tc_pad8(ni) / 8, N8 = nn_tc_pad8(no) / 8;
+    const float* W = net->params + poff;   // [no][ni]
+    for (int jt = 0; jt < N8; ++jt)
+      for (int kk = 0; kk < K8; ++kk)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int nn = jt * 8 + lane / 4, k = kk * 8 + lane % 4;
+          const float w0 = nn < no && k < ni ? W[(int64_t)nn * ni + k] : 0.f;
+          const float w1 = nn < no && k + 4 < ni ? W[(int64_t)nn * ni + k + 4] : 0.f;
+          const float h0 = tf32_rna_host(w0), h1 = tf32_rna_host(w1);
+          float* q = &b[(size_t)(off + (((int64_t)jt * K8 + kk) * 32 + lane) * 4)];
+          q[0] = h0;
+          q[1] = h1;
+          q[2] = tf32_rna_host(w0 - h0);
+          q[3] = tf32_rna_host(w1 - h1);
+        }
+    off += (int64_t)N8 * K8 * 8 * 8 * 2;
+    for (int jj = 0; jj < no; ++jj) b[(size_t)(off + jj)] = net->params[poff + (int64_t)no * ni + jj];
+    off += nn_tc_pad8(no);
+    poff += (int64_t)ni * no + no;
+  }
+  return b;
+}
+
 // offset of layer l's W in lbm_mlp.params
 int64_t off_of(const lbm_mlp* net, int l) {
   int64_t off = 0;
@@ -396,16 +450,19 @@ lbm_status upload_net(lbm_sim* s, const lbm_mlp* net, int n_in, int64_t np) {
       woff += (int64_t)npd * kp;
     }
   }
+  // the tensor-core blocks' blob (NN outflow: 81 inputs)
+  std::vector<float> tcb;
+  if (n_in == 81) tcb = nn_tc_blob(net);
   LBM_GUARD_BEGIN
   if (!s->nn.params_f || s->nn.blob_elems != (int32_t)blob_n ||
-      s->nn.bf16_elems != (int64_t)wb.size()) {
+      s->nn.bf16_elems != (int64_t)wb.size() || s->nn.tc_elems != (int32_t)tcb.size()) {
     // all copies or none: a failed allocation leaves the current network
     const lbm_allocator* a = s->have_alloc ? &s->alloc : nullptr;
-    const size_t bytes[3] = {blob.size() * sizeof(float), blob.size() * sizeof(double),
-                             wb.size() * sizeof(uint16_t)};
-    void* fresh[3] = {nullptr, nullptr, nullptr};
+    const size_t bytes[4] = {blob.size() * sizeof(float), blob.size() * sizeof(double),
+                             wb.size() * sizeof(uint16_t), tcb.size() * sizeof(float)};
+    void* fresh[4] = {nullptr, nullptr, nullptr, nullptr};
     try {
-      for (int k = 0; k < 3; ++k)
+      for (int k = 0; k < 4; ++k)
         if (bytes[k]) fresh[k] = lbm::dev_alloc_raw(a, bytes[k]);
     } catch (...) {
       for (void* q : fresh) lbm::dev_free_raw(a, q);
@@ -415,7 +472,8 @@ lbm_status upload_net(lbm_sim* s, const lbm_mlp* net, int n_in, int64_t np) {
       // launch tables may still name the old copies: free them once the stream is idle
       lbm::sim_settle(s);
       ck(cudaStreamSynchronize(s->stream), "net sync");
-      for (void* q : {(void*)s->nn.params_f, (void*)s->nn.params_d, (void*)s->nn.params_bf16}) {
+      for (void* q : {(void*)s->nn.params_f, (void*)s->nn.params_d, (void*)s->nn.params_bf16,
+                      (void*)s->nn.params_tc}) {
         if (!q) continue;
         s->owned.erase(std::remove(s->owned.begin(), s->owned.end(), q), s->owned.end());
         lbm::dev_free_raw(a, q);
@@ -424,6 +482,7 @@ lbm_status upload_net(lbm_sim* s, const lbm_mlp* net, int n_in, int64_t np) {
     s->nn.params_f = (float*)fresh[0];
     s->nn.params_d = (double*)fresh[1];
     s->nn.params_bf16 = (uint16_t*)fresh[2];
+    s->nn.params_tc = (float*)fresh[3];
     for (void* q : fresh)
       if (q) s->owned.push_back(q);
   }
@@ -435,8 +494,12 @@ lbm_status upload_net(lbm_sim* s, const lbm_mlp* net, int n_in, int64_t np) {
   if (!wb.empty())
     ck(cudaMemcpyAsync(s->nn.params_bf16, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice,
                        s->stream), "net copy");
+  if (!tcb.empty())
+    ck(cudaMemcpyAsync(s->nn.params_tc, tcb.data(), tcb.size() * 4, cudaMemcpyHostToDevice,
+                       s->stream), "net copy");
   ck(cudaStreamSynchronize(s->stream), "net sync");
   s->nn.bf16_elems = (int64_t)wb.size();
+  s->nn.tc_elems = (int32_t)tcb.size();
   s->nn.n_layers = net->n_layers;
   for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) s->nn.sizes[l] = l <= net->n_layers ? net->sizes[l] : 0;
   s->nn.act = net->act;

@@ -65,6 +65,11 @@ void fill_member(const lbm_sim* s, Member& m) {
       m.nn_net = s->prec == LBM_FP64 ? (const void*)s->nn.params_d : (const void*)s->nn.params_f;
       m.nn_bf16 = s->nn.params_bf16;
       m.nn_blob_elems = s->nn.blob_elems;
+      if (m.ext_kind == 1 && s->prec != LBM_FP64) {
+        // the tensor-core network blocks read their own blob
+        m.nn_net = s->nn.params_tc;
+        m.nn_blob_elems = s->nn.tc_elems;
+      }
       m.nn_layers = s->nn.n_layers;
       m.nn_act = s->nn.act;
       for (int l = 0; l <= LBM_MLP_MAX_LAYERS; ++l) m.nn_sizes[l] = s->nn.sizes[l];
@@ -376,7 +381,9 @@ StepParams params(const Group& g, int q) {
   p.has_cbc = 0;
   for (const lbm_sim* s : g.sims) {
     const int kind = ext_kind(s);
-    if (kind == 1) p.nn_blob_max = std::max(p.nn_blob_max, (int32_t)s->nn.blob_elems);
+    if (kind == 1)
+      p.nn_blob_max = std::max(p.nn_blob_max, (int32_t)(s->prec == LBM_FP64 ? s->nn.blob_elems
+                                                                          : s->nn.tc_elems));
     if (kind == 2) p.has_cbc = 1;
   }
   p.dyn_ctr = g.dyn_ctr;

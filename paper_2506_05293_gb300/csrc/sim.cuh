@@ -105,6 +105,31 @@ struct StepParams {
                                  // kernels then read it from the parameter bank
 };
 
+// Tensor-core network blocks of the NN outflow (FP32 and FP16 storage): a
+// block takes kNnTcNodes consecutive east nodes (the rows of one mma tile)
+// and stages the window of columns L-4 .. L at rows y0-2 .. y0+kNnTcNodes+1.
+constexpr int kNnTcNodes = 16;
+constexpr int kNnTcWin = kNnTcNodes + 4;
+constexpr int kNnTcFeat = 88;        // the 81 inputs padded to a multiple of 8
+constexpr int kNnTcLdIn = 92;        // row stride of the input tile (88 used; 92 = 28 mod 32
+                                     // keeps the fragment loads conflict-free)
+constexpr int kNnTcLdAct = 68;       // row stride of hidden activations (64 used)
+
+// Their network blob (floats, copied whole into shared memory):
+// [0, 4 kNnTcFeat): per input k < 88 the z-score shift (in_mean - w_i), the
+//   inverse standard deviation, and the window offsets of its pull when the
+//   node it is taken at is fluid and when it is solid (bounce-back reverses
+//   the direction), as small integers; zeros for k >= 81;
+// then per layer: the weights split into TF32 high and low parts in mma
+//   fragment order -- for each 8-column n-tile and 8-row k-step, lane
+//   (g, t) = (lane / 4, lane % 4) holds {hi W[n][k], hi W[n][k+4], lo W[n][k],
+//   lo W[n][k+4]} with n = 8 ntile + g, k = 8 kstep + t (zero outside the
+//   network) -- then the bias padded to a multiple of 8.
+__host__ __device__ constexpr int nn_tc_pad8(int n) { return (n + 7) / 8 * 8; }
+__host__ __device__ constexpr int nn_tc_layer_floats(int ni, int no) {
+  return nn_tc_pad8(no) * nn_tc_pad8(ni) * 2 + nn_tc_pad8(no);
+}
+
 // Direct-reconstruction network on the device (FP32 and FP64 copies).
 struct DevMlp {
   int n_layers = 0;
@@ -116,6 +141,8 @@ struct DevMlp {
   double* params_d = nullptr;
   uint16_t* params_bf16 = nullptr;   // tuner only: padded BF16 weights of the tensor-core path
   int64_t bf16_elems = 0;
+  float* params_tc = nullptr;        // NN outflow only: the blob of the tensor-core blocks
+  int32_t tc_elems = 0;
   float out_scale = 1.f;
 };
 

@@ -457,40 +457,40 @@ __device__ __forceinline__ R post_stream_h(const S* __restrict__ A, const Member
 // (1) One round of loads stages the window the block needs: the nine stored
 // populations of columns L-4 .. L at rows y0-2 .. y0+17 (every pull of the
 // 81 inputs of its nodes and of the nodes themselves) and the solid bits of
-// those rows, while one thread copies the whole network (weights and input
-// statistics, about 39 KB for 81-64-64-3) into shared memory with a single
-// cp.async.bulk.  (2) The 81 inputs of every node are formed in shared memory
-// (post-stream values: pulls, reversed at solid nodes; z-scored), zero-padded
-// to K = 88.  (3) Each layer is one GEMM [16 x K] x [K x N] with
-// mma.sync m16n8k8 on TF32 operands split into high and low parts (3xTF32:
-// hi*hi + hi*lo + lo*hi, FP32 accumulators initialised with the bias), which
-// keeps the products to FP32 accuracy; the warps take the layer's 8-column
-// n-tiles in turn, reading the weights from shared memory.  (4) One thread
+// those rows, while one thread copies the network blob (input constants and
+// the weights, already split into TF32 high and low parts in fragment order:
+// about 82 KB for 81-64-64-3) into shared memory with two cp.async.bulk
+// copies (the constants first, the weights waited for only before layer 1).
+// (2) The 81 inputs of every node are formed in shared memory (post-stream
+// values: pulls, reversed at solid nodes; z-scored), zero-padded to K = 88 and
+// stored as their TF32 high and low parts.  (3) Each layer is one GEMM
+// [16 x K] x [K x N] with mma.sync m16n8k8 (3xTF32: hi*hi + hi*lo + lo*hi,
+// FP32 accumulators initialised with the bias), which keeps the products to
+// FP32 accuracy; the warps take the layer's 8-column n-tiles in turn, and a
+// hidden layer's activations are stored split for the next.  (4) One thread
 // per node applies Eq. 15 with the Zou & He fallback and collides.
-constexpr int kNnTcNodes = 16;                 // east nodes per tensor-core network block
-constexpr int kNnTcWin = kNnTcNodes + 4;       // window rows y0-2 .. y0+17
-constexpr int kNnTcLdIn = 92;                  // row stride of the input tile (88 used; 92 = 28
-                                               // mod 32 keeps the fragment loads conflict-free)
-constexpr int kNnTcLdAct = 68;                 // row stride of hidden activations (64 used)
 
-// shared memory of a tensor-core network block: the network blob (per layer
-// W^T then b, in_mean, in_std; blob_elems floats, a multiple of 4), then the
-// window, solid bits, the two activation tiles and the copy's mbarrier
+// shared memory of a tensor-core network block: the network blob, then the
+// window, solid bits, the high and low planes of the two activation tiles
+// and the two copies' mbarriers
 __host__ __device__ constexpr size_t nn_tc_fixed_bytes() {
-  return (size_t)9 * kNnTcWin * 5 * 4 + 32 + (size_t)kNnTcNodes * kNnTcLdIn * 4 +
-         (size_t)kNnTcNodes * kNnTcLdAct * 4 + 16;
+  return (size_t)9 * kNnTcWin * 5 * 4 + 32 + 2 * (size_t)kNnTcNodes * kNnTcLdIn * 4 +
+         2 * (size_t)kNnTcNodes * kNnTcLdAct * 4 + 2 * 8;
 }
 __host__ __device__ constexpr size_t nn_tc_smem_bytes(int blob_elems) {
   return (size_t)blob_elems * 4 + nn_tc_fixed_bytes();
 }
 
-// out[16][n_out] = act(in[16][n_in] W^T + b) for the block's 16 nodes; in is
-// zero-padded to a multiple of 8 columns (row stride ldi), out gets the padded
-// columns too (zero weights and bias: act(0) = 0).  Wt is the transposed
-// weight matrix [n_in][n_out], bias [n_out], both in shared memory.
-__device__ inline void nn_layer_tc(const float* in, int ldi, int n_in, float* out, int ldo,
-                                   int n_out, const float* Wt, const float* bias, bool hidden,
-                                   int act) {
+// out[16][n_out] = act(in[16][n_in] W^T + b) for the block's 16 nodes.  in
+// is given as its TF32 high and low planes (inH, inL; row stride ldi, zero
+// past n_in up to a multiple of 8); wb is the layer's weights in fragment
+// order (nn_tc_layer_floats), bias the padded bias.  A hidden layer writes
+// its activations as high and low planes (outH, outL), the padded columns
+// zero (zero weights and bias, act(0) = 0); the last layer writes plain
+// values to outH.
+__device__ inline void nn_layer_tc(const float* inH, const float* inL, int ldi, int n_in,
+                                   float* outH, float* outL, int ldo, int n_out,
+                                   const float* wb, const float* bias, bool hidden, int act) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
   const int g = lane >> 2, t4 = lane & 3;
   const int K8 = (n_in + 7) / 8, N8 = (n_out + 7) / 8;
@@ -498,56 +498,65 @@ __device__ inline void nn_layer_tc(const float* in, int ldi, int n_in, float* ou
   const int j0 = warp, j1 = warp + nw;
   const bool has0 = j0 < N8, has1 = j1 < N8;
   if (!has0) return;
-  float c0[4], c1[4];
+  // per n-tile three accumulators: hi*hi (from the bias) and the two small
+  // cross terms, so that each mma chain is one k-step long per k-step
+  float c0[4], c1[4], p0[4] = {0.f, 0.f, 0.f, 0.f}, q0[4] = {0.f, 0.f, 0.f, 0.f};
+  float p1[4] = {0.f, 0.f, 0.f, 0.f}, q1[4] = {0.f, 0.f, 0.f, 0.f};
   {
     const int nc0 = j0 * 8 + 2 * t4, nc1 = j1 * 8 + 2 * t4;
-    c0[0] = nc0 < n_out ? bias[nc0] : 0.f;
-    c0[1] = nc0 + 1 < n_out ? bias[nc0 + 1] : 0.f;
-    c1[0] = has1 && nc1 < n_out ? bias[nc1] : 0.f;
-    c1[1] = has1 && nc1 + 1 < n_out ? bias[nc1 + 1] : 0.f;
-    c0[2] = c0[0];
-    c0[3] = c0[1];
-    c1[2] = c1[0];
-    c1[3] = c1[1];
+    c0[0] = c0[2] = bias[nc0];
+    c0[1] = c0[3] = bias[nc0 + 1];
+    c1[0] = c1[2] = has1 ? bias[nc1] : 0.f;
+    c1[1] = c1[3] = has1 ? bias[nc1 + 1] : 0.f;
   }
-  const int n0 = j0 * 8 + g, n1 = j1 * 8 + g;   // this lane's columns of B
+  const float4* w0 = reinterpret_cast<const float4*>(wb) + (size_t)j0 * K8 * 32 + lane;
+  const float4* w1 = reinterpret_cast<const float4*>(wb) + (size_t)j1 * K8 * 32 + lane;
 #pragma unroll 2
   for (int kk = 0; kk < K8; ++kk) {
     const int k0 = kk * 8 + t4;
     uint32_t ah[4], al[4];
-    tf32_split(in[g * ldi + k0], ah[0], al[0]);
-    tf32_split(in[(g + 8) * ldi + k0], ah[1], al[1]);
-    tf32_split(in[g * ldi + k0 + 4], ah[2], al[2]);
-    tf32_split(in[(g + 8) * ldi + k0 + 4], ah[3], al[3]);
-    const bool ka = k0 < n_in, kb = k0 + 4 < n_in;
+    ah[0] = __float_as_uint(inH[g * ldi + k0]);
+    ah[1] = __float_as_uint(inH[(g + 8) * ldi + k0]);
+    ah[2] = __float_as_uint(inH[g * ldi + k0 + 4]);
+    ah[3] = __float_as_uint(inH[(g + 8) * ldi + k0 + 4]);
+    al[0] = __float_as_uint(inL[g * ldi + k0]);
+    al[1] = __float_as_uint(inL[(g + 8) * ldi + k0]);
+    al[2] = __float_as_uint(inL[g * ldi + k0 + 4]);
+    al[3] = __float_as_uint(inL[(g + 8) * ldi + k0 + 4]);
     {
-      uint32_t bh0, bl0, bh1, bl1;
-      tf32_split(n0 < n_out && ka ? Wt[k0 * n_out + n0] : 0.f, bh0, bl0);
-      tf32_split(n0 < n_out && kb ? Wt[(k0 + 4) * n_out + n0] : 0.f, bh1, bl1);
-      mma_tf32_1688(c0, al, bh0, bh1);   // the small terms first
-      mma_tf32_1688(c0, ah, bl0, bl1);
-      mma_tf32_1688(c0, ah, bh0, bh1);
+      const float4 w = w0[kk * 32];
+      mma_tf32_1688(p0, al, __float_as_uint(w.x), __float_as_uint(w.y));
+      mma_tf32_1688(q0, ah, __float_as_uint(w.z), __float_as_uint(w.w));
+      mma_tf32_1688(c0, ah, __float_as_uint(w.x), __float_as_uint(w.y));
     }
     if (has1) {
-      uint32_t bh0, bl0, bh1, bl1;
-      tf32_split(n1 < n_out && ka ? Wt[k0 * n_out + n1] : 0.f, bh0, bl0);
-      tf32_split(n1 < n_out && kb ? Wt[(k0 + 4) * n_out + n1] : 0.f, bh1, bl1);
-      mma_tf32_1688(c1, al, bh0, bh1);
-      mma_tf32_1688(c1, ah, bl0, bl1);
-      mma_tf32_1688(c1, ah, bh0, bh1);
+      const float4 w = w1[kk * 32];
+      mma_tf32_1688(p1, al, __float_as_uint(w.x), __float_as_uint(w.y));
+      mma_tf32_1688(q1, ah, __float_as_uint(w.z), __float_as_uint(w.w));
+      mma_tf32_1688(c1, ah, __float_as_uint(w.x), __float_as_uint(w.y));
     }
   }
-  auto store = [&](const float c[4], int j) {
-    float v[4] = {c[0], c[1], c[2], c[3]};
-    if (hidden) {
+  // the small terms added first
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = act_hidden<float>(v[q], act);
-    }
+  for (int q = 0; q < 4; ++q) {
+    c0[q] += p0[q] + q0[q];
+    c1[q] += p1[q] + q1[q];
+  }
+  auto store = [&](const float c[4], int j) {
     const int nc = j * 8 + 2 * t4;
-    out[g * ldo + nc] = v[0];
-    out[g * ldo + nc + 1] = v[1];
-    out[(g + 8) * ldo + nc] = v[2];
-    out[(g + 8) * ldo + nc + 1] = v[3];
+    const int idx[4] = {g * ldo + nc, g * ldo + nc + 1, (g + 8) * ldo + nc,
+                        (g + 8) * ldo + nc + 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (hidden) {
+        uint32_t hi, lo;
+        tf32_split(act_hidden<float>(c[q], act), hi, lo);
+        outH[idx[q]] = __uint_as_float(hi);
+        outL[idx[q]] = __uint_as_float(lo);
+      } else {
+        outH[idx[q]] = c[q];
+      }
+    }
   };
   store(c0, j0);
   if (has1) store(c1, j1);
@@ -572,16 +581,24 @@ __device__ __noinline__ void nn_block_tc(const StepParams& p, const Member& m, i
   float* net = reinterpret_cast<float*>(smem);                      // the network blob
   float* win = net + m.nn_blob_elems;                               // [9][WR][5]
   uint8_t* sol = reinterpret_cast<uint8_t*>(win + NWIN);            // [WR] solid bits of L-4 .. L
-  float* buf0 = reinterpret_cast<float*>(sol + 32);                 // [G][kNnTcLdIn]
-  float* buf1 = buf0 + G * kNnTcLdIn;                               // [G][kNnTcLdAct]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(buf1 + G * kNnTcLdAct);
-  // (1) the network blob by one bulk copy, overlapping the window loads
-  const uint32_t blob_bytes = (uint32_t)m.nn_blob_elems * 4u;
+  float* buf0H = reinterpret_cast<float*>(sol + 32);                // [G][kNnTcLdIn], high
+  float* buf0L = buf0H + G * kNnTcLdIn;                             // and low parts
+  float* buf1H = buf0L + G * kNnTcLdIn;                             // [G][kNnTcLdAct]
+  float* buf1L = buf1H + G * kNnTcLdAct;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(buf1L + G * kNnTcLdAct);
+  // (1) the network blob by two bulk copies overlapping the window loads:
+  // the input constants (needed first, on bar[0]) and the weights (bar[1])
+  constexpr uint32_t tab_bytes = 4u * kNnTcFeat * 4u;
+  const uint32_t w_bytes = (uint32_t)m.nn_blob_elems * 4u - tab_bytes;
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    mbar_expect_tx(bar, blob_bytes);
-    bulk_copy_g2s(net, m.nn_net, blob_bytes, bar);
+    mbar_expect_tx(&bar[0], tab_bytes);
+    bulk_copy_g2s(net, m.nn_net, tab_bytes, &bar[0]);
+    mbar_expect_tx(&bar[1], w_bytes);
+    bulk_copy_g2s(net + 4 * kNnTcFeat,
+                  static_cast<const float*>(m.nn_net) + 4 * kNnTcFeat, w_bytes, &bar[1]);
   }
   // the window: A_i at rows y0-2+r, columns L-4+c; every load of a thread
   // issued before any is used
@@ -616,12 +633,12 @@ __device__ __noinline__ void nn_block_tc(const StepParams& p, const Member& m, i
     }
     sol[threadIdx.x] = (uint8_t)bits;
   }
-  // the copy must land before the weights are read (and before the block may
-  // exit): a bounded wait, which on giving up latches DEV_TIMEOUT and waits once
-  // more so that no copy is left in flight
-  if (threadIdx.x == 0 && !mbar_wait_bounded(bar, 0)) {
+  // the constants must land before the inputs are formed: a bounded wait,
+  // which on giving up latches DEV_TIMEOUT and waits once more so that no copy
+  // is left in flight (the weights are waited for before the layers)
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar[0], 0)) {
     atomicOr(m.status, DEV_TIMEOUT);
-    mbar_wait_bounded(bar, 0);
+    mbar_wait_bounded(&bar[0], 0);
   }
   __syncthreads();
   // post-stream h_i at window row r, column c (bounce-back at solid nodes)
@@ -630,49 +647,58 @@ __device__ __noinline__ void nn_block_tc(const StepParams& p, const Member& m, i
     const int k = solid ? opp(i) : i;
     return win[(k * WR + r - cy(k)) * 5 + c - cx(k)];
   };
-  int n_params = 0;
-  for (int l = 0; l < m.nn_layers; ++l)
-    n_params += m.nn_sizes[l] * m.nn_sizes[l + 1] + m.nn_sizes[l + 1];
-  const float* in_mean = net + n_params;
-  const float* in_std = in_mean + 81;
   // (2) inputs, index k*27 + j*9 + i: column L-1-k, row y-1+j, population i;
-  // a thread takes one input index for a quarter of the nodes (window offsets
-  // of the pull and of the reversed pull at a solid node computed once)
+  // a thread takes one input index for a quarter of the nodes, with its
+  // z-score constants and window offsets read from the blob's table
+  const float* tab = net;                       // [4][kNnTcFeat]
   constexpr int NQ = G / 4;
-  for (int e = threadIdx.x; e < 88 * 4; e += T) {
-    const int kx = e % 88, n0 = (e / 88) * NQ;
+  for (int e = threadIdx.x; e < kNnTcFeat * 4; e += T) {
+    const int kx = e % kNnTcFeat, n0 = (e / kNnTcFeat) * NQ;
     if (kx < 81) {
-      const int col = kx / 27, j = (kx / 9) % 3, i = kx % 9, o = opp(i);
-      const int c = 3 - col;
-      const float mean = in_mean[kx] - wgt<float>(i), inv = 1.f / in_std[kx];
-      const int off_f = (i * WR + j + 1 - cy(i)) * 5 + c - cx(i);   // node fluid
-      const int off_s = (o * WR + j + 1 - cy(o)) * 5 + c - cx(o);   // node solid
+      const int j = (kx / 9) % 3, c = 3 - kx / 27;
+      const float shift = tab[kx], inv = tab[kNnTcFeat + kx];
+      const int off_f = (int)tab[2 * kNnTcFeat + kx];   // node fluid
+      const int off_s = (int)tab[3 * kNnTcFeat + kx];   // node solid
 #pragma unroll
       for (int n = n0; n < n0 + NQ; ++n) {
         const bool solid = (sol[n + j + 1] >> c) & 1u;
-        buf0[n * kNnTcLdIn + kx] = (win[(solid ? off_s : off_f) + 5 * n] - mean) * inv;
+        uint32_t hi, lo;
+        tf32_split((win[(solid ? off_s : off_f) + 5 * n] - shift) * inv, hi, lo);
+        buf0H[n * kNnTcLdIn + kx] = __uint_as_float(hi);
+        buf0L[n * kNnTcLdIn + kx] = __uint_as_float(lo);
       }
     } else {
 #pragma unroll
-      for (int n = n0; n < n0 + NQ; ++n) buf0[n * kNnTcLdIn + kx] = 0.f;
+      for (int n = n0; n < n0 + NQ; ++n) {
+        buf0H[n * kNnTcLdIn + kx] = 0.f;
+        buf0L[n * kNnTcLdIn + kx] = 0.f;
+      }
     }
   }
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar[1], 0)) {
+    atomicOr(m.status, DEV_TIMEOUT);
+    mbar_wait_bounded(&bar[1], 0);
+  }
   __syncthreads();
-  // (3) the layers, alternating between the two buffers
-  int off = 0;
-  float* cur = buf0;
+  // (3) the layers, alternating between the two tiles
+  int off = 4 * kNnTcFeat;
+  float *curH = buf0H, *curL = buf0L;
   int ld = kNnTcLdIn;
   for (int l = 0; l < m.nn_layers; ++l) {
     const int n_in = m.nn_sizes[l], n_out = m.nn_sizes[l + 1];
     const bool last = l == m.nn_layers - 1;
-    float* nxt = cur == buf0 ? buf1 : buf0;
-    nn_layer_tc(cur, ld, n_in, nxt, kNnTcLdAct, n_out, net + off, net + off + n_in * n_out,
+    float* nxtH = curH == buf0H ? buf1H : buf0H;
+    float* nxtL = curH == buf0H ? buf1L : buf0L;
+    const int wfl = nn_tc_layer_floats(n_in, n_out) - nn_tc_pad8(n_out);
+    nn_layer_tc(curH, curL, ld, n_in, nxtH, nxtL, kNnTcLdAct, n_out, net + off, net + off + wfl,
                 !last, m.nn_act);
     __syncthreads();
-    off += n_in * n_out + n_out;
-    cur = nxt;
+    off += nn_tc_layer_floats(n_in, n_out);
+    curH = nxtH;
+    curL = nxtL;
     ld = kNnTcLdAct;
   }
+  const float* cur = curH;                      // the last layer's outputs (plain values)
   // (4) Eq. 15 with the Zou & He fallback, then collision; one thread per node
   const int n = threadIdx.x;
   const int y = y0 + n;
