@@ -176,24 +176,28 @@ __device__ __forceinline__ void collide_mrt(V h[9], const MrtRates<R>& s, V& drh
   using A = Ar<V>;
   V drho, jx, jy;
   moments_shifted(h, drho, jx, jy);
-  const V inv_rho = A::rcp(A::add(A::lit(1), drho));
+  const V rho = A::add(A::lit(1), drho);
+  const V inv_rho = A::rcp(rho);
   const V ux = A::mul(jx, inv_rho), uy = A::mul(jy, inv_rho);
-  V n[9];
-  heq_sym(drho, ux, uy, n);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) n[i] = A::sub(h[i], n[i]);
-  // moments of n (rows of M written out; integer coefficients)
-  const V axis = A::add(A::add(n[1], n[2]), A::add(n[3], n[4]));
-  const V diag = A::add(A::add(n[5], n[6]), A::add(n[7], n[8]));
+  // the six non-conserved moments of h (rows of M written out; integer
+  // coefficients; q(h) = j - 3 (h_1 - h_3) and its y twin) minus those of the
+  // shifted equilibrium: e = -2 drho + 3 rho u.u, eps = drho - 3 rho u.u,
+  // q = -j, pxx = rho (ux^2 - uy^2), pxy = rho ux uy -- the moments of
+  // n = h - h^eq without forming h^eq
+  const V axis = A::add(A::add(h[1], h[2]), A::add(h[3], h[4]));
+  const V diag = A::add(A::add(h[5], h[6]), A::add(h[7], h[8]));
   const V two = A::lit(2);
-  const V m_e = A::fma(two, diag, A::sub(A::mul(A::lit(-4), n[0]), axis));
-  const V m_eps = A::add(A::fma(A::lit(-2), axis, A::mul(A::lit(4), n[0])), diag);
-  const V m_qx = A::fma(A::lit(-2), A::sub(n[1], n[3]),
-                        A::add(A::sub(n[5], n[6]), A::sub(n[8], n[7])));
-  const V m_qy = A::fma(A::lit(-2), A::sub(n[2], n[4]),
-                        A::sub(A::add(n[5], n[6]), A::add(n[7], n[8])));
-  const V m_pxx = A::sub(A::add(n[1], n[3]), A::add(n[2], n[4]));
-  const V m_pxy = A::add(A::sub(n[5], n[6]), A::sub(n[7], n[8]));
+  const V ru2 = A::mul(rho, A::fma(ux, ux, A::mul(uy, uy)));
+  const V m_e = A::sub(A::fma(two, diag, A::sub(A::mul(A::lit(-4), h[0]), axis)),
+                       A::fma(A::lit(3), ru2, A::mul(A::lit(-2), drho)));
+  const V m_eps = A::sub(A::add(A::fma(A::lit(-2), axis, A::mul(A::lit(4), h[0])), diag),
+                         A::fma(A::lit(-3), ru2, drho));
+  const V m_qx = A::fma(A::lit(-3), A::sub(h[1], h[3]), A::mul(two, jx));
+  const V m_qy = A::fma(A::lit(-3), A::sub(h[2], h[4]), A::mul(two, jy));
+  const V m_pxx = A::sub(A::sub(A::add(h[1], h[3]), A::add(h[2], h[4])),
+                         A::mul(rho, A::mul(A::sub(ux, uy), A::add(ux, uy))));
+  const V m_pxy = A::fma(A::mul(A::lit(-1), A::mul(rho, ux)), uy,
+                         A::add(A::sub(h[5], h[6]), A::sub(h[7], h[8])));
   // relaxed amounts divided by the row norms
   using T = typename A::T;
   const V de = A::mul(A::splat((T)s.se * T(1.0 / 36.0)), m_e);
