@@ -206,20 +206,23 @@ __device__ __forceinline__ void collide_mrt(V h[9], const MrtRates<R>& s, V& drh
   const V dqy = A::mul(A::splat((T)s.sqy * T(1.0 / 12.0)), m_qy);
   const V dpxx = A::mul(A::splat((T)s.snxx * T(0.25)), m_pxx);
   const V dpxy = A::mul(A::splat((T)s.snxy * T(0.25)), m_pxy);
-  // h* = h - M^T d (columns of M)
+  // h* = h - M^T d (columns of M), with the sums the columns share
   const V e2 = A::fma(two, deps, de);            // de + 2 deps
   const V e5 = A::fma(two, de, deps);            // 2 de + deps
   h[0] = A::sub(h[0], A::mul(A::lit(4), A::sub(deps, de)));
-  // axis directions: -(de + 2 deps) -+ 2 dq +- dpxx
-  h[1] = A::sub(h[1], A::add(A::fma(A::lit(-2), dqx, dpxx), A::mul(A::lit(-1), e2)));
-  h[3] = A::sub(h[3], A::add(A::fma(two, dqx, dpxx), A::mul(A::lit(-1), e2)));
-  h[2] = A::sub(h[2], A::sub(A::fma(A::lit(-2), dqy, A::mul(A::lit(-1), e2)), dpxx));
-  h[4] = A::sub(h[4], A::sub(A::fma(two, dqy, A::mul(A::lit(-1), e2)), dpxx));
-  // diagonals: 2 de + deps +- dqx +- dqy +- dpxy
-  h[5] = A::sub(h[5], A::add(A::add(e5, A::add(dqx, dqy)), dpxy));
-  h[6] = A::sub(h[6], A::sub(A::add(e5, A::sub(dqy, dqx)), dpxy));
-  h[7] = A::sub(h[7], A::add(A::sub(e5, A::add(dqx, dqy)), dpxy));
-  h[8] = A::sub(h[8], A::sub(A::add(e5, A::sub(dqx, dqy)), dpxy));
+  // axis directions: h1, h3 -= dpxx - e2 -+ 2 dqx; h2, h4 -= -(e2 + dpxx) -+ 2 dqy
+  const V s13 = A::sub(dpxx, e2), s24 = A::mul(A::lit(-1), A::add(e2, dpxx));
+  h[1] = A::sub(h[1], A::fma(A::lit(-2), dqx, s13));
+  h[3] = A::sub(h[3], A::fma(two, dqx, s13));
+  h[2] = A::sub(h[2], A::fma(A::lit(-2), dqy, s24));
+  h[4] = A::sub(h[4], A::fma(two, dqy, s24));
+  // diagonals: h5, h7 -= (e5 + dpxy) +- (dqx + dqy); h6, h8 -= (e5 - dpxy) +- (dqy - dqx)
+  const V pp = A::add(e5, dpxy), pm = A::sub(e5, dpxy);
+  const V a = A::add(dqx, dqy), b = A::sub(dqy, dqx);
+  h[5] = A::sub(h[5], A::add(pp, a));
+  h[7] = A::sub(h[7], A::sub(pp, a));
+  h[6] = A::sub(h[6], A::add(pm, b));
+  h[8] = A::sub(h[8], A::sub(pm, b));
   drho_out = drho; ux_out = ux; uy_out = uy;
 }
 
