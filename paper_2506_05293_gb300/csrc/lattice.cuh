@@ -61,13 +61,11 @@ __device__ __forceinline__ void heq_all(R drho, R ux, R uy, R heq[9]) {
   }
 }
 
-// ---- lane arithmetic --------------------------------------------------------
-// The collision is written once over a lane type V: one node (float, double)
-// or two nodes side by side (float2, the packed FP32x2 instructions of sm_100
-// and later, one instruction for both nodes).  Every operation rounds once and
-// none is contracted by the compiler, so a pair of nodes collided as a float2
-// gets the bits of the same two nodes collided one at a time, whichever
-// kernel takes them.
+// ---- explicitly rounded arithmetic -------------------------------------------
+// The collision is written once over its arithmetic type V (float or double)
+// with every operation rounding once and none contracted by the compiler, so
+// every kernel that collides a node -- staged, register, in-place, boundary
+// blocks -- gets the same bits for it.
 template <typename V> struct Ar;
 template <> struct Ar<float> {
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
@@ -90,24 +88,6 @@ template <> struct Ar<double> {
   static __device__ __forceinline__ double splat(double v) { return v; }
   static __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
   static __device__ __forceinline__ bool bad(double x) { return !(fabs(x) < 1e30); }
-};
-template <> struct Ar<float2> {
-  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-  // a - b as b * (-1) + a: the product is exact, so this is RN(a - b)
-  static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
-    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
-  }
-  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-  using T = float;
-  static __device__ __forceinline__ float2 lit(double v) { return make_float2((float)v, (float)v); }
-  static __device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
-  static __device__ __forceinline__ float2 rcp(float2 x) {
-    return make_float2(__frcp_rn(x.x), __frcp_rn(x.y));
-  }
-  static __device__ __forceinline__ bool bad(float2 x) {
-    return !(fabsf(x.x) < 1e30f) || !(fabsf(x.y) < 1e30f);
-  }
 };
 
 // The same equilibrium evaluated pairwise: for a direction i and its opposite
