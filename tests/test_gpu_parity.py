@@ -383,6 +383,37 @@ def test_periodic_x_with_staged_kernel(L, variant):
     assert np.abs(f - o["f"]).max() < 1e-12
 
 
+@pytest.mark.parametrize("variant", [3, 4, 6])
+def test_periodic_x_fp16_row_windows(L, variant):
+    """FP16 storage through the staged variants (row windows fetched by tensor
+    copies, halo rows of three populations): an x-periodic box whose width is
+    not a multiple of the 128-column tile and strips of an odd height that do
+    not divide the lattice (the last strip is one row; its halo rows wrap in
+    y), against the register kernel (variant 1), which reads every pull from
+    global memory -- the same arithmetic, so the same bits."""
+    nx, ny = 300, 61
+    kind = cylinder_mask(nx, ny, 90.5, 30.1, 14)
+    init = random_smooth_state(nx, ny, seed=8, amp_u=0.03, amp_rho=0.01)
+
+    def run(rows, v):
+        cfg = L.lbm_config_default(nx=nx, ny=ny, tau=0.62, precision="fp16dev", x_periodic=1)
+        sim = L.lbm_create(cfg)
+        L.lbm_set_tiling(sim, rows, v)
+        L.lbm_set_geometry(sim, kind)
+        L.lbm_init_equilibrium(sim, *init)
+        L.lbm_step(sim, 37)
+        f = L.lbm_get_populations(sim)
+        fx, fy = L.lbm_forces(sim)
+        L.lbm_destroy(sim)
+        return f, fx, fy
+
+    ref = run(8, 1)
+    got = run(5, variant)
+    assert np.array_equal(got[0], ref[0])
+    assert np.allclose(got[1], ref[1], rtol=0, atol=1e-12 * np.abs(ref[1]).max())
+    assert np.allclose(got[2], ref[2], rtol=0, atol=1e-12 * np.abs(ref[1]).max())
+
+
 def test_inlet_ramp_fp64(L):
     """Inlet velocity ramped over the first steps (smooth start), with walls,
     a cylinder and the seeded perturbation."""
