@@ -118,9 +118,13 @@ typedef struct {
  * populations) and the momentum exchange is summed at the fluid side of each
  * counted link.  Results equal the AB step's (forces up to the summation
  * order).  An AA lattice runs alone (no batches), with the Zou & He outflow,
- * on its own kernel (tiling variants 0-2 set its occupancy; the autotuner
- * tries those), and supports neither capture calls nor lbm_copy_columns; one ghost column on each side keeps the
- * populations that leave the lattice, so exports stay exact. */
+ * on its own kernels (tiling variants 0-2: the register kernel at three
+ * occupancies; 3: a staged kernel, one block per strip, whose producer warp
+ * copies each row's source segments into shared memory with cp.async.bulk;
+ * the autotuner tries those four; variants 4-6 return LBM_ERR_UNSUPPORTED),
+ * and supports neither capture calls nor lbm_copy_columns; one ghost column on
+ * each side keeps the populations that leave the lattice, so exports stay
+ * exact. */
 typedef enum { LBM_LAYOUT_AB = 0, LBM_LAYOUT_AA = 1 } lbm_layout;
 
 /* Fill *cfg with defaults (tau 0.6, BGK, FP32, open x, rho_out 1). */

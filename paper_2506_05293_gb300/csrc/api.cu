@@ -1161,8 +1161,8 @@ static lbm_status check_tiling(int32_t rows, int32_t variant) {
 lbm_status lbm_set_tiling(lbm_sim* s, int32_t rows, int32_t variant) {
   if (lbm_status st = check_sim(s)) return st;
   if (lbm_status st = check_tiling(rows, variant)) return st;
-  if (s->layout == LBM_LAYOUT_AA && lbm::step_variant_is_bulk(variant))
-    return fail(LBM_ERR_UNSUPPORTED, "the in-place (AA) layout runs on variants 0-2");
+  if (s->layout == LBM_LAYOUT_AA && lbm::step_variant_is_bulk(variant) && variant != 3)
+    return fail(LBM_ERR_UNSUPPORTED, "the in-place (AA) layout runs on variants 0-3");
   LBM_GUARD_BEGIN
   lbm::group_set_tiling(s->own, rows, variant);
   return LBM_OK;

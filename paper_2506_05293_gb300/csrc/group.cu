@@ -823,7 +823,7 @@ float group_autotune(Group& g, int steps, int64_t flush_bytes) {
     float best = 1e30f;
     int best_rows = g.rows, best_var = g.variant;
     for (int v = 0; v < step_variants(); ++v) {
-      if (g.aa && step_variant_is_bulk(v)) continue;   // the in-place kernel: variants 0-2
+      if (g.aa && step_variant_is_bulk(v) && v != 3) continue;   // the in-place kernel: 0-3
       for (int r : rows_c) {
         group_set_tiling(g, r, v);
         build_table(g);

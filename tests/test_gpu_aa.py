@@ -1,5 +1,6 @@
 """The in-place (AA) layout against the FP64 oracle and against the two-buffer
-(AB) step: the walled cylinder channel with the Zou & He inlet (seeded
+(AB) step, through the register kernel (variant 0) and the staged kernel
+(variant 3): the walled cylinder channel with the Zou & He inlet (seeded
 perturbation) and outflow, BGK and MRT, an x-periodic lattice with a counted
 body, after odd and even step counts (the two layouts of the buffer); FP32
 bit for bit equal to the AB step; checkpoints, imports at odd counts and the
@@ -29,13 +30,13 @@ def _channel(nx=150, ny=48):
     return kind, (rho, ux, uy)
 
 
-def _run(L, kind, init, steps, layout, precision="fp64", rows=8, **kw):
+def _run(L, kind, init, steps, layout, precision="fp64", rows=8, variant=0, **kw):
     ny, nx = kind.shape
     cfg = L.lbm_config_default(nx=nx, ny=ny, precision=precision, layout=layout, **kw)
     s = L.lbm_create(cfg)
     L.lbm_set_geometry(s, kind)
     L.lbm_init_equilibrium(s, *init)
-    L.lbm_set_tiling(s, rows, 0)
+    L.lbm_set_tiling(s, rows, variant)
     L.lbm_step(s, steps)
     L.lbm_sync(s)
     out = dict(f=L.lbm_get_populations(s), fields=L.lbm_fields(s),
@@ -44,13 +45,15 @@ def _run(L, kind, init, steps, layout, precision="fp64", rows=8, **kw):
     return out
 
 
+@pytest.mark.parametrize("variant", [0, 3])
 @pytest.mark.parametrize("steps", [1, 2, 37, 40])
 @pytest.mark.parametrize("collision", ["bgk", "mrt"])
-def test_aa_matches_oracle_fp64(L, steps, collision):
+def test_aa_matches_oracle_fp64(L, steps, collision, variant):
     kind, init = _channel()
     ny, nx = kind.shape
     kw = dict(tau=0.58, collision=collision, u_in=0.05, v_pert_amp=1e-3, seed=9)
-    g = _run(L, kind, init, steps, "aa", **kw)
+    # variant 3: the staged in-place kernel, strips of 5 rows (48 = 9 x 5 + 3)
+    g = _run(L, kind, init, steps, "aa", rows=8 if variant == 0 else 5, variant=variant, **kw)
     o = lbm.Solver(lbm.Config(nx=nx, ny=ny, **kw), kind)
     o.init_equilibrium(*init)
     o.step(steps)
@@ -65,14 +68,15 @@ def test_aa_matches_oracle_fp64(L, steps, collision):
     assert np.abs(g["F"] - F).max() <= 1e-10 * np.abs(F).max()
 
 
+@pytest.mark.parametrize("variant", [0, 3])
 @pytest.mark.parametrize("steps", [5, 6])
-def test_aa_x_periodic_body_matches_oracle_fp64(L, steps):
-    nx, ny = 96, 40
+def test_aa_x_periodic_body_matches_oracle_fp64(L, steps, variant):
+    nx, ny = 160, 40        # two tiles: the wrap crosses tile boundaries
     kind = cylinder_mask(nx, ny, 30, ny / 2 - 0.3, 10)
     rho, ux, uy = random_smooth_state(nx, ny, seed=6, amp_u=0.02, amp_rho=0.004)
     ux = np.where(kind == 0, 0.03 + ux, 0.0)
     init = (rho, ux, np.where(kind == 0, uy, 0.0))
-    g = _run(L, kind, init, steps, "aa", tau=0.7, x_periodic=1)
+    g = _run(L, kind, init, steps, "aa", tau=0.7, x_periodic=1, variant=variant)
     o = lbm.Solver(lbm.Config(nx=nx, ny=ny, tau=0.7, x_periodic=True), kind)
     o.init_equilibrium(*init)
     o.step(steps)
@@ -83,11 +87,11 @@ def test_aa_x_periodic_body_matches_oracle_fp64(L, steps):
 
 
 @pytest.mark.parametrize("steps", [7, 8])
-@pytest.mark.parametrize("rows", [1, 16])
-def test_aa_equals_ab_bitwise_fp32(L, steps, rows):
+@pytest.mark.parametrize("rows,variant", [(1, 0), (16, 0), (16, 3), (7, 3)])
+def test_aa_equals_ab_bitwise_fp32(L, steps, rows, variant):
     kind, init = _channel(300, 96)
     kw = dict(tau=0.56, collision="mrt", u_in=0.05, v_pert_amp=1e-3, seed=2)
-    a = _run(L, kind, init, steps, "aa", precision="fp32", rows=rows, **kw)
+    a = _run(L, kind, init, steps, "aa", precision="fp32", rows=rows, variant=variant, **kw)
     b = _run(L, kind, init, steps, "ab", precision="fp32", rows=rows, **kw)
     fl = kind == 0
     assert np.array_equal(a["f"][:, fl], b["f"][:, fl])
@@ -166,15 +170,15 @@ def test_aa_rejects_what_it_does_not_support(L):
     calls = [lambda: L.lbm_set_outflow_cbc(s, 0.25, 0.1, 0.1),
              lambda: L.lbm_capture_plane(s, 10, 1, rows),
              lambda: L.lbm_capture_snapshot(s, 5, 6, rows),
-             lambda: L.lbm_set_tiling(s, 8, 3),
+             lambda: L.lbm_set_tiling(s, 8, 4),
              lambda: L.lbm_batch_create([s])]
     for c in calls:
         with pytest.raises(L.LbmError) as ei:
             c()
         assert ei.value.status == 7
-    # the autotuner times the register variants only and restores the state
+    # the autotuner times the in-place variants only and restores the state
     f0 = L.lbm_get_populations(s)
     rows_, var, _ = L.lbm_autotune(s, steps=4)
-    assert var in (0, 1, 2) and L.lbm_time(s) == 0
+    assert var in (0, 1, 2, 3) and L.lbm_time(s) == 0
     assert np.array_equal(L.lbm_get_populations(s), f0)
     L.lbm_destroy(s)
