@@ -414,15 +414,12 @@ def workload_config(wl, prec, layout, world):
 
 
 def graph_chunks(n):
-    """How group_step cuts a run of n steps: chunks of 32, 16, 8 or 4 steps
-    replayed from graphs, the remaining 0-3 steps launched directly.
-    Returns (chunks, direct launches)."""
+    """How group_step cuts a run of n steps: chunks of 32 steps and one of the
+    remaining 4-31 replayed from graphs, a remainder of 0-3 steps launched
+    directly.  Returns (chunks, direct launches)."""
     chunks = 0
     while n >= 4:
-        c = 32
-        while c > n:
-            c //= 2
-        n -= c
+        n -= min(32, n)
         chunks += 1
     return chunks, n
 

@@ -482,9 +482,9 @@ lbm_status lbm_step_noalloc(const lbm_config* cfg, const float* src, float* dst,
  * collision operators, inlet velocities and outflows -- by one kernel launch
  * per time step (the east boundary blocks of NN and characteristic outflows
  * run inside it), the launch table listing every member's strips; runs of
- * steps are cut into chunks of 32, 16, 8 or 4 steps that replay from CUDA
- * graphs (a graph is instantiated the first time its length and starting
- * buffer occur, then reused).  Members must share one precision and one stream
+ * steps are cut into chunks of 32 steps and one of the remaining 4-31 (fewer
+ * launch directly) that replay from CUDA graphs (a graph is instantiated the
+ * first time its length and starting buffer occur, then reused).  Members must share one precision and one stream
  * (lbm_config.stream) and be at the same step (for instance all freshly
  * initialised); the batch keeps them in lockstep.  Members remain ordinary
  * sims for every other call (lbm_forces, lbm_fields, ...); stepping a member

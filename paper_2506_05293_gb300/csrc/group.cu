@@ -729,10 +729,11 @@ void group_step(Group& g, int64_t n) {
     // steps that may run before the next capture
     const int64_t room = dcap <= 0 ? n : std::min<int64_t>(n, dcap);
     if (use_graphs && dcap != 0 && room >= kMinGraphChunk) {
-      // chunk lengths are powers of two (32, 16, 8, 4), so a run of any
-      // length replays graphs that earlier runs already instantiated
-      int64_t len = kGraphChunk;
-      while (len > room) len >>= 1;
+      // chunks of 32 steps and one of the remainder (4-31 steps): a run
+      // replays graphs of those lengths, each instantiated at its first use
+      // (at most 29 lengths per starting buffer); a short run is one graph,
+      // so one chunk boundary less breaks the programmatic launch chain
+      const int64_t len = std::min<int64_t>(kGraphChunk, room);
       cudaGraphExec_t ex = chunk_graph(g, len, q);
       group_finalize(g);
       launch_set_t(g.t_base, t, g.stream);

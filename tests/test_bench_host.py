@@ -81,11 +81,12 @@ def test_traffic_lookup_follows_the_summary_and_its_source_hash():
 
 def test_graph_chunks_and_launch_count():
     # runs are cut into chunks of 32, 16, 8 or 4 steps; 0-3 steps stay direct
-    assert bench.graph_chunks(20) == (2, 0)          # 16 + 4
+    assert bench.graph_chunks(20) == (1, 0)          # one 20-step graph
     assert bench.graph_chunks(2000) == (63, 0)       # 62 x 32 + 16
-    assert bench.graph_chunks(37) == (2, 1)          # 32 + 4 + 1
+    assert bench.graph_chunks(37) == (2, 0)          # 32 + 5
+    assert bench.graph_chunks(35) == (1, 3)          # 32, then 3 direct steps
     assert bench.graph_chunks(3) == (0, 3)
-    assert bench.step_launches(20) == 24
+    assert bench.step_launches(20) == 22
     assert bench.step_launches(2000) == 2126
 
 
